@@ -21,7 +21,7 @@ Sketch layout (the library's definition, restated in its header):
   element e of a row-major matrix belongs to group g = e // 4; group g is the
   Philox block at counter (g mod 2^32, g >> 32, stream, 0) and key
   (seed mod 2^32, seed >> 32); its words x0..x3 give
-  u_j = ((x_j >> 8) + 0.5) / 2^24 and
+  u_j = ((x_j >> 9) + 0.5) / 2^23 (24 significant bits, exact in float32) and
       z[4g]   = sqrt(-2 ln u0) cos(2 pi u1),  z[4g+1] = sqrt(-2 ln u0) sin(2 pi u1),
       z[4g+2] = sqrt(-2 ln u2) cos(2 pi u3),  z[4g+3] = sqrt(-2 ln u2) sin(2 pi u3).
   Omega_L (m x nu) uses stream 0, Omega_R (nu x n) stream 1.
@@ -62,8 +62,8 @@ def philox4x32_10(counter: np.ndarray, key) -> np.ndarray:
 
 
 def uniforms_from_words(x: np.ndarray) -> np.ndarray:
-    """u = ((x >> 8) + 0.5) / 2^24, exactly representable in float32 and float64."""
-    return ((np.asarray(x, dtype=np.uint64) >> np.uint64(8)).astype(np.float64) + 0.5) / 16777216.0
+    """u = ((x >> 9) + 0.5) / 2^23 in (0, 1), exactly representable in float32 and float64."""
+    return ((np.asarray(x, dtype=np.uint64) >> np.uint64(9)).astype(np.float64) + 0.5) / 8388608.0
 
 
 def gaussian_matrix(rows: int, cols: int, seed: int, stream: int) -> np.ndarray:

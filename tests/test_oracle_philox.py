@@ -27,8 +27,9 @@ def test_known_answer_vectors():
 
 
 def test_uniform_end_points():
-    u = philox.uniforms_from_words(np.array([0, 0xFFFFFFFF, 0xFF, 0x100]))
-    np.testing.assert_array_equal(u, [0.5 / 2**24, (2**24 - 0.5) / 2**24, 0.5 / 2**24, 1.5 / 2**24])
+    u = philox.uniforms_from_words(np.array([0, 0xFFFFFFFF, 0x1FF, 0x200]))
+    np.testing.assert_array_equal(u, [0.5 / 2**23, (2**23 - 0.5) / 2**23, 0.5 / 2**23, 1.5 / 2**23])
+    assert np.all(u.astype(np.float32).astype(np.float64) == u)
 
 
 def test_box_muller_radius_identity():
