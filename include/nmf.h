@@ -1,0 +1,212 @@
+/*
+ * nmf.h -- C ABI of libnmf: compressed NeNMF on one GB300 GPU (sm_103a).
+ *
+ * The problem (eq. 1): X ~= G F with X (n x m) nonnegative, G (n x p) >= 0,
+ * F (p x m) >= 0. NeNMF alternately solves eq. (2) for G and eq. (3) for F by
+ * an inner Nesterov loop (Sec. 2). Compressed NeNMF (Alg. 1) runs the same
+ * loop on X_L = L X and X_R = X R, where L (nu x n) and R (m x nu) come from
+ * the randomized subspace iteration of Alg. 2.
+ *
+ * Conventions shared by every call
+ *  - Matrices are dense, row-major, float32, with the leading dimension equal
+ *    to the number of columns (no padding): X is n x m, G is n x p, F is p x m,
+ *    L is nu x n, R is m x nu, X_L is nu x m, X_R is n x nu.
+ *  - Every matrix pointer is DEVICE memory owned by the caller, unless a
+ *    parameter says "host". The library keeps no pointer after a call returns.
+ *  - The library allocates no device memory. Each call that needs scratch space
+ *    has a *_workspace_size() query; the caller passes that many bytes of
+ *    device memory, 256-byte aligned. Workspace contents need no initialisation
+ *    and are not meaningful after the call.
+ *  - Calls are asynchronous and stream ordered on `stream` (a cudaStream_t;
+ *    NULL is the legacy default stream). They return after enqueueing work.
+ *    Argument errors are detected on the host, before anything is enqueued.
+ *  - Errors found on the device (non-finite values, a Cholesky breakdown the
+ *    shifted retry could not repair, a bounded wait that ran out) are written
+ *    to a status word in the workspace; nmf_workspace_status() reads it after
+ *    the stream has reached that point. A later kernel of the same call turns
+ *    into a no-op once that word is nonzero.
+ *  - Sizes: 1 <= p <= NMF_MAX_RANK, p <= nu <= NMF_MAX_SKETCH, nu <= min(n, m).
+ */
+#ifndef NMF_H
+#define NMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* nmf_stream_t; /* identical to cudaStream_t */
+
+typedef enum nmf_status {
+  NMF_OK = 0,
+  NMF_ERR_INVALID_ARG = 1,    /* bad size, null pointer, unsupported combination */
+  NMF_ERR_WORKSPACE = 2,      /* workspace null, too small or misaligned */
+  NMF_ERR_CUDA = 3,           /* a CUDA runtime call failed (launch, config) */
+  NMF_ERR_NOT_SPD = 4,        /* Gram matrix not positive definite even after the shift */
+  NMF_ERR_NONFINITE = 5,      /* NaN or Inf met on the device */
+  NMF_ERR_DEVICE_TIMEOUT = 6, /* a bounded device-side wait gave up */
+  NMF_ERR_UNSUPPORTED = 7     /* device is not sm_103 or feature not built */
+} nmf_status_t;
+
+typedef enum nmf_prec {
+  NMF_PREC_FP32 = 0, /* X products in float32 on CUDA cores */
+  NMF_PREC_BF16 = 1  /* X rounded once to bfloat16; products on tcgen05 tensor cores, float32 accumulate */
+} nmf_prec_t;
+
+enum { NMF_MAX_RANK = 32, NMF_MAX_SKETCH = 64 };
+
+/* Human-readable name of a status code (static storage). */
+const char* nmf_status_string(nmf_status_t status);
+
+/* Library ABI version: 100 * major + minor. */
+int nmf_version(void);
+
+/*
+ * Reads the device status word of a workspace used by an earlier call.
+ * Blocks until `stream` has drained. *status receives an nmf_status_t value.
+ */
+nmf_status_t nmf_workspace_status(nmf_stream_t stream, const void* workspace, int* status);
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian sketches (Alg. 2, first line: "Draw Gaussian random matrices")   */
+/* ------------------------------------------------------------------------ */
+/*
+ * out (rows x cols, device, row-major) <- iid N(0, 1) values, counter-based:
+ * element e uses Philox4x32-10 (Salmon et al. 2011) at counter
+ * (e/4 mod 2^32, (e/4) >> 32, stream_id, 0) with key (seed mod 2^32, seed >> 32);
+ * the four words x0..x3 map to u_j = ((x_j >> 9) + 0.5) / 2^23 and Box-Muller
+ * pairs (u0, u1) -> elements 4g, 4g+1 and (u2, u3) -> 4g+2, 4g+3 (cos, sin).
+ * nmf_compress uses stream_id 0 for Omega_L (m x nu) and 1 for Omega_R (nu x n).
+ */
+nmf_status_t nmf_gaussian_sketch(nmf_stream_t stream, int rows, int cols, uint64_t seed,
+                                 uint32_t stream_id, float* out);
+
+/* ------------------------------------------------------------------------ */
+/* Compression: randomized subspace iteration (Alg. 2) and X_L, X_R (Alg. 1) */
+/* ------------------------------------------------------------------------ */
+size_t nmf_compress_workspace_size(int n, int m, int nu, nmf_prec_t prec);
+
+/*
+ * Alg. 2 with q power steps, each orthonormalisation a CholeskyQR2 whose Gram
+ * matrix is accumulated in extended (float-float) precision and factorised in
+ * float64; then X_L = L X and X_R = X R (first line of Alg. 1).
+ *
+ *  X        n x m input, nonnegative (not checked).
+ *  omega_L  m x nu Gaussian sketch, or NULL to draw it from `seed` (stream 0).
+ *  omega_R  nu x n Gaussian sketch, or NULL to draw it from `seed` (stream 1).
+ *           Both NULL or both non-NULL.
+ *  L        out, nu x n, orthonormal rows: L = (Q_L^(q))^T.
+ *  R        out, m x nu, orthonormal columns: R = (Q_R^(q))^T.
+ *  XL       out, nu x m, X_L = L X.
+ *  XR       out, n x nu, X_R = X R.
+ * Alg. 2's last line names the half-step bases Q~^(q), which have the wrong
+ * shapes; the full-step bases Q^(q) are used. prec selects how the 2q+2
+ * passes over X compute (NMF_PREC_BF16: X rounded to bfloat16 once, tensor
+ * cores; NMF_PREC_FP32: float32 CUDA cores).
+ */
+nmf_status_t nmf_compress(nmf_stream_t stream, int n, int m, int nu, int q, nmf_prec_t prec,
+                          const float* X, const float* omega_L, const float* omega_R, uint64_t seed,
+                          float* L, float* R, float* XL, float* XR, void* workspace,
+                          size_t workspace_bytes);
+
+/* ------------------------------------------------------------------------ */
+/* NeNMF solve: plain (eq. 2-3) or compressed (Alg. 1)                        */
+/* ------------------------------------------------------------------------ */
+typedef enum nenmf_mode { NENMF_PLAIN = 0, NENMF_COMPRESSED = 1 } nenmf_mode_t;
+typedef enum nenmf_tol_mode { NENMF_TOL_REL = 0, NENMF_TOL_ABS = 1 } nenmf_tol_mode_t;
+
+typedef struct nenmf_problem {
+  int mode;          /* nenmf_mode_t */
+  int n, m, p, nu;   /* nu is ignored in plain mode */
+  int prec;          /* plain mode: nmf_prec_t of the two X products per outer iteration */
+  const float* X;    /* plain mode: n x m; ignored in compressed mode */
+  const float* L;    /* compressed: nu x n */
+  const float* R;    /* compressed: m x nu */
+  const float* XL;   /* compressed: nu x m */
+  const float* XR;   /* compressed: n x nu */
+} nenmf_problem_t;
+
+typedef struct nenmf_params {
+  int max_outer;       /* outer iterations T (>= 0) */
+  int max_inner;       /* Max_iter of the inner loop, per factor (>= 1) */
+  int min_inner;       /* the stop test is not applied before this many iterations (>= 1) */
+  int tol_mode;        /* nenmf_tol_mode_t */
+  double tol;          /* <= 0 disables the projected-gradient stop test */
+  float* record_G;     /* optional device [max_outer][n][p]: G after each outer iteration */
+  float* record_F;     /* optional device [max_outer][p][m]: F after each outer iteration */
+  long long* record_time_ns; /* optional device [max_outer + 1]: %globaltimer at the start and after each outer iteration */
+} nenmf_params_t;
+
+typedef struct nenmf_stats {
+  int status;             /* device-detected nmf_status_t */
+  int outer_done;         /* outer iterations completed */
+  int last_inner[2];      /* inner iterations of the last G and F solves */
+  long long total_inner[2]; /* inner iterations summed over the run (G, F) */
+  double eps;             /* absolute stop threshold used (0 when disabled) */
+  double pg_norm[2];      /* ||P grad||_F of the last G and F solves at their returned iterates */
+  double lipschitz[2];    /* L_c of the last G and F solves */
+} nenmf_stats_t;
+
+size_t nenmf_solve_workspace_size(const nenmf_problem_t* problem);
+
+/*
+ * Runs max_outer outer iterations from (G, F), updating both in place.
+ * The inner loop (Sec. 2): Y_0 = current factor, alpha_0 = 1; per k:
+ * F_k = max(0, Y_k - (H Y_k - B) / L_c), Y_{k+1} = F_k + beta_k (F_k - F_{k-1}),
+ * beta_k = (alpha_k - 1) / alpha_{k+1}, with L_c = lambda_max(H) and the
+ * projected-gradient test ||P grad(F_k)||_F <= eps from min_inner on
+ * (eps = tol * initial joint projected-gradient norm for NENMF_TOL_REL).
+ * The returned factor is the projected iterate F_k.
+ *  problem  host pointer; its matrix pointers are device memory.
+ *  params   host pointer.
+ *  stats    device pointer to one nenmf_stats_t (may be NULL).
+ */
+nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, float* G, float* F,
+                         const nenmf_params_t* params, nenmf_stats_t* stats, void* workspace,
+                         size_t workspace_bytes);
+
+/* ------------------------------------------------------------------------ */
+/* One pass over X, two products (the building block of Alg. 2)              */
+/* ------------------------------------------------------------------------ */
+size_t nmf_dual_product_workspace_size(int n, int m, int k, nmf_prec_t prec);
+
+/*
+ * YN = X A (n x k) and YT = X^T B (m x k) from a single read of X, the two
+ * products every pass of Alg. 2 needs (X Q~_L and X^T Q_L^T for one chain,
+ * the transposed pair for the other; Alg. 1's X R and L X likewise).
+ *  A   m x k (or NULL together with YN), B  n x k (or NULL together with YT);
+ *  1 <= k <= NMF_MAX_SKETCH. Partial sums are combined in a fixed order, so
+ *  results are bitwise reproducible. prec as for nmf_compress (NMF_PREC_BF16
+ *  rounds X, A and B to bfloat16 and accumulates in float32).
+ */
+nmf_status_t nmf_dual_product(nmf_stream_t stream, int n, int m, int k, nmf_prec_t prec, const float* X,
+                              const float* A, const float* B, float* YN, float* YT, void* workspace,
+                              size_t workspace_bytes);
+
+/*
+ * Selects the kernel for NMF_PREC_BF16 X passes: 0 (default) uses tcgen05
+ * tensor cores, 1 uses float32 CUDA cores on the same bfloat16 inputs (same
+ * input rounding, different summation order). Process-wide; not thread-safe
+ * against concurrent calls. Workspace sizes depend on it: query after setting.
+ */
+void nmf_set_kernel_path(int force_cuda_cores);
+
+/* ------------------------------------------------------------------------ */
+/* Relative reconstruction error, eq. (4)                                     */
+/* ------------------------------------------------------------------------ */
+size_t nmf_rre_workspace_size(int n, int m, int p);
+
+/*
+ * out (device, 2 doubles) <- { ||X - G F||_F^2, ||X||_F^2 } in one pass over X,
+ * products in float32 and sums in float64 (fixed reduction order).
+ */
+nmf_status_t nmf_rre(nmf_stream_t stream, int n, int m, int p, const float* X, const float* G,
+                     const float* F, double* out, void* workspace, size_t workspace_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMF_H */

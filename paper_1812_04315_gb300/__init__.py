@@ -1,0 +1,287 @@
+"""Python binding of libnmf (compressed NeNMF on GB300): argument marshalling only.
+
+Every function takes and returns torch CUDA tensors (float32, contiguous) and
+enqueues work on torch's current stream through the C ABI of include/nmf.h;
+all arithmetic runs in the library's CUDA kernels. The library must have been
+built (`paper_1812_04315_gb300.build.build()`); there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnmf.so")
+
+PREC_FP32 = 0
+PREC_BF16 = 1
+PLAIN = 0
+COMPRESSED = 1
+TOL_REL = 0
+TOL_ABS = 1
+MAX_RANK = 32
+MAX_SKETCH = 64
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "workspace", 3: "CUDA error", 4: "not SPD",
+          5: "non-finite", 6: "device timeout", 7: "unsupported"}
+
+
+class NmfError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)} (status {code})")
+        self.code = code
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("n", ctypes.c_int), ("m", ctypes.c_int), ("p", ctypes.c_int),
+                ("nu", ctypes.c_int), ("prec", ctypes.c_int), ("X", ctypes.c_void_p), ("L", ctypes.c_void_p),
+                ("R", ctypes.c_void_p), ("XL", ctypes.c_void_p), ("XR", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int), ("min_inner", ctypes.c_int),
+                ("tol_mode", ctypes.c_int), ("tol", ctypes.c_double), ("record_G", ctypes.c_void_p),
+                ("record_F", ctypes.c_void_p), ("record_time_ns", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_done", ctypes.c_int), ("last_inner", ctypes.c_int * 2),
+                ("total_inner", ctypes.c_longlong * 2), ("eps", ctypes.c_double), ("pg_norm", ctypes.c_double * 2),
+                ("lipschitz", ctypes.c_double * 2)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libnmf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1812_04315_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, sz, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_uint64
+    sigs = {
+        "nmf_status_string": (ctypes.c_char_p, [i]),
+        "nmf_version": (i, []),
+        "nmf_workspace_status": (i, [vp, vp, ctypes.POINTER(i)]),
+        "nmf_gaussian_sketch": (i, [vp, i, i, u64, ctypes.c_uint32, vp]),
+        "nmf_compress_workspace_size": (sz, [i, i, i, i]),
+        "nmf_compress": (i, [vp, i, i, i, i, i, vp, vp, vp, u64, vp, vp, vp, vp, vp, sz]),
+        "nenmf_solve_workspace_size": (sz, [ctypes.POINTER(Problem)]),
+        "nenmf_solve": (i, [vp, ctypes.POINTER(Problem), vp, vp, ctypes.POINTER(Params), vp, vp, sz]),
+        "nmf_rre_workspace_size": (sz, [i, i, i]),
+        "nmf_rre": (i, [vp, i, i, i, vp, vp, vp, vp, vp, sz]),
+        "nmf_dual_product_workspace_size": (sz, [i, i, i, i]),
+        "nmf_dual_product": (i, [vp, i, i, i, i, vp, vp, vp, vp, vp, vp, sz]),
+        "nmf_set_kernel_path": (None, [i]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names declared by the binding (all must resolve in the library)."""
+    return ["nmf_status_string", "nmf_version", "nmf_workspace_status", "nmf_gaussian_sketch",
+            "nmf_compress_workspace_size", "nmf_compress", "nenmf_solve_workspace_size", "nenmf_solve",
+            "nmf_rre_workspace_size", "nmf_rre", "nmf_dual_product_workspace_size", "nmf_dual_product",
+            "nmf_set_kernel_path"]
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check_f32(name, t, shape):
+    torch = _torch()
+    if t.device.type != "cuda" or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def _ok(code, where):
+    if code != 0:
+        raise NmfError(code, where)
+
+
+def workspace(nbytes: int):
+    """Device workspace of nbytes (256-byte aligned through the caching allocator)."""
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device="cuda")
+
+
+def workspace_status(ws) -> int:
+    v = ctypes.c_int(0)
+    _ok(lib().nmf_workspace_status(_stream(), _ptr(ws), ctypes.byref(v)), "nmf_workspace_status")
+    return v.value
+
+
+def set_kernel_path(force_cuda_cores: bool):
+    lib().nmf_set_kernel_path(1 if force_cuda_cores else 0)
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+
+def gaussian_sketch(rows: int, cols: int, seed: int, stream_id: int, out=None):
+    torch = _torch()
+    if out is None:
+        out = torch.empty((rows, cols), dtype=torch.float32, device="cuda")
+    _check_f32("out", out, (rows, cols))
+    _ok(lib().nmf_gaussian_sketch(_stream(), rows, cols, seed, stream_id, _ptr(out)), "nmf_gaussian_sketch")
+    return out
+
+
+def compress_workspace_size(n, m, nu, prec=PREC_BF16) -> int:
+    return int(lib().nmf_compress_workspace_size(n, m, nu, prec))
+
+
+def compress(X, nu: int, q: int, prec: int = PREC_BF16, omega_L=None, omega_R=None, seed: int = 0, ws=None,
+             out=None):
+    """Alg. 2 + first line of Alg. 1: returns (L nu x n, R m x nu, X_L nu x m, X_R n x nu)."""
+    torch = _torch()
+    n, m = X.shape
+    _check_f32("X", X, (n, m))
+    if omega_L is not None:
+        _check_f32("omega_L", omega_L, (m, nu))
+        _check_f32("omega_R", omega_R, (nu, n))
+    if out is None:
+        out = (torch.empty((nu, n), dtype=torch.float32, device="cuda"),
+               torch.empty((m, nu), dtype=torch.float32, device="cuda"),
+               torch.empty((nu, m), dtype=torch.float32, device="cuda"),
+               torch.empty((n, nu), dtype=torch.float32, device="cuda"))
+    L, R, XL, XR = out
+    if ws is None:
+        ws = workspace(compress_workspace_size(n, m, nu, prec))
+    _ok(lib().nmf_compress(_stream(), n, m, nu, q, prec, _ptr(X), _ptr(omega_L), _ptr(omega_R), seed, _ptr(L),
+                           _ptr(R), _ptr(XL), _ptr(XR), _ptr(ws), ws.numel()), "nmf_compress")
+    return L, R, XL, XR
+
+
+def _problem(mode, n, m, p, nu=0, prec=PREC_FP32, X=None, L=None, R=None, XL=None, XR=None):
+    pr = Problem()
+    pr.mode, pr.n, pr.m, pr.p, pr.nu, pr.prec = mode, n, m, p, nu, prec
+    pr.X = X.data_ptr() if X is not None else None
+    pr.L = L.data_ptr() if L is not None else None
+    pr.R = R.data_ptr() if R is not None else None
+    pr.XL = XL.data_ptr() if XL is not None else None
+    pr.XR = XR.data_ptr() if XR is not None else None
+    return pr
+
+
+def plain_problem(X, p: int, prec: int = PREC_FP32):
+    n, m = X.shape
+    _check_f32("X", X, (n, m))
+    return _problem(PLAIN, n, m, p, 0, prec, X=X)
+
+
+def compressed_problem(L, R, XL, XR, p: int):
+    nu, n = L.shape
+    m = R.shape[0]
+    for name, t, shp in (("L", L, (nu, n)), ("R", R, (m, nu)), ("XL", XL, (nu, m)), ("XR", XR, (n, nu))):
+        _check_f32(name, t, shp)
+    return _problem(COMPRESSED, n, m, p, nu, PREC_FP32, L=L, R=R, XL=XL, XR=XR)
+
+
+def solve_workspace_size(problem: Problem) -> int:
+    return int(lib().nenmf_solve_workspace_size(ctypes.byref(problem)))
+
+
+@dataclass
+class SolveRecord:
+    G: object = None      # [T, n, p]
+    F: object = None      # [T, p, m]
+    times: object = None  # int64 [T + 1] (ns, %globaltimer)
+
+
+def solve(problem: Problem, G, F, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
+          tol_mode: int = TOL_REL, record: SolveRecord | None = None, stats=None, ws=None):
+    """Runs nenmf_solve in place on G (n x p) and F (p x m); returns the device stats buffer."""
+    torch = _torch()
+    n, m, p = problem.n, problem.m, problem.p
+    _check_f32("G", G, (n, p))
+    _check_f32("F", F, (p, m))
+    pa = Params()
+    pa.max_outer, pa.max_inner, pa.min_inner, pa.tol_mode, pa.tol = max_outer, max_inner, min_inner, tol_mode, tol
+    if record is not None:
+        pa.record_G = record.G.data_ptr() if record.G is not None else None
+        pa.record_F = record.F.data_ptr() if record.F is not None else None
+        pa.record_time_ns = record.times.data_ptr() if record.times is not None else None
+    if stats is None:
+        stats = torch.zeros(ctypes.sizeof(Stats), dtype=torch.uint8, device="cuda")
+    if ws is None:
+        ws = workspace(solve_workspace_size(problem))
+    _ok(lib().nenmf_solve(_stream(), ctypes.byref(problem), _ptr(G), _ptr(F), ctypes.byref(pa), _ptr(stats),
+                          _ptr(ws), ws.numel()), "nenmf_solve")
+    return stats
+
+
+def read_stats(stats) -> Stats:
+    raw = bytes(stats.cpu().numpy().tobytes())
+    return Stats.from_buffer_copy(raw)
+
+
+def rre_workspace_size(n, m, p) -> int:
+    return int(lib().nmf_rre_workspace_size(n, m, p))
+
+
+def rre_terms(X, G, F, out=None, ws=None):
+    """Device tensor [||X - G F||^2, ||X||^2] (float64)."""
+    torch = _torch()
+    n, m = X.shape
+    p = G.shape[1]
+    _check_f32("X", X, (n, m))
+    _check_f32("G", G, (n, p))
+    _check_f32("F", F, (p, m))
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device="cuda")
+    if ws is None:
+        ws = workspace(rre_workspace_size(n, m, p))
+    _ok(lib().nmf_rre(_stream(), n, m, p, _ptr(X), _ptr(G), _ptr(F), _ptr(out), _ptr(ws), ws.numel()), "nmf_rre")
+    return out
+
+
+def rre(X, G, F) -> float:
+    t = rre_terms(X, G, F).cpu()
+    return float((t[0] / t[1]).sqrt())
+
+
+def dual_product(X, A=None, B=None, prec: int = PREC_FP32, ws=None):
+    """(X A, X^T B) from one pass over X; either operand may be None."""
+    torch = _torch()
+    n, m = X.shape
+    k = (A if A is not None else B).shape[1]
+    _check_f32("X", X, (n, m))
+    if A is not None:
+        _check_f32("A", A, (m, k))
+    if B is not None:
+        _check_f32("B", B, (n, k))
+    YN = torch.empty((n, k), dtype=torch.float32, device="cuda") if A is not None else None
+    YT = torch.empty((m, k), dtype=torch.float32, device="cuda") if B is not None else None
+    if ws is None:
+        ws = workspace(lib().nmf_dual_product_workspace_size(n, m, k, prec))
+    _ok(lib().nmf_dual_product(_stream(), n, m, k, prec, _ptr(X), _ptr(A), _ptr(B), _ptr(YN), _ptr(YT), _ptr(ws),
+                               ws.numel()), "nmf_dual_product")
+    return YN, YT

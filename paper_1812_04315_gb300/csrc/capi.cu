@@ -1,0 +1,576 @@
+// capi.cu -- the extern "C" entry points of include/nmf.h: argument checks,
+// workspace carving and the stream-ordered schedules of Alg. 2 (nmf_compress)
+// and of Alg. 1 / plain NeNMF (nenmf_solve).
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+using namespace nmf;
+
+namespace {
+
+#define NMF_CU(call)                                   \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return NMF_ERR_CUDA;        \
+  } while (0)
+
+int g_force_simt = 0;  // nmf_set_kernel_path
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 152;
+  return sms;
+}
+
+bool ws_ok(const void* ws, size_t bytes, size_t need) {
+  return ws != nullptr && (reinterpret_cast<uintptr_t>(ws) & 255u) == 0 && bytes >= need;
+}
+
+bool use_tc(nmf_prec_t prec) { return prec == NMF_PREC_BF16 && !g_force_simt && xpass_tc_available(); }
+
+}  // namespace
+
+namespace nmf {
+
+int device_sm_count() { return sm_count(); }
+
+XPassPlan xpass_plan(int n, int m, int nu, nmf_prec_t prec, int num_sms) {
+  if (use_tc(prec)) return xpass_tc_plan(n, m, nu, num_sms);
+  return xpass_simt_plan(n, m, nu, num_sms);
+}
+
+cudaError_t xpass_launch(const XPassPlan& plan, const XPassArgs& a, nmf_prec_t prec, cudaStream_t s) {
+  if (use_tc(prec)) return xpass_tc_launch(plan, a, s);
+  return xpass_simt_launch(plan, a, prec == NMF_PREC_BF16, s);
+}
+
+}  // namespace nmf
+
+namespace {
+
+// ----------------------------------------------------------------------------
+// nmf_compress workspace
+// ----------------------------------------------------------------------------
+struct CompressWs {
+  Control* ctrl;
+  __nv_bfloat16* Xb;
+  int ldxb;
+  void* opA;   // NV x lda
+  int lda;
+  void* opB;   // NV x ldb
+  int ldb;
+  float* partN;
+  float* partT;
+  float* YN[2];
+  float* YT[2];
+  float2* gramN;
+  float2* gramT;
+  float* rinvN[3];
+  float* rinvT[3];
+  float* omega;
+  XPassPlan plan;
+  size_t bytes;
+};
+
+CompressWs carve_compress(void* base, int n, int m, int nu, nmf_prec_t prec) {
+  CompressWs w{};
+  Carver cv(base);
+  w.plan = xpass_plan(n, m, nu, prec, sm_count());
+  const int NV = w.plan.NV;
+  const size_t es = prec == NMF_PREC_BF16 ? 2 : 4;
+  w.ctrl = cv.take<Control>(1);
+  if (prec == NMF_PREC_BF16) {
+    w.ldxb = round_up(m, 64);
+    w.Xb = cv.take<__nv_bfloat16>((size_t)n * w.ldxb);
+  }
+  w.lda = round_up(m, 128);
+  w.ldb = round_up(n, 128);
+  w.opA = cv.take<char>((size_t)NV * w.lda * es);
+  w.opB = cv.take<char>((size_t)NV * w.ldb * es);
+  w.partN = cv.take<float>((size_t)w.plan.S_c * n * NV);
+  w.partT = cv.take<float>((size_t)w.plan.S_r * m * NV);
+  for (int i = 0; i < 2; ++i) {
+    w.YN[i] = cv.take<float>((size_t)n * nu);
+    w.YT[i] = cv.take<float>((size_t)m * nu);
+  }
+  const int E = nu * (nu + 1) / 2;
+  w.gramN = cv.take<float2>((size_t)rows_ctas(n) * E);
+  w.gramT = cv.take<float2>((size_t)rows_ctas(m) * E);
+  for (int i = 0; i < 3; ++i) {
+    w.rinvN[i] = cv.take<float>((size_t)nu * nu);
+    w.rinvT[i] = cv.take<float>((size_t)nu * nu);
+  }
+  w.omega = cv.take<float>((size_t)(n > m ? n : m) * nu);
+  w.bytes = cv.size();
+  return w;
+}
+
+// One CholeskyQR2 (+ conditional third pass) of the two products of a pass.
+// Outputs: next operands (N job -> opB, T job -> opA), and on the last
+// orthonormalisation L = Q_N^T and R = Q_T.
+nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16, float* Lout, float* Rout,
+                            cudaStream_t s) {
+  Control* ctrl = w.ctrl;
+  int* flagN = &ctrl->flags[0];
+  int* flagT = &ctrl->flags[1];
+  const int NV = w.plan.NV;
+  // K1: reduce the partials, Gram 1
+  RowJob r1[2] = {};
+  r1[0].part = w.partN; r1[0].S = w.plan.S_c; r1[0].ldp = NV; r1[0].N = n; r1[0].nu = nu;
+  r1[0].Y = w.YN[0]; r1[0].gram_part = w.gramN;
+  r1[1].part = w.partT; r1[1].S = w.plan.S_r; r1[1].ldp = NV; r1[1].N = m; r1[1].nu = nu;
+  r1[1].Y = w.YT[0]; r1[1].gram_part = w.gramT;
+  NMF_CU(rows_launch(r1, 2, ctrl, s));
+  // K2
+  CholJob c1[2] = {};
+  c1[0].gram_part = w.gramN; c1[0].parts = rows_ctas(n); c1[0].nu = nu; c1[0].rinv = w.rinvN[0];
+  c1[0].shift_flag = flagN; c1[0].reset_flag = 1;
+  c1[1].gram_part = w.gramT; c1[1].parts = rows_ctas(m); c1[1].nu = nu; c1[1].rinv = w.rinvT[0];
+  c1[1].shift_flag = flagT; c1[1].reset_flag = 1;
+  NMF_CU(chol_launch(c1, 2, ctrl, s));
+  // K3: Q1 = Y R1^-1, Gram 2
+  RowJob r2[2] = {};
+  r2[0].src = w.YN[0]; r2[0].rinv = w.rinvN[0]; r2[0].N = n; r2[0].nu = nu; r2[0].Y = w.YN[1]; r2[0].gram_part = w.gramN;
+  r2[1].src = w.YT[0]; r2[1].rinv = w.rinvT[0]; r2[1].N = m; r2[1].nu = nu; r2[1].Y = w.YT[1]; r2[1].gram_part = w.gramT;
+  NMF_CU(rows_launch(r2, 2, ctrl, s));
+  // K4
+  CholJob c2[2] = {c1[0], c1[1]};
+  c2[0].rinv = w.rinvN[1]; c2[0].reset_flag = 0;
+  c2[1].rinv = w.rinvT[1]; c2[1].reset_flag = 0;
+  NMF_CU(chol_launch(c2, 2, ctrl, s));
+  // K5: Q2 = Q1 R2^-1 -> outputs; Gram 3 only if a shift was taken.
+  float* QN = w.YN[0];
+  float* QT = Rout ? Rout : w.YT[0];
+  RowJob r3[2] = {};
+  r3[0].src = w.YN[1]; r3[0].rinv = w.rinvN[1]; r3[0].N = n; r3[0].nu = nu; r3[0].Y = QN;
+  r3[0].op = w.opB; r3[0].ldop = w.ldb; r3[0].op_bf16 = bf16; r3[0].Yt = Lout;
+  r3[0].gram_part = w.gramN; r3[0].gram_flag = flagN;
+  r3[1].src = w.YT[1]; r3[1].rinv = w.rinvT[1]; r3[1].N = m; r3[1].nu = nu; r3[1].Y = QT;
+  r3[1].op = w.opA; r3[1].ldop = w.lda; r3[1].op_bf16 = bf16;
+  r3[1].gram_part = w.gramT; r3[1].gram_flag = flagT;
+  NMF_CU(rows_launch(r3, 2, ctrl, s));
+  // K6, K7: third pass, in place, only where a shift was taken.
+  CholJob c3[2] = {c1[0], c1[1]};
+  c3[0].rinv = w.rinvN[2]; c3[0].shift_flag = nullptr; c3[0].run_flag = flagN;
+  c3[1].rinv = w.rinvT[2]; c3[1].shift_flag = nullptr; c3[1].run_flag = flagT;
+  NMF_CU(chol_launch(c3, 2, ctrl, s));
+  RowJob r4[2] = {r3[0], r3[1]};
+  r4[0].src = QN; r4[0].rinv = w.rinvN[2]; r4[0].gram_part = nullptr; r4[0].gram_flag = nullptr; r4[0].run_flag = flagN;
+  r4[1].src = QT; r4[1].rinv = w.rinvT[2]; r4[1].gram_part = nullptr; r4[1].gram_flag = nullptr; r4[1].run_flag = flagT;
+  NMF_CU(rows_launch(r4, 2, ctrl, s));
+  return NMF_OK;
+}
+
+
+// ----------------------------------------------------------------------------
+// nenmf_solve workspace
+// ----------------------------------------------------------------------------
+constexpr int kMaxInner = 4096;
+
+struct SolveWs {
+  Control* ctrl;
+  float* beta;
+  float* Gt;       // p x n
+  int ctasG, ctasF;
+  float* WG;       // [ctasF][p][nu]: partials of F_R = F R (compressed)
+  float* WF;       // [ctasG][p][nu]: partials of G_L^T = G^T L^T
+  float* HG;       // [ctasF][p][p]: partials of F F^T (plain)
+  float* HF;       // [ctasG][p][p]: partials of G^T G
+  double* pg2G;    // [3 * ctasG]
+  double* pg2F;    // [3 * ctasF]
+  double* initG;   // [ctasG]
+  double* initF;   // [ctasF]
+  __nv_bfloat16* Xb;
+  int ldxb;
+  void* opF;       // NV x ldF: F as the N-product operand (A^T = F)
+  int ldF;
+  void* opG;       // NV x ldG: G^T as the T-product operand (B^T = G^T)
+  int ldG;
+  float* partN;
+  float* partT;
+  XPassPlan plan;
+  size_t bytes;
+};
+
+SolveWs carve_solve(void* base, const nenmf_problem_t& pr) {
+  SolveWs w{};
+  Carver cv(base);
+  const int n = pr.n, m = pr.m, p = pr.p;
+  const bool plain = pr.mode == NENMF_PLAIN;
+  const int nu = plain ? 0 : pr.nu;
+  w.ctrl = cv.take<Control>(1);
+  w.beta = cv.take<float>(kMaxInner);
+  w.Gt = cv.take<float>((size_t)p * n);
+  w.ctasG = solve_ctas(n);
+  w.ctasF = solve_ctas(m);
+  if (!plain) {
+    w.WG = cv.take<float>((size_t)w.ctasF * p * nu);
+    w.WF = cv.take<float>((size_t)w.ctasG * p * nu);
+  } else {
+    w.HG = cv.take<float>((size_t)w.ctasF * p * p);
+    w.HF = cv.take<float>((size_t)w.ctasG * p * p);
+  }
+  w.pg2G = cv.take<double>((size_t)3 * w.ctasG);
+  w.pg2F = cv.take<double>((size_t)3 * w.ctasF);
+  w.initG = cv.take<double>(w.ctasG);
+  w.initF = cv.take<double>(w.ctasF);
+  if (plain) {
+    const nmf_prec_t prec = (nmf_prec_t)pr.prec;
+    w.plan = xpass_plan(n, m, p, prec, sm_count());
+    const size_t es = prec == NMF_PREC_BF16 ? 2 : 4;
+    if (prec == NMF_PREC_BF16) {
+      w.ldxb = round_up(m, 64);
+      w.Xb = cv.take<__nv_bfloat16>((size_t)n * w.ldxb);
+    }
+    w.ldF = round_up(m, 128);
+    w.ldG = round_up(n, 128);
+    w.opF = cv.take<char>((size_t)w.plan.NV * w.ldF * es);
+    w.opG = cv.take<char>((size_t)w.plan.NV * w.ldG * es);
+    w.partN = cv.take<float>((size_t)w.plan.S_c * n * w.plan.NV);
+    w.partT = cv.take<float>((size_t)w.plan.S_r * m * w.plan.NV);
+  }
+  w.bytes = cv.size();
+  return w;
+}
+
+bool problem_ok(const nenmf_problem_t* pr) {
+  if (!pr) return false;
+  if (pr->n < 1 || pr->m < 1 || pr->p < 1 || pr->p > NMF_MAX_RANK) return false;
+  if (pr->mode == NENMF_PLAIN) {
+    if (!pr->X) return false;
+    if (pr->prec != NMF_PREC_FP32 && pr->prec != NMF_PREC_BF16) return false;
+    return true;
+  }
+  if (pr->mode != NENMF_COMPRESSED) return false;
+  if (pr->nu < pr->p || pr->nu > NMF_MAX_SKETCH) return false;
+  return pr->L && pr->R && pr->XL && pr->XR;
+}
+
+// ----------------------------------------------------------------------------
+// nmf_dual_product workspace
+// ----------------------------------------------------------------------------
+struct DualWs {
+  Control* ctrl;
+  __nv_bfloat16* Xb;
+  int ldxb;
+  void* opA;
+  int lda;
+  void* opB;
+  int ldb;
+  float* partN;
+  float* partT;
+  XPassPlan plan;
+  size_t bytes;
+};
+
+DualWs carve_dual(void* base, int n, int m, int k, nmf_prec_t prec) {
+  DualWs w{};
+  Carver cv(base);
+  w.plan = xpass_plan(n, m, k, prec, sm_count());
+  const size_t es = prec == NMF_PREC_BF16 ? 2 : 4;
+  w.ctrl = cv.take<Control>(1);
+  if (prec == NMF_PREC_BF16) {
+    w.ldxb = round_up(m, 64);
+    w.Xb = cv.take<__nv_bfloat16>((size_t)n * w.ldxb);
+  }
+  w.lda = round_up(m, 128);
+  w.ldb = round_up(n, 128);
+  w.opA = cv.take<char>((size_t)w.plan.NV * w.lda * es);
+  w.opB = cv.take<char>((size_t)w.plan.NV * w.ldb * es);
+  w.partN = cv.take<float>((size_t)w.plan.S_c * n * w.plan.NV);
+  w.partT = cv.take<float>((size_t)w.plan.S_r * m * w.plan.NV);
+  w.bytes = cv.size();
+  return w;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nmf_status_string(nmf_status_t st) {
+  switch (st) {
+    case NMF_OK: return "ok";
+    case NMF_ERR_INVALID_ARG: return "invalid argument";
+    case NMF_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case NMF_ERR_CUDA: return "CUDA runtime error";
+    case NMF_ERR_NOT_SPD: return "Gram matrix not positive definite";
+    case NMF_ERR_NONFINITE: return "non-finite value";
+    case NMF_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
+    case NMF_ERR_UNSUPPORTED: return "unsupported device or configuration";
+  }
+  return "unknown status";
+}
+
+int nmf_version(void) { return 100; }
+
+nmf_status_t nmf_workspace_status(nmf_stream_t stream, const void* workspace, int* status) {
+  if (!workspace || !status) return NMF_ERR_INVALID_ARG;
+  int v = 0;
+  NMF_CU(cudaMemcpyAsync(&v, workspace, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  NMF_CU(cudaStreamSynchronize((cudaStream_t)stream));
+  *status = v;
+  return NMF_OK;
+}
+
+void nmf_set_kernel_path(int force_cuda_cores) { g_force_simt = force_cuda_cores ? 1 : 0; }
+
+nmf_status_t nmf_gaussian_sketch(nmf_stream_t stream, int rows, int cols, uint64_t seed, uint32_t stream_id,
+                                 float* out) {
+  if (rows < 0 || cols < 0 || (!out && rows * (long long)cols > 0)) return NMF_ERR_INVALID_ARG;
+  if (rows == 0 || cols == 0) return NMF_OK;
+  NMF_CU(sketch_launch(rows, cols, seed, stream_id, out, (cudaStream_t)stream));
+  return NMF_OK;
+}
+
+size_t nmf_compress_workspace_size(int n, int m, int nu, nmf_prec_t prec) {
+  if (n < 1 || m < 1 || nu < 1 || nu > NMF_MAX_SKETCH) return 0;
+  return carve_compress(nullptr, n, m, nu, prec).bytes;
+}
+
+nmf_status_t nmf_compress(nmf_stream_t stream, int n, int m, int nu, int q, nmf_prec_t prec, const float* X,
+                          const float* omega_L, const float* omega_R, uint64_t seed, float* L, float* R, float* XL,
+                          float* XR, void* workspace, size_t workspace_bytes) {
+  if (n < 1 || m < 1 || nu < 1 || nu > NMF_MAX_SKETCH || nu > n || nu > m || q < 0) return NMF_ERR_INVALID_ARG;
+  if (prec != NMF_PREC_FP32 && prec != NMF_PREC_BF16) return NMF_ERR_INVALID_ARG;
+  if (!X || !L || !R || !XL || !XR) return NMF_ERR_INVALID_ARG;
+  if ((omega_L == nullptr) != (omega_R == nullptr)) return NMF_ERR_INVALID_ARG;
+  const CompressWs w = carve_compress(workspace, n, m, nu, prec);
+  if (!ws_ok(workspace, workspace_bytes, w.bytes)) return NMF_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool bf16 = prec == NMF_PREC_BF16;
+  const size_t es = bf16 ? 2 : 4;
+  const int NV = w.plan.NV;
+
+  NMF_CU(cudaMemsetAsync(w.ctrl, 0, sizeof(Control), s));
+  NMF_CU(cudaMemsetAsync(w.opA, 0, (size_t)NV * w.lda * es, s));
+  NMF_CU(cudaMemsetAsync(w.opB, 0, (size_t)NV * w.ldb * es, s));
+  if (bf16) NMF_CU(to_bf16_launch(X, n, m, w.Xb, w.ldxb, w.ctrl, s));
+
+  // Omega_L (m x nu) -> opA rows (A^T), Omega_R (nu x n) -> opB rows (B^T = Omega_R).
+  const float* oL = omega_L;
+  if (!oL) {
+    NMF_CU(sketch_launch(m, nu, seed, 0u, w.omega, s));
+    oL = w.omega;
+  }
+  NMF_CU(transpose_launch(oL, m, nu, w.opA, w.lda, bf16, w.ctrl, s));
+  const float* oR = omega_R;
+  if (!oR) {
+    NMF_CU(sketch_launch(nu, n, seed, 1u, w.omega, s));
+    oR = w.omega;
+  }
+  NMF_CU(copy_rows_launch(oR, nu, n, w.opB, w.ldb, bf16, w.ctrl, s));
+
+  XPassArgs xa{};
+  xa.n = n;
+  xa.m = m;
+  xa.X = bf16 ? (const void*)w.Xb : (const void*)X;
+  xa.ldx = bf16 ? w.ldxb : m;
+  xa.opA = w.opA;
+  xa.lda = w.lda;
+  xa.opB = w.opB;
+  xa.ldb = w.ldb;
+  xa.partN = w.partN;
+  xa.partT = w.partT;
+  xa.nu = nu;
+  xa.doN = xa.doT = true;
+  xa.ctrl = w.ctrl;
+
+  const int passes = 2 * q + 2;
+  for (int pass = 0; pass < passes; ++pass) {
+    NMF_CU(xpass_launch(w.plan, xa, prec, s));
+    if (pass == passes - 1) {
+      // Final pass: X_R = X R (N product), X_L = (X^T L^T)^T (T product).
+      RowJob r[2] = {};
+      r[0].part = w.partN; r[0].S = w.plan.S_c; r[0].ldp = NV; r[0].N = n; r[0].nu = nu; r[0].Y = XR;
+      r[1].part = w.partT; r[1].S = w.plan.S_r; r[1].ldp = NV; r[1].N = m; r[1].nu = nu; r[1].Yt = XL;
+      NMF_CU(rows_launch(r, 2, w.ctrl, s));
+    } else {
+      const bool last = pass == passes - 2;
+      nmf_status_t st = orthonormalize(w, n, m, nu, bf16, last ? L : nullptr, last ? R : nullptr, s);
+      if (st != NMF_OK) return st;
+    }
+  }
+  return NMF_OK;
+}
+
+size_t nenmf_solve_workspace_size(const nenmf_problem_t* problem) {
+  if (!problem_ok(problem)) return 0;
+  return carve_solve(nullptr, *problem).bytes;
+}
+
+nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, float* G, float* F,
+                         const nenmf_params_t* params, nenmf_stats_t* stats, void* workspace, size_t workspace_bytes) {
+  if (!problem_ok(problem) || !params || !G || !F) return NMF_ERR_INVALID_ARG;
+  const nenmf_problem_t pr = *problem;
+  const nenmf_params_t pa = *params;
+  if (pa.max_outer < 0 || pa.max_inner < 1 || pa.max_inner > kMaxInner || pa.min_inner < 1) return NMF_ERR_INVALID_ARG;
+  if (pa.tol_mode != NENMF_TOL_REL && pa.tol_mode != NENMF_TOL_ABS) return NMF_ERR_INVALID_ARG;
+  const SolveWs w = carve_solve(workspace, pr);
+  if (!ws_ok(workspace, workspace_bytes, w.bytes)) return NMF_ERR_WORKSPACE;
+  const bool plain = pr.mode == NENMF_PLAIN;
+  const int n = pr.n, m = pr.m, p = pr.p, nu = plain ? 0 : pr.nu;
+  const bool test = pa.tol > 0.0;
+  const int epiG = plain ? EPI_GRAM : EPI_W_COLS;
+  const int epiF = plain ? EPI_GRAM : EPI_W_ROWS;
+  if (test && (w.ctasG > solve_max_coresident(p, nu, epiG) || w.ctasF > solve_max_coresident(p, nu, epiF)))
+    return NMF_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  Control* ctrl = w.ctrl;
+  const nmf_prec_t prec = (nmf_prec_t)pr.prec;
+  const bool bf16 = plain && prec == NMF_PREC_BF16;
+  unsigned long long* times = reinterpret_cast<unsigned long long*>(pa.record_time_ns);
+
+  NMF_CU(cudaMemsetAsync(ctrl, 0, sizeof(Control), s));
+  if (stats) NMF_CU(cudaMemsetAsync(stats, 0, sizeof(nenmf_stats_t), s));
+  if (times) {
+    NMF_CU(cudaMemsetAsync(times, 0, sizeof(long long) * ((size_t)pa.max_outer + 1), s));
+    NMF_CU(timestamp_launch(times, s));
+  }
+  NMF_CU(beta_launch(w.beta, pa.max_inner, s));
+  NMF_CU(transpose_launch(G, n, p, w.Gt, n, 0, ctrl, s));
+
+  XPassArgs xa{};
+  if (plain) {
+    const size_t es = bf16 ? 2 : 4;
+    NMF_CU(cudaMemsetAsync(w.opF, 0, (size_t)w.plan.NV * w.ldF * es, s));
+    NMF_CU(cudaMemsetAsync(w.opG, 0, (size_t)w.plan.NV * w.ldG * es, s));
+    if (bf16) NMF_CU(to_bf16_launch(pr.X, n, m, w.Xb, w.ldxb, ctrl, s));
+    xa.n = n;
+    xa.m = m;
+    xa.X = bf16 ? (const void*)w.Xb : (const void*)pr.X;
+    xa.ldx = bf16 ? w.ldxb : m;
+    xa.opA = w.opF;
+    xa.lda = w.ldF;
+    xa.opB = w.opG;
+    xa.ldb = w.ldG;
+    xa.partN = w.partN;
+    xa.partT = w.partT;
+    xa.nu = p;
+    xa.ctrl = ctrl;
+  }
+  XPassArgs xN = xa, xT = xa;
+  xN.doN = true; xN.doT = false;
+  xT.doN = false; xT.doT = true;
+
+  SolveArgs g{};
+  g.p = p; g.N = n; g.nu = nu; g.Y = w.Gt;
+  g.max_inner = pa.max_inner; g.min_inner = pa.min_inner; g.stop_test = test; g.side = 0;
+  g.pg2_init = w.initG; g.pg2_part = w.pg2G; g.stats = stats; g.ctrl = ctrl;
+  g.epi = epiG;
+  SolveArgs f = g;
+  f.N = m; f.Y = F; f.side = 1; f.pg2_init = w.initF; f.pg2_part = w.pg2F; f.epi = epiF;
+  if (plain) {
+    g.bsrc = B_FROM_PARTIALS; g.Bpart = w.partN; g.Bparts = w.plan.S_c; g.Bld = w.plan.NV;
+    g.Hpart = w.HG; g.Hparts = w.ctasF; g.Hpart_out = w.HF; g.op_out = w.opG; g.op_ld = w.ldG; g.op_bf16 = bf16;
+    f.bsrc = B_FROM_PARTIALS; f.Bpart = w.partT; f.Bparts = w.plan.S_r; f.Bld = w.plan.NV;
+    f.Hpart = w.HF; f.Hparts = w.ctasG; f.Hpart_out = w.HG; f.op_out = w.opF; f.op_ld = w.ldF; f.op_bf16 = bf16;
+  } else {
+    g.bsrc = B_FROM_ROWS; g.D = pr.XR; g.Wpart = w.WG; g.Wparts = w.ctasF; g.E = pr.L; g.Wpart_out = w.WF;
+    f.bsrc = B_FROM_COLS; f.D = pr.XL; f.Wpart = w.WF; f.Wparts = w.ctasG; f.E = pr.R; f.Wpart_out = w.WG;
+  }
+
+  // Products of the initial F for the first G update (and its operand copy).
+  {
+    SolveArgs f0 = f;
+    f0.stats = nullptr;
+    NMF_CU(solve_launch_mode(f0, w.beta, MODE_EPI_ONLY, s));
+  }
+  if (test) {
+    // eps from the projected gradients at (G0, F0) of the objective being solved.
+    if (plain) NMF_CU(xpass_launch(w.plan, xN, prec, s));
+    SolveArgs g0 = g;
+    g0.stats = nullptr;
+    NMF_CU(solve_launch_mode(g0, w.beta, MODE_EVAL, s));
+    if (plain) NMF_CU(xpass_launch(w.plan, xT, prec, s));
+    SolveArgs f0 = f;
+    f0.stats = nullptr;
+    f0.epi = EPI_NONE;
+    f0.op_out = nullptr;
+    NMF_CU(solve_launch_mode(f0, w.beta, MODE_EVAL, s));
+  }
+  NMF_CU(eps_launch(ctrl, w.initG, w.ctasG, w.initF, w.ctasF, pa.tol, pa.tol_mode, stats, s));
+
+  for (int t = 0; t < pa.max_outer; ++t) {
+    if (plain) NMF_CU(xpass_launch(w.plan, xN, prec, s));
+    SolveArgs gt = g;
+    if (pa.record_G) {
+      gt.record = pa.record_G + (size_t)t * n * p;
+      gt.record_transposed = 1;
+    }
+    NMF_CU(solve_launch_mode(gt, w.beta, MODE_SOLVE, s));
+    if (plain) NMF_CU(xpass_launch(w.plan, xT, prec, s));
+    SolveArgs ft = f;
+    if (pa.record_F) ft.record = pa.record_F + (size_t)t * p * m;
+    if (times) ft.time_out = times + t + 1;
+    NMF_CU(solve_launch_mode(ft, w.beta, MODE_SOLVE, s));
+  }
+  if (stats || pa.max_outer > 0)
+    NMF_CU(stats_launch(stats, pa.max_outer > 0 ? w.pg2G + 2 * w.ctasG : nullptr, w.ctasG,
+                        pa.max_outer > 0 ? w.pg2F + 2 * w.ctasF : nullptr, w.ctasF, ctrl, pa.max_outer, s));
+  NMF_CU(transpose_launch(w.Gt, p, n, G, p, 0, nullptr, s));
+  return NMF_OK;
+}
+
+size_t nmf_rre_workspace_size(int n, int m, int p) {
+  if (n < 1 || m < 1 || p < 1) return 0;
+  return round_up_sz((size_t)rre_parts(n, m) * 2 * sizeof(double), 256);
+}
+
+nmf_status_t nmf_rre(nmf_stream_t stream, int n, int m, int p, const float* X, const float* G, const float* F,
+                     double* out, void* workspace, size_t workspace_bytes) {
+  if (n < 1 || m < 1 || p < 1 || p > NMF_MAX_RANK || !X || !G || !F || !out) return NMF_ERR_INVALID_ARG;
+  if (!ws_ok(workspace, workspace_bytes, nmf_rre_workspace_size(n, m, p))) return NMF_ERR_WORKSPACE;
+  NMF_CU(rre_launch(n, m, p, X, G, F, out, static_cast<double*>(workspace), rre_parts(n, m), (cudaStream_t)stream));
+  return NMF_OK;
+}
+
+size_t nmf_dual_product_workspace_size(int n, int m, int k, nmf_prec_t prec) {
+  if (n < 1 || m < 1 || k < 1 || k > NMF_MAX_SKETCH) return 0;
+  return carve_dual(nullptr, n, m, k, prec).bytes;
+}
+
+nmf_status_t nmf_dual_product(nmf_stream_t stream, int n, int m, int k, nmf_prec_t prec, const float* X,
+                              const float* A, const float* B, float* YN, float* YT, void* workspace,
+                              size_t workspace_bytes) {
+  if (n < 1 || m < 1 || k < 1 || k > NMF_MAX_SKETCH || !X) return NMF_ERR_INVALID_ARG;
+  if (prec != NMF_PREC_FP32 && prec != NMF_PREC_BF16) return NMF_ERR_INVALID_ARG;
+  if ((A == nullptr) != (YN == nullptr) || (B == nullptr) != (YT == nullptr) || (!A && !B))
+    return NMF_ERR_INVALID_ARG;
+  const DualWs w = carve_dual(workspace, n, m, k, prec);
+  if (!ws_ok(workspace, workspace_bytes, w.bytes)) return NMF_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool bf16 = prec == NMF_PREC_BF16;
+  const size_t es = bf16 ? 2 : 4;
+  NMF_CU(cudaMemsetAsync(w.ctrl, 0, sizeof(Control), s));
+  NMF_CU(cudaMemsetAsync(w.opA, 0, (size_t)w.plan.NV * w.lda * es, s));
+  NMF_CU(cudaMemsetAsync(w.opB, 0, (size_t)w.plan.NV * w.ldb * es, s));
+  if (bf16) NMF_CU(to_bf16_launch(X, n, m, w.Xb, w.ldxb, w.ctrl, s));
+  if (A) NMF_CU(transpose_launch(A, m, k, w.opA, w.lda, bf16, w.ctrl, s));
+  if (B) NMF_CU(transpose_launch(B, n, k, w.opB, w.ldb, bf16, w.ctrl, s));
+  XPassArgs xa{};
+  xa.n = n; xa.m = m;
+  xa.X = bf16 ? (const void*)w.Xb : (const void*)X;
+  xa.ldx = bf16 ? w.ldxb : m;
+  xa.opA = w.opA; xa.lda = w.lda; xa.opB = w.opB; xa.ldb = w.ldb;
+  xa.partN = w.partN; xa.partT = w.partT; xa.nu = k;
+  xa.doN = A != nullptr; xa.doT = B != nullptr;
+  xa.ctrl = w.ctrl;
+  NMF_CU(xpass_launch(w.plan, xa, prec, s));
+  RowJob r[2] = {};
+  int nj = 0;
+  if (A) {
+    r[nj].part = w.partN; r[nj].S = w.plan.S_c; r[nj].ldp = w.plan.NV; r[nj].N = n; r[nj].nu = k; r[nj].Y = YN;
+    ++nj;
+  }
+  if (B) {
+    r[nj].part = w.partT; r[nj].S = w.plan.S_r; r[nj].ldp = w.plan.NV; r[nj].N = m; r[nj].nu = k; r[nj].Y = YT;
+    ++nj;
+  }
+  NMF_CU(rows_launch(r, nj, w.ctrl, s));
+  return NMF_OK;
+}
+
+}  // extern "C"

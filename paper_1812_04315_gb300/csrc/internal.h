@@ -1,0 +1,185 @@
+// internal.h -- launchers shared between libnmf translation units (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace nmf {
+
+// ---------------------------------------------------------------------------
+// Workspace carving: a bump allocator over the caller's workspace. With a
+// null base it only measures (used by the *_workspace_size queries).
+// ---------------------------------------------------------------------------
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = round_up_sz(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+  size_t size() const { return round_up_sz(off, 256); }
+};
+
+// ---------------------------------------------------------------------------
+// X passes: Y_N = X * A (n x nu) and Y_T = X^T * B (m x nu) in one read of X,
+// as per-region partial sums (deterministic split-K).
+// Operands are stored transposed and zero padded: opA is NV x lda holding
+// A^T (row c = column c of A), opB is NV x ldb holding B^T.
+// Partials: partN[S_c][n][NV], partT[S_r][m][NV] (float32).
+// ---------------------------------------------------------------------------
+struct XPassPlan {
+  int tile_r, tile_c;   // tile size in rows / columns of X
+  int tiles_r, tiles_c;
+  int S_r, S_c;         // region grid: S_r row groups x S_c column groups
+  int NV;               // padded operand / partial width
+  int ctas;
+};
+
+struct XPassArgs {
+  int n, m;
+  const void* X;        // float (prec FP32) or __nv_bfloat16 (prec BF16)
+  int ldx;              // elements
+  const void* opA;      // NV x lda, same element type as X
+  int lda;
+  const void* opB;      // NV x ldb
+  int ldb;
+  float* partN;         // may be null when !doN
+  float* partT;         // may be null when !doT
+  int nu;               // meaningful columns (<= NV)
+  bool doN, doT;
+  Control* ctrl;
+};
+
+// Plans (tile sizes, region grid) for a pass at the given width.
+XPassPlan xpass_plan(int n, int m, int nu, nmf_prec_t prec, int num_sms);
+cudaError_t xpass_launch(const XPassPlan& plan, const XPassArgs& a, nmf_prec_t prec, cudaStream_t s);
+// Float32 CUDA-core path for bfloat16 X (same rounding of inputs as the
+// tensor-core path, different summation order); used as an independent check.
+cudaError_t xpass_simt_launch(const XPassPlan& plan, const XPassArgs& a, bool bf16, cudaStream_t s);
+XPassPlan xpass_simt_plan(int n, int m, int nu, int num_sms);
+// Tensor-core (tcgen05) path for bfloat16 X.
+XPassPlan xpass_tc_plan(int n, int m, int nu, int num_sms);
+cudaError_t xpass_tc_launch(const XPassPlan& plan, const XPassArgs& a, cudaStream_t s);
+bool xpass_tc_available();
+
+// ---------------------------------------------------------------------------
+// Row kernels of the orthonormalisation (CholeskyQR with float-float Gram).
+// A "job" is one tall matrix of N rows and nu columns.
+// ---------------------------------------------------------------------------
+constexpr int kOrthRows = 128;  // rows per CTA in the row kernels
+
+struct RowJob {
+  // source: partial sums (part != null) or a dense N x nu matrix times Rinv
+  const float* part;    // S x N x ldp
+  int S, ldp;
+  const float* src;     // N x nu (used when part == null)
+  const float* rinv;    // nu x nu upper-triangular inverse (float), with src
+  int N, nu;
+  // outputs (each optional)
+  float* Y;             // N x nu row-major
+  float* Yt;            // nu x N row-major (transpose)
+  void* op;             // NV x ldop transposed operand (float or bf16)
+  int ldop, op_bf16;
+  float2* gram_part;    // [ctas][nu*(nu+1)/2] float-float partial Gram of the output rows
+  const int* gram_flag; // optional: compute gram_part only if *gram_flag != 0
+  const int* run_flag;  // optional: skip the job unless *run_flag != 0
+};
+
+struct CholJob {
+  const float2* gram_part;
+  int parts, nu;
+  float* rinv;          // out: nu x nu, inverse of the upper Cholesky factor
+  int* shift_flag;      // out: 1 when the shifted factorisation was needed
+  int reset_flag;       // 1: write 0/1 to *shift_flag; 0: only raise it
+  const int* run_flag;  // optional
+};
+
+cudaError_t rows_launch(const RowJob* jobs, int njobs, Control* ctrl, cudaStream_t s);
+cudaError_t chol_launch(const CholJob* jobs, int njobs, Control* ctrl, cudaStream_t s);
+inline int rows_ctas(int N) { return ceil_div(N, kOrthRows); }
+
+// ---------------------------------------------------------------------------
+// Nesterov inner solve (Sec. 2) over the columns of a p x N unknown.
+// ---------------------------------------------------------------------------
+enum BSource { B_FROM_ROWS = 0, B_FROM_COLS = 1, B_FROM_PARTIALS = 2 };
+enum Epilogue { EPI_NONE = 0, EPI_W_ROWS = 1, EPI_W_COLS = 2, EPI_GRAM = 3 };
+constexpr int kSolveThreads = 128;
+
+struct SolveArgs {
+  int p, N, nu;
+  float* Y;              // p x N, in/out (unchanged when max_inner == 0)
+  // H and B
+  int bsrc;              // BSource
+  const float* D;        // B_FROM_ROWS: N x nu; B_FROM_COLS: nu x N
+  const float* Wpart;    // [Wparts][p][nu] partials of W (compressed modes)
+  int Wparts;
+  const float* Bpart;    // B_FROM_PARTIALS: [Bparts][N][Bld]
+  int Bparts, Bld;
+  const float* Hpart;    // B_FROM_PARTIALS: [Hparts][p][p]
+  int Hparts;
+  // iteration
+  int max_inner, min_inner;
+  bool stop_test;        // needs cooperative launch
+  int side;              // 0 = G, 1 = F (stats slot)
+  double* pg2_init;      // when max_inner == 0: per-CTA ||P grad(Y0)||^2 partials
+  double* pg2_part;      // [2][ctas] per-iteration partials (stop test) and [ctas] final
+  // epilogue
+  int epi;               // Epilogue
+  const float* E;        // EPI_W_ROWS: N x nu; EPI_W_COLS: nu x N
+  float* Wpart_out;      // [ctas][p][nu]
+  float* Hpart_out;      // [ctas][p][p]
+  void* op_out;          // optional transposed operand NV x op_ld (float or bf16)
+  int op_ld, op_bf16;
+  float* record;         // optional snapshot: Y^T as N x p (G) or Y as p x N (F)
+  int record_transposed;
+  unsigned long long* time_out;  // optional: atomicMax of %globaltimer at exit
+  nenmf_stats_t* stats;  // optional
+  Control* ctrl;
+};
+
+enum SolveMode { MODE_EPI_ONLY = 0, MODE_EVAL = 1, MODE_SOLVE = 2 };
+int solve_ctas(int N);
+// MODE_EPI_ONLY: only the epilogue on Y as given; MODE_EVAL: prologue, the
+// projected-gradient norm of Y0 into pg2_init, then the epilogue on Y0;
+// MODE_SOLVE: the inner loop. `beta` holds beta_k for k < max_inner.
+cudaError_t solve_launch_mode(const SolveArgs& a, const float* beta, int mode, cudaStream_t s);
+cudaError_t beta_launch(float* beta, int K, cudaStream_t s);
+// CTAs that can be co-resident for the solve kernel (cooperative launches).
+int solve_max_coresident(int p, int nu, int epi);
+// Sums final per-CTA partials into the stats struct (one thread).
+cudaError_t stats_launch(nenmf_stats_t* stats, const double* pg2_final_G, int ctasG,
+                         const double* pg2_final_F, int ctasF, Control* ctrl, int outer, cudaStream_t s);
+// eps2 = tol^2 * (sum of init partials) (REL) or tol^2 (ABS), or -1 when off.
+cudaError_t eps_launch(Control* ctrl, const double* pg2_G, int ctasG, const double* pg2_F, int ctasF,
+                       double tol, int tol_mode, nenmf_stats_t* stats, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Auxiliary kernels.
+// ---------------------------------------------------------------------------
+cudaError_t sketch_launch(int rows, int cols, uint64_t seed, uint32_t stream_id, float* out, cudaStream_t s);
+// X (n x m float, ld m) -> Xb (n x ldb bfloat16), padding columns zero.
+cudaError_t to_bf16_launch(const float* X, int n, int m, __nv_bfloat16* Xb, int ldb, Control* ctrl,
+                           cudaStream_t s);
+// out[c][r] = in[r][c] for an R x C float matrix; `out` has leading dim ldo and
+// element type float or bf16. Padding (rows >= C, cols >= R) is untouched.
+cudaError_t transpose_launch(const float* in, int R, int C, void* out, int ldo, int out_bf16, Control* ctrl,
+                             cudaStream_t s);
+// Copies a rows x cols float matrix into a float or bf16 matrix with leading dim ldo.
+cudaError_t copy_rows_launch(const float* in, int rows, int cols, void* out, int ldo, int out_bf16,
+                             Control* ctrl, cudaStream_t s);
+cudaError_t timestamp_launch(unsigned long long* t, cudaStream_t s);
+cudaError_t rre_launch(int n, int m, int p, const float* X, const float* G, const float* F, double* out,
+                       double* part, int parts, cudaStream_t s);
+int rre_parts(int n, int m);
+
+int device_sm_count();
+bool device_is_sm103();
+
+}  // namespace nmf

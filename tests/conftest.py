@@ -25,3 +25,14 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def nmf():
+    """The built binding (builds libnmf.so in-tree when it is missing)."""
+    import paper_1812_04315_gb300 as pkg
+    if not os.path.exists(pkg.LIB_PATH):
+        from paper_1812_04315_gb300 import build
+        build.build()
+    pkg.lib()
+    return pkg

@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, every
+function declared in include/*.h is exported, size queries and argument
+validation answer before any device work is enqueued."""
+
+import ctypes
+import glob
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b((?:nmf|nenmf)_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def L():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    import paper_1812_04315_gb300 as pkg
+    if not os.path.exists(pkg.LIB_PATH):
+        from paper_1812_04315_gb300 import build
+        build.build()
+    return pkg.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared_functions()
+    assert {"nmf_compress", "nenmf_solve", "nmf_rre", "nmf_gaussian_sketch"} <= set(names)
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in include/ but not exported"
+    import paper_1812_04315_gb300 as pkg
+    assert set(pkg.exported_symbols()) <= set(names)
+
+
+def test_version_and_status_strings(L):
+    assert L.nmf_version() == 100
+    for code in range(8):
+        assert L.nmf_status_string(code)
+
+
+def test_workspace_queries(L):
+    assert L.nmf_compress_workspace_size(1000, 800, 20, 1) > 1000 * 800 * 2
+    assert L.nmf_compress_workspace_size(0, 800, 20, 1) == 0
+    assert L.nmf_compress_workspace_size(10, 10, 65, 0) == 0
+    assert L.nmf_rre_workspace_size(100, 100, 5) > 0
+    import paper_1812_04315_gb300 as pkg
+    pr = pkg._problem(pkg.COMPRESSED, 100, 90, 4, 8, 0)
+    pr.L = pr.R = pr.XL = pr.XR = 256
+    assert pkg.solve_workspace_size(pr) > 0
+    pr.nu = 2  # nu < p
+    assert pkg.solve_workspace_size(pr) == 0
+
+
+def test_argument_errors_are_host_side(L):
+    # Invalid sizes and null pointers are rejected before any CUDA call.
+    v = ctypes.c_void_p
+    assert L.nmf_compress(None, 0, 10, 4, 1, 1, v(256), None, None, 0, v(256), v(256), v(256), v(256), v(256), 1 << 30) == 1
+    assert L.nmf_compress(None, 10, 10, 4, 1, 1, None, None, None, 0, v(256), v(256), v(256), v(256), v(256), 1 << 30) == 1
+    assert L.nmf_compress(None, 10, 10, 11, 1, 1, v(256), None, None, 0, v(256), v(256), v(256), v(256), v(256), 1 << 30) == 1
+    # one sketch given without the other
+    assert L.nmf_compress(None, 10, 10, 4, 1, 1, v(256), v(256), None, 0, v(256), v(256), v(256), v(256), v(256), 1 << 30) == 1
+    # misaligned / too small workspace
+    assert L.nmf_compress(None, 10, 10, 4, 1, 0, v(256), None, None, 0, v(256), v(256), v(256), v(256), v(100), 1 << 30) == 2
+    assert L.nmf_compress(None, 10, 10, 4, 1, 0, v(256), None, None, 0, v(256), v(256), v(256), v(256), v(256), 16) == 2
+    assert L.nenmf_solve(None, None, None, None, None, None, None, 0) == 1
+    assert L.nmf_rre(None, 10, 10, 0, v(256), v(256), v(256), v(256), v(256), 1 << 20) == 1
+    assert L.nmf_dual_product(None, 10, 10, 4, 0, v(256), None, None, None, None, v(256), 1 << 30) == 1

@@ -1,0 +1,114 @@
+"""GPU parity of nmf_compress (Alg. 2 + X_L, X_R of Alg. 1) against the FP64 oracle.
+
+Both sides get the same Gaussian sketches (host-drawn, or the library's own
+Philox draw reproduced by the oracle). What is compared:
+* orthonormality of L (rows) and R (columns);
+* the leading p basis vectors entrywise (they depend only on well-conditioned
+  leading columns of the sketch products), and the whole subspace through the
+  largest principal angle to the oracle's;
+* X_L = L X and X_R = X R against float64 products of the library's own L, R;
+* exact recovery on exactly low-rank X (nu >= rank X): X = L^T L X = X R R^T.
+Tolerances: float32 path 2^-24-scale errors amplified by the conditioning of
+the sketch products (kept below 1e2 here); the bfloat16 path rounds X and the
+bases to 8 significant bits (relative 2^-9), so its subspace agrees to ~1e-2.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import philox, subspace
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def _np(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _max_angle(Q1, Q2):
+    """sin of the largest principal angle between the column spans of Q1 and Q2 (orthonormal)."""
+    return np.linalg.norm(Q1 - Q2 @ (Q2.T @ Q1), 2)
+
+
+CASES = [
+    # n, m, p, nu, q, snr
+    (300, 257, 5, 12, 2, 30.0),
+    (257, 300, 4, 9, 4, 30.0),
+    (640, 384, 10, 20, 4, 30.0),
+    (130, 70, 1, 1, 1, 20.0),
+    (200, 190, 6, 64, 1, 40.0),
+]
+
+
+@pytest.mark.parametrize("n,m,p,nu,q,snr", CASES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_compress_matches_oracle(nmf, n, m, p, nu, q, snr, prec):
+    X, _, _ = synth.lowrank_data(n, m, p, seed=n + m, snr_db=snr, dtype=np.float32)
+    OmL, OmR = synth.gaussian_sketches(n, m, nu, seed=7)
+    OmL, OmR = OmL.astype(np.float32), OmR.astype(np.float32)
+    L, R, XL, XR = (_np(t) for t in nmf.compress(_t(X), nu, q, prec=prec, omega_L=_t(OmL), omega_R=_t(OmR)))
+    Xd = X.astype(np.float64)
+    Lo, Ro, XLo, XRo = subspace.compress(Xd, nu, q, OmL.astype(np.float64), OmR.astype(np.float64))
+    orth_tol = 2e-5 if prec == 0 else 2e-5
+    np.testing.assert_allclose(L @ L.T, np.eye(nu), atol=orth_tol)
+    np.testing.assert_allclose(R.T @ R, np.eye(nu), atol=orth_tol)
+    # subspaces
+    ang_tol = 1e-3 if prec == 0 else 5e-2
+    assert _max_angle(L.T[:, :p], Lo.T) < ang_tol
+    assert _max_angle(R[:, :p], Ro) < ang_tol
+    # leading basis vectors entrywise
+    lead_tol = 2e-4 if prec == 0 else 3e-2
+    np.testing.assert_allclose(L[:p], Lo[:p], atol=lead_tol * np.abs(Lo[:p]).max())
+    np.testing.assert_allclose(R[:, :p], Ro[:, :p], atol=lead_tol * np.abs(Ro[:, :p]).max())
+    # the final pass against float64 products of the library's own bases
+    if prec == 0:
+        np.testing.assert_allclose(XL, L @ Xd, atol=4 * np.sqrt(m) * 2**-24 * (np.abs(L) @ np.abs(Xd)).max())
+        np.testing.assert_allclose(XR, Xd @ R, atol=4 * np.sqrt(m) * 2**-24 * (np.abs(Xd) @ np.abs(R)).max())
+    else:
+        Xb = X.astype(np.float64)
+        rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel(XL, L @ Xb) < 1e-2 and rel(XR, Xb @ R) < 1e-2
+    # captured energy agrees with the oracle's
+    e_gpu = np.linalg.norm(XL) / np.linalg.norm(Xd)
+    e_ora = np.linalg.norm(XLo) / np.linalg.norm(Xd)
+    assert abs(e_gpu - e_ora) < (1e-6 if prec == 0 else 1e-3)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_exact_low_rank_projectors(nmf, prec):
+    n, m, p, nu, q = 333, 222, 6, 10, 2
+    X, _, _ = synth.lowrank_data(n, m, p, seed=3, dtype=np.float32)
+    L, R, XL, XR = (_np(t) for t in nmf.compress(_t(X), nu, q, prec=prec, seed=11))
+    Xd = X.astype(np.float64)
+    tol = 1e-5 if prec == 0 else 1e-2
+    nx = np.linalg.norm(Xd)
+    assert np.linalg.norm(Xd - L.T @ (L @ Xd)) / nx < tol
+    assert np.linalg.norm(Xd - (Xd @ R) @ R.T) / nx < tol
+    np.testing.assert_allclose(L @ L.T, np.eye(nu), atol=1e-4)
+    np.testing.assert_allclose(R.T @ R, np.eye(nu), atol=1e-4)
+
+
+def test_internal_sketch_is_the_oracle_sketch(nmf):
+    # With no sketch passed, the library draws Omega_L, Omega_R from the seed;
+    # the oracle's Philox reproduces them, so the two compressions agree.
+    n, m, p, nu, q, seed = 200, 150, 4, 8, 1, 2**33 + 5
+    X, _, _ = synth.lowrank_data(n, m, p, seed=9, snr_db=30.0, dtype=np.float32)
+    L, R, XL, XR = (_np(t) for t in nmf.compress(_t(X), nu, q, prec=0, seed=seed))
+    OmL, OmR = philox.sketches(n, m, nu, seed)
+    Lo, Ro, _, _ = subspace.compress(X.astype(np.float64), nu, q, OmL.astype(np.float32).astype(np.float64),
+                                     OmR.astype(np.float32).astype(np.float64))
+    np.testing.assert_allclose(L[:p], Lo[:p], atol=2e-4 * np.abs(Lo[:p]).max())
+
+
+def test_compress_deterministic(nmf):
+    X, _, _ = synth.lowrank_data(500, 400, 5, seed=1, snr_db=30.0, dtype=np.float32)
+    a = [_np(t) for t in nmf.compress(_t(X), 15, 3, prec=1, seed=4)]
+    b = [_np(t) for t in nmf.compress(_t(X), 15, 3, prec=1, seed=4)]
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
