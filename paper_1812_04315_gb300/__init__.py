@@ -182,6 +182,8 @@ def compress(X, nu: int, q: int, prec: int = PREC_BF16, omega_L=None, omega_R=No
 
 def _problem(mode, n, m, p, nu=0, prec=PREC_FP32, X=None, L=None, R=None, XL=None, XR=None):
     pr = Problem()
+    # The struct holds raw device pointers: keep the tensors alive with it.
+    pr._tensors = (X, L, R, XL, XR)
     pr.mode, pr.n, pr.m, pr.p, pr.nu, pr.prec = mode, n, m, p, nu, prec
     pr.X = X.data_ptr() if X is not None else None
     pr.L = L.data_ptr() if L is not None else None
