@@ -1,0 +1,456 @@
+#!/usr/bin/env python3
+"""Benchmark of the compressed-NeNMF hot path on GB300.
+
+One step = the whole path on one synthetic problem, through the C ABI:
+  nmf_compress  (Alg. 2: Gaussian sketches, 2q+2 passes over X, CholeskyQR2
+                 bases, then X_L = L X and X_R = X R), bfloat16 X products
+  nenmf_solve   (Alg. 1: 100 outer iterations, <= 10 Nesterov inner
+                 iterations per factor, projected-gradient stop test 1e-6)
+on the workload n = m = 10^4, p = 10, nu = 20, q = 4, X = G0 F0 + nonnegative
+noise at 30 dB (G0, F0, initial G, F iid Uniform[0, 1], seeded).
+
+value   = outer iterations per second of the whole step (compression
+          included), summed over ranks (each rank solves its own replica).
+e2e     = the same with X and the initial factors copied from pinned host
+          memory and the factors copied back inside the timed region.
+Also reported: time to a relative reconstruction error for compressed versus
+plain NeNMF on the same GPU, the roofline of the dominant kernel, the FP64
+CPU oracle timed on the host (`cpu_baseline`).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import datetime
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-rel-error & outer iters/s: compressed vs plain NeNMF, 1 GB300"
+UNIT = "outer_iter/s"
+WORKLOAD = dict(n=10000, m=10000, p=10, nu=20, q=4, snr_db=30.0, max_outer=100, max_inner=10, tol=1e-6,
+                data_seed=0, init_seed=1, sketch_seed=2)
+WORKLOAD_NAME = ("compressed NeNMF, n=m=10000, p=10, nu=20, q=4, 30 dB, 100 outer x <=10 inner, "
+                 "bf16 compression GEMMs, fp32 inner loop")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--no-rre", action="store_true", help="skip the time-to-RRE runs")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# multi-process plumbing (one process per GPU, launched by torch.distributed.run)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def dist_init(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """Max of a float over all ranks (identity on one rank)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed divided by the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+_CLOCK_FIELDS = ["timestamp", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+                 "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+                 "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.proc = None
+        self.window = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={index}", "--query-gpu=" + ",".join(_CLOCK_FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def mark(self, t0: datetime.datetime, t1: datetime.datetime):
+        self.window = (t0, t1)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        return summarize_clocks(out, self.window)
+
+
+def summarize_clocks(out: str, window=None):
+    """Median SM clock, max clock and active throttle reasons from nvidia-smi CSV rows.
+
+    Rows inside `window` (a pair of datetimes) are used when there are any,
+    otherwise all rows.
+    """
+    rows = []
+    for line in out.splitlines():
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) != len(_CLOCK_FIELDS):
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+            rows.append((ts, float(parts[1]), float(parts[2]), parts[5:]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    inside = [r for r in rows if window and window[0] <= r[0] <= window[1]]
+    use = inside if inside else rows
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in use for i, v in enumerate(r[3]) if v.lower() == "active"})
+    return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+            "reasons": reasons, "samples": len(use), "samples_in_window": len(inside)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_inputs(rank: int = 0):
+    import synth
+    w = WORKLOAD
+    X, _, _ = synth.lowrank_data(w["n"], w["m"], w["p"], seed=w["data_seed"] + 1000 * rank, snr_db=w["snr_db"],
+                                 dtype=np.float32)
+    G0, F0 = synth.initial_factors(w["n"], w["m"], w["p"], seed=w["init_seed"] + 1000 * rank)
+    return X, G0.astype(np.float32), F0.astype(np.float32)
+
+
+def solve_kernel_bytes(n, m, p, nu):
+    """Algorithmic bytes of one fused inner-solve launch (mean of the G and F sides).
+
+    Per column (the unit): the factor column read and written (2p floats), its
+    compressed data vector (nu floats: a row of X_R or a column of X_L) and
+    its basis vector (nu floats: a column of L or a row of R), all float32.
+    """
+    return 4.0 * (2 * p + 2 * nu) * (n + m) / 2.0
+
+
+def xpass_bytes(n, m, nu, elem=2):
+    """Algorithmic bytes of one pass: X once, the two operands and the two outputs."""
+    return elem * n * m + elem * nu * (n + m) + 4 * nu * (n + m)
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import paper_1812_04315_gb300 as nmf
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = dist_init(world, "nccl")
+    dev = torch.device("cuda", local_rank)
+    w = WORKLOAD
+    n, m, p, nu, q, T, K_in, tol = w["n"], w["m"], w["p"], w["nu"], w["q"], w["max_outer"], w["max_inner"], w["tol"]
+    X, G0, F0 = make_inputs(rank)
+    Xg = torch.from_numpy(X).to(dev)
+    G0g, F0g = torch.from_numpy(G0).to(dev), torch.from_numpy(F0).to(dev)
+    G, F = G0g.clone(), F0g.clone()
+    prec = nmf.PREC_BF16
+    ws_c = nmf.workspace(nmf.compress_workspace_size(n, m, nu, prec))
+    out = tuple(torch.empty(s, dtype=torch.float32, device=dev) for s in [(nu, n), (m, nu), (nu, m), (n, nu)])
+    prob = nmf.compressed_problem(*out, p)
+    ws_s = nmf.workspace(nmf.solve_workspace_size(prob))
+    stats = torch.zeros(256, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        nmf.compress(Xg, nu, q, prec=prec, seed=w["sketch_seed"], ws=ws_c, out=out)
+        if ev is not None:
+            ev[1].record(stream)
+        G.copy_(G0g)
+        F.copy_(F0g)
+        nmf.solve(prob, G, F, T, K_in, tol=tol, stats=stats, ws=ws_s)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = nmf.read_stats(stats)
+    if st.status != 0:
+        raise RuntimeError(f"device status {st.status} in the warm-up")
+
+    sampler = ClockSampler(local_rank)
+    time.sleep(0.3)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = nmf.kernel_launches()
+    barrier(dist, local_rank)
+    torch.cuda.synchronize()
+    t0 = datetime.datetime.now()
+    e_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    t1 = datetime.datetime.now()
+    barrier(dist, local_rank)
+    launches = nmf.kernel_launches() - launches0
+    sampler.mark(t0, t1)
+    time.sleep(0.2)
+    clocks = sampler.stop()
+    ms_total = e_start.elapsed_time(e_end)
+    ms_step = max_over_ranks(dist, ms_total / args.steps, dev)
+    ms_compress = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    ms_solve = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    value = aggregate_value(T, world, ms_step / 1e3)
+
+    # ---- end to end: host buffers, copies inside the timed region ----
+    Xh = torch.from_numpy(X).pin_memory()
+    G0h, F0h = torch.from_numpy(G0).pin_memory(), torch.from_numpy(F0).pin_memory()
+    Gh, Fh = torch.empty_like(G0h).pin_memory(), torch.empty_like(F0h).pin_memory()
+
+    def e2e_step():
+        Xg.copy_(Xh, non_blocking=True)
+        G.copy_(G0h, non_blocking=True)
+        F.copy_(F0h, non_blocking=True)
+        nmf.compress(Xg, nu, q, prec=prec, seed=w["sketch_seed"], ws=ws_c, out=out)
+        nmf.solve(prob, G, F, T, K_in, tol=tol, stats=stats, ws=ws_s)
+        Gh.copy_(G, non_blocking=True)
+        Fh.copy_(F, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(dist, local_rank)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(dist, a.elapsed_time(b) / args.steps, dev)
+    barrier(dist, local_rank)
+    h2d = X.nbytes + G0.nbytes + F0.nbytes
+    d2h = G0.nbytes + F0.nbytes
+
+    # ---- roofline of the dominant kernel: the fused inner solve ----
+    # nenmf_solve = a few set-up launches + 2T solve launches; the per-launch
+    # time is the live-timed solve call divided by its 2T solve launches.
+    solve_launch_ms = ms_solve / (2 * T)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sbytes = solve_kernel_bytes(n, m, p, nu)
+    achieved = sbytes / (solve_launch_ms / 1e3) / 1e9
+    roofline = {"kernel": "solve_kernel (fused Nesterov inner loop, Sec. 2 / Alg. 1)", "bound": "hbm",
+                "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 5), "traffic": profile_traffic("solve_kernel"),
+                "algorithmic_bytes_per_launch": sbytes, "launch_ms": round(solve_launch_ms, 5),
+                "peak_source": peak_src}
+
+    result = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+              "data": "synthetic (seeded low-rank nonnegative + 30 dB noise; random init)",
+              "config": {"workload": WORKLOAD_NAME, "n": n, "m": m, "p": p, "nu": nu, "q": q,
+                         "max_outer": T, "max_inner": K_in, "tol": tol, "parallelism": "replicas",
+                         "l2": "inputs larger than L2 (X is 400 MB float32, read 2q+2 times per step)"},
+              "breakdown_ms": {"compress": round(ms_compress, 4), "solve": round(ms_solve, 4)},
+              "clocks": clocks, "gpu_launches": launches,
+              "e2e": {"value": round(aggregate_value(T, world, ms_e2e / 1e3), 3), "unit": UNIT,
+                      "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+              "roofline": roofline}
+
+    if not args.no_rre and rank == 0:
+        result["time_to_rre"] = time_to_rre(nmf, Xg, G0g, F0g, dev)
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        result["cpu_baseline"] = cpu_baseline(X, G0, F0)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def profile_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+    except (OSError, ValueError, KeyError):
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_1812_04315_gb300", "csrc", rec["source"])
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["dram_bytes_per_launch"] if digest == rec.get("source_sha256_16") else None
+
+
+def time_to_rre(nmf, Xg, G0g, F0g, dev):
+    """RRE-versus-time curves of compressed and plain NeNMF (bf16 X products) on the GPU."""
+    import torch
+    w = WORKLOAD
+    n, m, p, nu, q, T, K_in, tol = w["n"], w["m"], w["p"], w["nu"], w["q"], w["max_outer"], w["max_inner"], w["tol"]
+    stream = torch.cuda.current_stream()
+    rec = nmf.SolveRecord(G=torch.empty((T, n, p), device=dev), F=torch.empty((T, p, m), device=dev),
+                          times=torch.zeros(T + 1, dtype=torch.int64, device=dev))
+
+    def rre_curve():
+        terms = [nmf.rre_terms(Xg, rec.G[t], rec.F[t]) for t in range(T)]
+        torch.cuda.synchronize()
+        return np.array([float((x[0] / x[1]).sqrt()) for x in (t.cpu() for t in terms)])
+
+    # compressed: compression time + solve time stamps
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    L, R, XL, XR = nmf.compress(Xg, nu, q, prec=nmf.PREC_BF16, seed=w["sketch_seed"])
+    b.record(stream)
+    G, F = G0g.clone(), F0g.clone()
+    nmf.solve(nmf.compressed_problem(L, R, XL, XR, p), G, F, T, K_in, tol=tol, record=rec)
+    torch.cuda.synchronize()
+    t_comp = a.elapsed_time(b) / 1e3
+    ts = rec.times.cpu().numpy().astype(np.float64)
+    t_c = t_comp + (ts[1:] - ts[0]) / 1e9
+    r_c = rre_curve()
+    # plain, same precision policy for the X products
+    G, F = G0g.clone(), F0g.clone()
+    nmf.solve(nmf.plain_problem(Xg, p, nmf.PREC_BF16), G, F, T, K_in, tol=tol, record=rec)
+    torch.cuda.synchronize()
+    ts = rec.times.cpu().numpy().astype(np.float64)
+    t_p = (ts[1:] - ts[0]) / 1e9
+    r_p = rre_curve()
+    tau = (1 + 1e-3) * max(r_c[-1], r_p[-1])
+
+    def first(t, r):
+        idx = np.nonzero(r <= tau)[0]
+        return (float(t[idx[0]]), int(idx[0]) + 1) if idx.size else (None, None)
+
+    tc, kc = first(t_c, r_c)
+    tp, kp = first(t_p, r_p)
+    return {"tau": tau, "rre_final": {"compressed": float(r_c[-1]), "plain": float(r_p[-1])},
+            "compressed": {"seconds": tc, "outer_iters": kc, "compress_s": t_comp,
+                           "outer_iters_per_s": T / t_c[-1]},
+            "plain": {"seconds": tp, "outer_iters": kp, "outer_iters_per_s": T / t_p[-1]},
+            "speedup": (tp / tc) if (tc and tp) else None,
+            "definition": "tau = (1 + 1e-3) * max(final RRE of the two runs); time from the start of the "
+                          "compression (compressed) or of the solve (plain) to the first outer iteration "
+                          "with RRE <= tau; device time"}
+
+
+# ---------------------------------------------------------------------------
+# the FP64 CPU oracle: cpu_baseline leg and the reference arm
+# ---------------------------------------------------------------------------
+
+def oracle_step(X64, G0, F0, T=None):
+    """One step of the oracle on the host: Alg. 2 then Alg. 1, same sketch seed as the GPU."""
+    from oracle import nenmf, philox, subspace
+    w = WORKLOAD
+    T = w["max_outer"] if T is None else T
+    OmL, OmR = philox.sketches(w["n"], w["m"], w["nu"], w["sketch_seed"])
+    L, R, XL, XR = subspace.compress(X64, w["nu"], w["q"], OmL, OmR)
+    nenmf.nenmf_compressed(L, R, XL, XR, G0, F0, T, w["max_inner"], tol=w["tol"])
+
+
+def cpu_baseline(X, G0, F0):
+    X64 = X.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle_step(X64, G0, F0)
+    dt = time.perf_counter() - t0
+    return {"value": round(WORKLOAD["max_outer"] / dt, 4), "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle", "seconds": round(dt, 3),
+            "sample": "one full step on the host (numpy float64, all cores): Alg. 2 compression plus "
+                      f"{WORKLOAD['max_outer']} outer iterations of Alg. 1 on the same workload"}
+
+
+def run_reference(args):
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return
+    X, G0, F0 = make_inputs(0)
+    X64 = X.astype(np.float64)
+    for _ in range(args.warmup):
+        oracle_step(X64, G0, F0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(X64, G0, F0)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = WORKLOAD["max_outer"] / dt
+    sample = (f"each step: Alg. 2 compression plus {WORKLOAD['max_outer']} outer iterations of Alg. 1 "
+              "(numpy float64 oracle, all host cores) on the full workload")
+    print(json.dumps({"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2),
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "impl": "reference",
+                      "config": {"workload": WORKLOAD_NAME, "parallelism": "host cores"},
+                      "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(),
+                                       "kind": "oracle", "sample": sample},
+                      "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

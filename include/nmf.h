@@ -193,6 +193,13 @@ nmf_status_t nmf_dual_product(nmf_stream_t stream, int n, int m, int k, nmf_prec
  */
 void nmf_set_kernel_path(int force_cuda_cores);
 
+/*
+ * Number of kernel launches this library has enqueued in the process so far
+ * (all calls, all threads; memsets and copies are not counted). Benchmarks
+ * take the difference around a timed region.
+ */
+long long nmf_kernel_launches(void);
+
 /* ------------------------------------------------------------------------ */
 /* Relative reconstruction error, eq. (4)                                     */
 /* ------------------------------------------------------------------------ */

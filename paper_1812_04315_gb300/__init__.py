@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
         "nmf_dual_product_workspace_size": (sz, [i, i, i, i]),
         "nmf_dual_product": (i, [vp, i, i, i, i, vp, vp, vp, vp, vp, vp, sz]),
         "nmf_set_kernel_path": (None, [i]),
+        "nmf_kernel_launches": (ctypes.c_longlong, []),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -92,7 +93,7 @@ def exported_symbols():
     return ["nmf_status_string", "nmf_version", "nmf_workspace_status", "nmf_gaussian_sketch",
             "nmf_compress_workspace_size", "nmf_compress", "nenmf_solve_workspace_size", "nenmf_solve",
             "nmf_rre_workspace_size", "nmf_rre", "nmf_dual_product_workspace_size", "nmf_dual_product",
-            "nmf_set_kernel_path"]
+            "nmf_set_kernel_path", "nmf_kernel_launches"]
 
 
 # ---------------------------------------------------------------------------
@@ -135,6 +136,10 @@ def workspace_status(ws) -> int:
     v = ctypes.c_int(0)
     _ok(lib().nmf_workspace_status(_stream(), _ptr(ws), ctypes.byref(v)), "nmf_workspace_status")
     return v.value
+
+
+def kernel_launches() -> int:
+    return int(lib().nmf_kernel_launches())
 
 
 def set_kernel_path(force_cuda_cores: bool):

@@ -187,12 +187,14 @@ int grid_for(long long work, int threads) {
 
 cudaError_t sketch_launch(int rows, int cols, uint64_t seed, uint32_t stream_id, float* out, cudaStream_t s) {
   const long long groups = ((long long)rows * cols + 3) / 4;
+  count_launches(1);
   sketch_kernel<<<grid_for(groups, 256), 256, 0, s>>>(rows, cols, seed, stream_id, out);
   return cudaGetLastError();
 }
 
 cudaError_t to_bf16_launch(const float* X, int n, int m, __nv_bfloat16* Xb, int ldb, Control* ctrl, cudaStream_t s) {
   const long long pairs = (long long)n * ldb / 2;
+  count_launches(1);
   to_bf16_kernel<<<grid_for(pairs, 256), 256, 0, s>>>(X, n, m, Xb, ldb, ctrl);
   return cudaGetLastError();
 }
@@ -200,17 +202,20 @@ cudaError_t to_bf16_launch(const float* X, int n, int m, __nv_bfloat16* Xb, int 
 cudaError_t transpose_launch(const float* in, int R, int C, void* out, int ldo, int out_bf16, Control* ctrl,
                              cudaStream_t s) {
   dim3 grid(ceil_div(C, 32), ceil_div(R, 32));
+  count_launches(1);
   transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(in, R, C, out, ldo, out_bf16, ctrl);
   return cudaGetLastError();
 }
 
 cudaError_t copy_rows_launch(const float* in, int rows, int cols, void* out, int ldo, int out_bf16, Control* ctrl,
                              cudaStream_t s) {
+  count_launches(1);
   copy_rows_kernel<<<grid_for((long long)rows * cols, 256), 256, 0, s>>>(in, rows, cols, out, ldo, out_bf16, ctrl);
   return cudaGetLastError();
 }
 
 cudaError_t timestamp_launch(unsigned long long* t, cudaStream_t s) {
+  count_launches(1);
   timestamp_kernel<<<1, 32, 0, s>>>(t);
   return cudaGetLastError();
 }
@@ -220,9 +225,11 @@ int rre_parts(int n, int m) { return ceil_div(m, kRreThreads) * ceil_div(n, kRre
 cudaError_t rre_launch(int n, int m, int p, const float* X, const float* G, const float* F, double* out, double* part,
                        int parts, cudaStream_t s) {
   dim3 grid(ceil_div(m, kRreThreads), ceil_div(n, kRreRows));
+  count_launches(1);
   rre_kernel<<<grid, kRreThreads, 0, s>>>(n, m, p, X, G, F, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  count_launches(1);
   rre_final_kernel<<<1, 1024, 0, s>>>(part, parts, out);
   return cudaGetLastError();
 }

@@ -1,6 +1,7 @@
 // capi.cu -- the extern "C" entry points of include/nmf.h: argument checks,
 // workspace carving and the stream-ordered schedules of Alg. 2 (nmf_compress)
 // and of Alg. 1 / plain NeNMF (nenmf_solve).
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -34,6 +35,9 @@ bool use_tc(nmf_prec_t prec) { return prec == NMF_PREC_BF16 && !g_force_simt && 
 }  // namespace
 
 namespace nmf {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 int device_sm_count() { return sm_count(); }
 
@@ -316,6 +320,8 @@ nmf_status_t nmf_workspace_status(nmf_stream_t stream, const void* workspace, in
 }
 
 void nmf_set_kernel_path(int force_cuda_cores) { g_force_simt = force_cuda_cores ? 1 : 0; }
+
+long long nmf_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 nmf_status_t nmf_gaussian_sketch(nmf_stream_t stream, int rows, int cols, uint64_t seed, uint32_t stream_id,
                                  float* out) {

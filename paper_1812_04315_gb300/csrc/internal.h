@@ -182,4 +182,7 @@ int rre_parts(int n, int m);
 int device_sm_count();
 bool device_is_sm103();
 
+// Host-side count of kernel launches enqueued by the library (all threads).
+void count_launches(int k);
+
 }  // namespace nmf

@@ -359,6 +359,7 @@ cudaError_t launch_pm(const KParams& kp, cudaStream_t s) {
   }
   cfg.attrs = attr;
   cfg.numAttrs = nattr;
+  count_launches(1);
   return cudaLaunchKernelEx(&cfg, solve_kernel<PM>, kp);
 }
 
@@ -428,18 +429,21 @@ cudaError_t solve_launch_mode(const SolveArgs& a, const float* beta, int mode, c
 }
 
 cudaError_t beta_launch(float* beta, int K, cudaStream_t s) {
+  count_launches(1);
   beta_kernel<<<1, 32, 0, s>>>(beta, K);
   return cudaGetLastError();
 }
 
 cudaError_t stats_launch(nenmf_stats_t* stats, const double* pgG, int cG, const double* pgF, int cF, Control* ctrl,
                          int outer, cudaStream_t s) {
+  count_launches(1);
   stats_kernel<<<1, 32, 0, s>>>(stats, pgG, cG, pgF, cF, ctrl, outer);
   return cudaGetLastError();
 }
 
 cudaError_t eps_launch(Control* ctrl, const double* pgG, int cG, const double* pgF, int cF, double tol, int tol_mode,
                        nenmf_stats_t* stats, cudaStream_t s) {
+  count_launches(1);
   eps_kernel<<<1, 32, 0, s>>>(ctrl, pgG, cG, pgF, cF, tol, tol_mode, stats);
   return cudaGetLastError();
 }

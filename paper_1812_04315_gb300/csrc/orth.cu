@@ -254,6 +254,7 @@ cudaError_t rows_launch(const RowJob* jobs, int njobs, Control* ctrl, cudaStream
   const size_t smem = (size_t)(kOrthRows * kYsStride + max_nu * max_nu) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  count_launches(1);
   rows_kernel<<<total, kRowThreads, smem, s>>>(rj, ctrl);
   return cudaGetLastError();
 }
@@ -269,6 +270,7 @@ cudaError_t chol_launch(const CholJob* jobs, int njobs, Control* ctrl, cudaStrea
   const size_t smem = (size_t)2 * max_nu * kSS * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  count_launches(1);
   chol_kernel<<<njobs, kCholThreads, smem, s>>>(cj, ctrl);
   return cudaGetLastError();
 }

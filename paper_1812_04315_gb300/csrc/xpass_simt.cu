@@ -188,6 +188,7 @@ cudaError_t launch_t(const XPassPlan& pl, const XPassArgs& a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(xpass_simt_kernel<T, NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
+  count_launches(1);
   xpass_simt_kernel<T, NVC><<<pl.ctas, kSimtThreads, smem, s>>>(a, pl);
   return cudaGetLastError();
 }
