@@ -4,6 +4,9 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "internal.h"
 
@@ -38,6 +41,25 @@ namespace nmf {
 
 static std::atomic<long long> g_launches{0};
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+cudaError_t allow_dynamic_smem(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void*, int>, int>> done;  // (kernel, device) -> bytes
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& d : done)
+    if (d.first.first == kernel && d.first.second == dev) {
+      if (d.second >= bytes) return cudaSuccess;
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (e == cudaSuccess) d.second = bytes;
+      return e;
+    }
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.push_back({{kernel, dev}, bytes});
+  return e;
+}
 
 int device_sm_count() { return sm_count(); }
 
@@ -179,12 +201,16 @@ struct SolveWs {
   float* beta;
   float* Gt;       // p x n
   int ctasG, ctasF;
-  float* WG;       // [ctasF][p][nu]: partials of F_R = F R (compressed)
-  float* WF;       // [ctasG][p][nu]: partials of G_L^T = G^T L^T
-  float* HG;       // [ctasF][p][p]: partials of F F^T (plain)
-  float* HF;       // [ctasG][p][p]: partials of G^T G
-  double* pg2G;    // [3 * ctasG]
-  double* pg2F;    // [3 * ctasF]
+  Reduced* redG;   // W = F_R, H, L_c for the G update (written by the F side's tail)
+  Reduced* redF;   // W = G_L^T, H, L_c for the F update (written by the G side's tail)
+  float* partG;    // [ctasG][P] per-CTA partials of the G side's epilogue
+  float* partF;    // [ctasF][P]
+  float* groupG;   // [tail_groups(ctasG)][P]
+  float* groupF;
+  unsigned int* ctr;  // tail counters: G side [groupsG + 1], then F side [groupsF + 1]
+  int nctr;
+  double* pg2G;    // [(kStopSlots + 1) * ctasG]
+  double* pg2F;
   double* initG;   // [ctasG]
   double* initF;   // [ctasF]
   __nv_bfloat16* Xb;
@@ -205,20 +231,22 @@ SolveWs carve_solve(void* base, const nenmf_problem_t& pr) {
   const int n = pr.n, m = pr.m, p = pr.p;
   const bool plain = pr.mode == NENMF_PLAIN;
   const int nu = plain ? 0 : pr.nu;
+  const int P = plain ? p * p : p * nu;
   w.ctrl = cv.take<Control>(1);
   w.beta = cv.take<float>(kMaxInner);
   w.Gt = cv.take<float>((size_t)p * n);
   w.ctasG = solve_ctas(n);
   w.ctasF = solve_ctas(m);
-  if (!plain) {
-    w.WG = cv.take<float>((size_t)w.ctasF * p * nu);
-    w.WF = cv.take<float>((size_t)w.ctasG * p * nu);
-  } else {
-    w.HG = cv.take<float>((size_t)w.ctasF * p * p);
-    w.HF = cv.take<float>((size_t)w.ctasG * p * p);
-  }
-  w.pg2G = cv.take<double>((size_t)3 * w.ctasG);
-  w.pg2F = cv.take<double>((size_t)3 * w.ctasF);
+  w.redG = cv.take<Reduced>(1);
+  w.redF = cv.take<Reduced>(1);
+  w.partG = cv.take<float>((size_t)w.ctasG * P);
+  w.partF = cv.take<float>((size_t)w.ctasF * P);
+  w.groupG = cv.take<float>((size_t)tail_groups(w.ctasG) * P);
+  w.groupF = cv.take<float>((size_t)tail_groups(w.ctasF) * P);
+  w.nctr = tail_groups(w.ctasG) + 1 + tail_groups(w.ctasF) + 1;
+  w.ctr = cv.take<unsigned int>(w.nctr);
+  w.pg2G = cv.take<double>((size_t)(kStopSlots + 1) * w.ctasG);
+  w.pg2F = cv.take<double>((size_t)(kStopSlots + 1) * w.ctasF);
   w.initG = cv.take<double>(w.ctasG);
   w.initF = cv.take<double>(w.ctasF);
   if (plain) {
@@ -430,6 +458,7 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
   unsigned long long* times = reinterpret_cast<unsigned long long*>(pa.record_time_ns);
 
   NMF_CU(cudaMemsetAsync(ctrl, 0, sizeof(Control), s));
+  NMF_CU(cudaMemsetAsync(w.ctr, 0, sizeof(unsigned int) * w.nctr, s));
   if (stats) NMF_CU(cudaMemsetAsync(stats, 0, sizeof(nenmf_stats_t), s));
   if (times) {
     NMF_CU(cudaMemsetAsync(times, 0, sizeof(long long) * ((size_t)pa.max_outer + 1), s));
@@ -465,17 +494,20 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
   g.p = p; g.N = n; g.nu = nu; g.Y = w.Gt;
   g.max_inner = pa.max_inner; g.min_inner = pa.min_inner; g.stop_test = test; g.side = 0;
   g.pg2_init = w.initG; g.pg2_part = w.pg2G; g.stats = stats; g.ctrl = ctrl;
-  g.epi = epiG;
+  g.epi = epiG; g.red_in = w.redG; g.red_out = w.redF;
+  g.part_out = w.partG; g.group_out = w.groupG; g.tail_ctr = w.ctr;
   SolveArgs f = g;
   f.N = m; f.Y = F; f.side = 1; f.pg2_init = w.initF; f.pg2_part = w.pg2F; f.epi = epiF;
+  f.red_in = w.redF; f.red_out = w.redG;
+  f.part_out = w.partF; f.group_out = w.groupF; f.tail_ctr = w.ctr + tail_groups(w.ctasG) + 1;
   if (plain) {
     g.bsrc = B_FROM_PARTIALS; g.Bpart = w.partN; g.Bparts = w.plan.S_c; g.Bld = w.plan.NV;
-    g.Hpart = w.HG; g.Hparts = w.ctasF; g.Hpart_out = w.HF; g.op_out = w.opG; g.op_ld = w.ldG; g.op_bf16 = bf16;
+    g.op_out = w.opG; g.op_ld = w.ldG; g.op_bf16 = bf16;
     f.bsrc = B_FROM_PARTIALS; f.Bpart = w.partT; f.Bparts = w.plan.S_r; f.Bld = w.plan.NV;
-    f.Hpart = w.HF; f.Hparts = w.ctasG; f.Hpart_out = w.HG; f.op_out = w.opF; f.op_ld = w.ldF; f.op_bf16 = bf16;
+    f.op_out = w.opF; f.op_ld = w.ldF; f.op_bf16 = bf16;
   } else {
-    g.bsrc = B_FROM_ROWS; g.D = pr.XR; g.Wpart = w.WG; g.Wparts = w.ctasF; g.E = pr.L; g.Wpart_out = w.WF;
-    f.bsrc = B_FROM_COLS; f.D = pr.XL; f.Wpart = w.WF; f.Wparts = w.ctasG; f.E = pr.R; f.Wpart_out = w.WG;
+    g.bsrc = B_FROM_ROWS; g.D = pr.XR; g.E = pr.L;
+    f.bsrc = B_FROM_COLS; f.D = pr.XL; f.E = pr.R;
   }
 
   // Products of the initial F for the first G update (and its operand copy).
@@ -514,8 +546,8 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
     NMF_CU(solve_launch_mode(ft, w.beta, MODE_SOLVE, s));
   }
   if (stats || pa.max_outer > 0)
-    NMF_CU(stats_launch(stats, pa.max_outer > 0 ? w.pg2G + 2 * w.ctasG : nullptr, w.ctasG,
-                        pa.max_outer > 0 ? w.pg2F + 2 * w.ctasF : nullptr, w.ctasF, ctrl, pa.max_outer, s));
+    NMF_CU(stats_launch(stats, pa.max_outer > 0 ? w.pg2G + kStopSlots * w.ctasG : nullptr, w.ctasG,
+                        pa.max_outer > 0 ? w.pg2F + kStopSlots * w.ctasF : nullptr, w.ctasF, ctrl, pa.max_outer, s));
   NMF_CU(transpose_launch(w.Gt, p, n, G, p, 0, nullptr, s));
   return NMF_OK;
 }

@@ -111,30 +111,43 @@ inline int rows_ctas(int N) { return ceil_div(N, kOrthRows); }
 enum BSource { B_FROM_ROWS = 0, B_FROM_COLS = 1, B_FROM_PARTIALS = 2 };
 enum Epilogue { EPI_NONE = 0, EPI_W_ROWS = 1, EPI_W_COLS = 2, EPI_GRAM = 3 };
 constexpr int kSolveThreads = 128;
+constexpr int kStopSlots = 8;    // per-test partial-sum slots of the stop test
+constexpr int kTailGroup = 8;    // CTAs per first-level group of the tail reduction
+
+// What one solve hands the next: the reduced W (compressed modes), the Gram
+// matrix H and its largest eigenvalue L_c.
+struct Reduced {
+  float W[NMF_MAX_RANK * NMF_MAX_SKETCH];  // p x nu, row stride nu
+  float H[NMF_MAX_RANK * NMF_MAX_RANK];    // p x p, row stride p
+  float Lc;
+  int status;
+  double Lc_d;
+};
+
+__host__ __device__ inline int tail_groups(int ctas) { return ceil_div(ctas, kTailGroup); }
 
 struct SolveArgs {
   int p, N, nu;
-  float* Y;              // p x N, in/out (unchanged when max_inner == 0)
-  // H and B
+  float* Y;              // p x N, in/out (unchanged unless MODE_SOLVE)
+  // B of the subproblem
   int bsrc;              // BSource
   const float* D;        // B_FROM_ROWS: N x nu; B_FROM_COLS: nu x N
-  const float* Wpart;    // [Wparts][p][nu] partials of W (compressed modes)
-  int Wparts;
   const float* Bpart;    // B_FROM_PARTIALS: [Bparts][N][Bld]
   int Bparts, Bld;
-  const float* Hpart;    // B_FROM_PARTIALS: [Hparts][p][p]
-  int Hparts;
+  const Reduced* red_in; // W, H, L_c of this subproblem
   // iteration
   int max_inner, min_inner;
   bool stop_test;        // needs cooperative launch
   int side;              // 0 = G, 1 = F (stats slot)
-  double* pg2_init;      // when max_inner == 0: per-CTA ||P grad(Y0)||^2 partials
-  double* pg2_part;      // [2][ctas] per-iteration partials (stop test) and [ctas] final
-  // epilogue
+  double* pg2_init;      // MODE_EVAL: per-CTA ||P grad(Y0)||^2
+  double* pg2_part;      // [kStopSlots + 1][ctas]: stop-test partials, then the final one
+  // epilogue: partial products for the next phase, reduced by the last CTA
   int epi;               // Epilogue
   const float* E;        // EPI_W_ROWS: N x nu; EPI_W_COLS: nu x N
-  float* Wpart_out;      // [ctas][p][nu]
-  float* Hpart_out;      // [ctas][p][p]
+  float* part_out;       // [ctas][p * (nu or p)]
+  float* group_out;      // [tail_groups(ctas)][p * (nu or p)]
+  unsigned int* tail_ctr;  // [tail_groups(ctas) + 1], zero, left zero
+  Reduced* red_out;
   void* op_out;          // optional transposed operand NV x op_ld (float or bf16)
   int op_ld, op_bf16;
   float* record;         // optional snapshot: Y^T as N x p (G) or Y as p x N (F)
@@ -146,9 +159,9 @@ struct SolveArgs {
 
 enum SolveMode { MODE_EPI_ONLY = 0, MODE_EVAL = 1, MODE_SOLVE = 2 };
 int solve_ctas(int N);
-// MODE_EPI_ONLY: only the epilogue on Y as given; MODE_EVAL: prologue, the
-// projected-gradient norm of Y0 into pg2_init, then the epilogue on Y0;
-// MODE_SOLVE: the inner loop. `beta` holds beta_k for k < max_inner.
+// MODE_EPI_ONLY: only the epilogue on Y as given; MODE_EVAL: the projected-
+// gradient norm of Y0 into pg2_init, then the epilogue on Y0; MODE_SOLVE:
+// the inner loop. `beta` holds beta_k for k < max_inner.
 cudaError_t solve_launch_mode(const SolveArgs& a, const float* beta, int mode, cudaStream_t s);
 cudaError_t beta_launch(float* beta, int K, cudaStream_t s);
 // CTAs that can be co-resident for the solve kernel (cooperative launches).
@@ -184,5 +197,9 @@ bool device_is_sm103();
 
 // Host-side count of kernel launches enqueued by the library (all threads).
 void count_launches(int k);
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` once per device
+// (cached: the attribute call is not repeated on the launch path).
+cudaError_t allow_dynamic_smem(const void* kernel, int bytes);
 
 }  // namespace nmf

@@ -57,13 +57,22 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
   float* Rs = Ys + kOrthRows * kYsStride;        // nu x nu (apply only)
 
   if (J.part) {
+    // Sum over the S partials with 4 independent accumulators (loads in
+    // flight together), combined in a fixed order.
     for (int i = tid; i < rows * nu; i += kRowThreads) {
       const int r = i / nu, c = i % nu;
       const float* p = J.part + (size_t)(r0 + r) * J.ldp + c;
       const size_t stride = (size_t)J.N * J.ldp;
-      float s = 0.f;
-      for (int k = 0; k < J.S; ++k) s += p[k * stride];
-      Ys[r * kYsStride + c] = s;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int k = 0;
+      for (; k + 4 <= J.S; k += 4) {
+        s0 += __ldcg(p + (k + 0) * stride);
+        s1 += __ldcg(p + (k + 1) * stride);
+        s2 += __ldcg(p + (k + 2) * stride);
+        s3 += __ldcg(p + (k + 3) * stride);
+      }
+      for (; k < J.S; ++k) s0 += __ldcg(p + k * stride);
+      Ys[r * kYsStride + c] = (s0 + s1) + (s2 + s3);
     }
   } else {
     for (int i = tid; i < nu * nu; i += kRowThreads) Rs[i] = J.rinv[i];
@@ -147,15 +156,30 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(CholJobs jobs, Contr
   __shared__ int fail;
   __shared__ double shift;
 
+  // Sum of the per-CTA float-float partials: 8 independent accumulators per
+  // entry (loads in flight together), combined in a fixed order.
   for (int e = tid; e < E; e += kCholThreads) {
-    DF s{0.f, 0.f};
-    for (int p = 0; p < J.parts; ++p) {
-      const float2 v = J.gram_part[(size_t)p * E + e];
-      df_add(s, v.x, v.y);
+    constexpr int kAcc = 8;
+    DF s[kAcc];
+#pragma unroll
+    for (int i = 0; i < kAcc; ++i) s[i] = DF{0.f, 0.f};
+    int p = 0;
+    for (; p + kAcc <= J.parts; p += kAcc) {
+#pragma unroll
+      for (int i = 0; i < kAcc; ++i) {
+        const float2 v = __ldcg(J.gram_part + (size_t)(p + i) * E + e);
+        df_add(s[i], v.x, v.y);
+      }
     }
+    for (int i = 0; p < J.parts; ++p, ++i) {
+      const float2 v = __ldcg(J.gram_part + (size_t)p * E + e);
+      df_add(s[i], v.x, v.y);
+    }
+#pragma unroll
+    for (int i = 1; i < kAcc; ++i) df_add(s[0], s[i].hi, s[i].lo);
     int a, b;
     tri_index(e, nu, a, b);
-    const double v = (double)s.hi + (double)s.lo;
+    const double v = (double)s[0].hi + (double)s[0].lo;
     S[a * kSS + b] = v;
     S[b * kSS + a] = v;
   }
@@ -252,7 +276,7 @@ cudaError_t rows_launch(const RowJob* jobs, int njobs, Control* ctrl, cudaStream
   }
   rj.start[njobs] = total;
   const size_t smem = (size_t)(kOrthRows * kYsStride + max_nu * max_nu) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void*)rows_kernel, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
   rows_kernel<<<total, kRowThreads, smem, s>>>(rj, ctrl);
@@ -268,7 +292,7 @@ cudaError_t chol_launch(const CholJob* jobs, int njobs, Control* ctrl, cudaStrea
     if (jobs[i].nu > max_nu) max_nu = jobs[i].nu;
   }
   const size_t smem = (size_t)2 * max_nu * kSS * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void*)chol_kernel, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
   chol_kernel<<<njobs, kCholThreads, smem, s>>>(cj, ctrl);

@@ -185,8 +185,7 @@ template <typename T, int NVC>
 cudaError_t launch_t(const XPassPlan& pl, const XPassArgs& a, cudaStream_t s) {
   const int maxct = ceil_div(pl.tiles_c, pl.S_c);
   size_t smem = simt_fixed_smem(NVC) + (a.doT ? (size_t)maxct * kTile * NVC * sizeof(float) : 0);
-  cudaError_t e = cudaFuncSetAttribute(xpass_simt_kernel<T, NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void*)xpass_simt_kernel<T, NVC>, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
   xpass_simt_kernel<T, NVC><<<pl.ctas, kSimtThreads, smem, s>>>(a, pl);
