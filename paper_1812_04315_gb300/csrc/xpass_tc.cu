@@ -1,12 +1,446 @@
-// xpass_tc.cu -- tcgen05 tensor-core X pass for bfloat16 X (not yet enabled).
+// xpass_tc.cu -- one pass over a bfloat16 X on the tcgen05 tensor cores:
+//   Y_N = X * A (n x nu) and Y_T = X^T * B (m x nu) from a single read of X,
+// the two products of every pass of Alg. 2 (and Alg. 1's X R, X^T L^T, plain
+// NeNMF's X F^T, X^T G).
+//
+// Tiles. X is cut into 128 x 128 tiles; a CTA owns a rectangle of tiles
+// (row tiles rt0..rt1, column tiles ct0..ct1) and walks it row by row. One
+// X tile lands in shared memory once (TMA, 128-byte swizzle, two 128 x 64
+// boxes) and feeds two MMAs:
+//   N product: D_N[128 rows x NV] += X_tile (K-major, K = tile columns) * A^T tile
+//   T product: D_T[ct][128 cols x NV] += X_tile^T (MN-major view of the same
+//              bytes, K = tile rows) * B^T tile
+// D_N (double buffered) completes at the end of a row of tiles and is drained
+// by the epilogue warps as one partial of the CTA's column group; every D_T[ct]
+// accumulates over the CTA's row tiles in TMEM and is drained at the end as
+// one partial of its row group. Partials are summed in a fixed order later.
+//
+// Warps: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2..5 = epilogue
+// (TMEM lane quarter = warp % 4). Every mbarrier wait is bounded; on expiry
+// the CTA records NMF_ERR_DEVICE_TIMEOUT, stops issuing work, waits (bounded)
+// for its own copies in flight, frees its TMEM and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "internal.h"
 
 namespace nmf {
+namespace {
 
-bool xpass_tc_available() { return false; }
-XPassPlan xpass_tc_plan(int n, int m, int nu, int num_sms) { return xpass_simt_plan(n, m, nu, num_sms); }
-cudaError_t xpass_tc_launch(const XPassPlan& plan, const XPassArgs& a, cudaStream_t s) {
-  return xpass_simt_launch(plan, a, true, s);
+constexpr int kTM = 128;             // tile rows (M of the N product)
+constexpr int kTK = 128;             // tile columns (M of the T product)
+constexpr int kBoxK = 64;            // bf16 elements per 128-byte swizzle row
+constexpr int kMaxStages = 4;
+constexpr int kThreads = 192;
+constexpr size_t kSmemBudget = 220 * 1024;
+constexpr int kXStageBytes = kTM * kTK * 2;  // 32 KB
+constexpr uint32_t kMaxTmemCols = 512;
+constexpr long long kWaitLimit = 1ll << 31;  // clock cycles (~1 s)
+
+struct TcParams {
+  int n, m, stages;
+  int tiles_r, tiles_c, S_r, S_c;
+  int doN, doT;
+  float* partN;
+  float* partT;
+  Control* ctrl;
+  uint32_t tmem_cols;
+};
+
+__host__ __device__ __forceinline__ int split_point(int total, int parts, int i) {
+  return (int)(((long long)total * i) / parts);
+}
+
+// ---- PTX wrappers ---------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, P1;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait: false when the deadline passed or the CTA is aborting.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitLimit) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05): start, leading and stride byte
+// offsets (>> 4), descriptor version 1, 128-byte swizzle (layout type 2).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor, kind::f16: fp32 accumulate, bf16 A and B,
+// A major-ness (0 = K-major, 1 = MN-major), B K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N, int a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kThreads, 1)
+    xpass_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapA,
+                    const __grid_constant__ CUtensorMap mapB, TcParams P) {
+  if (call_failed(P.ctrl)) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int opBox = NV * kBoxK * 2;          // one NV x 64 operand box
+  constexpr int stageBytes = kXStageBytes + 4 * opBox;
+  const int kStages = P.stages;
+  __shared__ uint64_t full[kMaxStages], empty[kMaxStages], tfull[2], tempty[2], tdone;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rg = blockIdx.x / P.S_c, cg = blockIdx.x % P.S_c;
+  const int rt0 = split_point(P.tiles_r, P.S_r, rg), rt1 = split_point(P.tiles_r, P.S_r, rg + 1);
+  const int ct0 = split_point(P.tiles_c, P.S_c, cg), ct1 = split_point(P.tiles_c, P.S_c, cg + 1);
+  const int nrt = rt1 - rt0, nct = ct1 - ct0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(&tdone, 1);
+    abort_s = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(P.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+  volatile int* abort_flag = &abort_s;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      const uint32_t bytes = kXStageBytes + (P.doN ? 2 * opBox : 0) + (P.doT ? 2 * opBox : 0);
+      int it = 0;
+      for (int rt = rt0; rt < rt1 && !*abort_flag; ++rt) {
+        for (int ct = ct0; ct < ct1; ++ct, ++it) {
+          const int s = it % kStages;
+          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+          uint8_t* st = smem + (size_t)s * stageBytes;
+          mbar_arrive_expect_tx(&full[s], bytes);
+          tma_load_2d(st, &mapX, &full[s], ct * kTK, rt * kTM);
+          tma_load_2d(st + kXStageBytes / 2, &mapX, &full[s], ct * kTK + kBoxK, rt * kTM);
+          if (P.doN) {
+            tma_load_2d(st + kXStageBytes, &mapA, &full[s], ct * kTK, 0);
+            tma_load_2d(st + kXStageBytes + opBox, &mapA, &full[s], ct * kTK + kBoxK, 0);
+          }
+          if (P.doT) {
+            tma_load_2d(st + kXStageBytes + 2 * opBox, &mapB, &full[s], rt * kTM, 0);
+            tma_load_2d(st + kXStageBytes + 3 * opBox, &mapB, &full[s], rt * kTM + kBoxK, 0);
+          }
+        }
+      }
+      if (*abort_flag) {
+        // let the copies already issued land before the CTA exits
+        const int issued = it;
+        for (int j = issued - kStages < 0 ? 0 : issued - kStages; j < issued; ++j) {
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u) && clock64() - t0 < kWaitLimit) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idN = instr_desc(kTM, NV, 0);
+      const uint32_t idT = instr_desc(kTK, NV, 1);
+      int it = 0;
+      bool ok = true;
+      for (int ri = 0; ri < nrt && ok; ++ri) {
+        const int buf = ri & 1;
+        const uint32_t dN = tmem + (uint32_t)(buf * NV);
+        if (P.doN) {
+          if (!mbar_wait(&tempty[buf], ((uint32_t)(ri >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+        }
+        for (int ci = 0; ci < nct; ++ci, ++it) {
+          const int s = it % kStages;
+          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          if (!mbar_wait(&full[s], ph, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + (size_t)s * stageBytes);
+          const uint32_t xa = st, opa = st + kXStageBytes, opb = st + kXStageBytes + 2 * opBox;
+          if (P.doN) {
+#pragma unroll
+            for (int kk = 0; kk < kTK / 16; ++kk) {
+              const uint32_t off = (uint32_t)((kk >> 2) * (kXStageBytes / 2) + (kk & 3) * 32);
+              const uint32_t boff = (uint32_t)((kk >> 2) * opBox + (kk & 3) * 32);
+              tc_mma(dN, smem_desc(xa + off, 16, 1024), smem_desc(opa + boff, 16, 1024), idN,
+                     (ci > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          if (P.doT) {
+            const uint32_t dT = tmem + (uint32_t)((2 + ci) * NV);
+#pragma unroll
+            for (int kk = 0; kk < kTM / 16; ++kk) {
+              const uint32_t aoff = (uint32_t)(kk * 2048);
+              const uint32_t boff = (uint32_t)((kk >> 2) * opBox + (kk & 3) * 32);
+              tc_mma(dT, smem_desc(xa + aoff, kXStageBytes / 2, 1024), smem_desc(opb + boff, 16, 1024), idT,
+                     (ri > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          tc_commit(&empty[s]);
+        }
+        if (ok && P.doN) tc_commit(&tfull[buf]);
+      }
+      tc_commit(&tdone);
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int q = warp & 3;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    float v[NV];
+    if (P.doN) {
+      for (int ri = 0; ri < nrt; ++ri) {
+        const int buf = ri & 1;
+        if (!mbar_wait(&tfull[buf], (uint32_t)(ri >> 1) & 1u, abort_flag)) break;
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < NV; c += 8) tmem_ld8(tmem + lane_off + (uint32_t)(buf * NV + c), v + c);
+        tmem_ld_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        const int row = (rt0 + ri) * kTM + q * 32 + lane;
+        if (row < P.n) {
+          float4* dst = reinterpret_cast<float4*>(P.partN + ((size_t)cg * P.n + row) * NV);
+#pragma unroll
+          for (int c = 0; c < NV; c += 4) dst[c / 4] = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+        }
+      }
+    }
+    if (P.doT && mbar_wait(&tdone, 0u, abort_flag)) {
+      tc_fence_after();
+      for (int ci = 0; ci < nct; ++ci) {
+#pragma unroll
+        for (int c = 0; c < NV; c += 8) tmem_ld8(tmem + lane_off + (uint32_t)((2 + ci) * NV + c), v + c);
+        tmem_ld_wait();
+        const int col = (ct0 + ci) * kTK + q * 32 + lane;
+        if (col < P.m) {
+          float4* dst = reinterpret_cast<float4*>(P.partT + ((size_t)rg * P.m + col) * NV);
+#pragma unroll
+          for (int c = 0; c < NV; c += 4) dst[c / 4] = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+        }
+      }
+    } else if (!P.doT) {
+      mbar_wait(&tdone, 0u, abort_flag);
+    }
+  }
+  // The MMA issuer's last commit (tdone) completes only when every MMA has
+  // finished reading shared memory and writing TMEM.
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) set_status(P.ctrl, NMF_ERR_DEVICE_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols));
+  }
+}
+
+// ---- host side -------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2D bf16 map over a row-major [rows][ld] array, box box_cols x box_rows, 128-byte swizzle.
+bool make_map(CUtensorMap* map, const void* base, int ld, int rows, int box_cols, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+uint32_t tmem_cols_for(int NV, int maxct) {
+  const uint32_t need = (uint32_t)((2 + maxct) * NV);
+  uint32_t c = 32;
+  while (c < need) c <<= 1;
+  return c;
+}
+
+int max_col_tiles(int NV) { return (int)(kMaxTmemCols / NV) - 2; }
+
+size_t tc_stage_bytes(int NV) { return (size_t)(kXStageBytes + 4 * NV * kBoxK * 2); }
+int tc_stages(int NV) {
+  int st = (int)((kSmemBudget - 1024) / tc_stage_bytes(NV));
+  return st > kMaxStages ? kMaxStages : st;
+}
+size_t tc_smem_bytes(int NV) { return (size_t)tc_stages(NV) * tc_stage_bytes(NV) + 1024; }
+
+template <int NV>
+cudaError_t launch_nv(const CUtensorMap& mX, const CUtensorMap& mA, const CUtensorMap& mB, const TcParams& P,
+                      int ctas, cudaStream_t s) {
+  const size_t smem = tc_smem_bytes(NV);
+  cudaError_t e = allow_dynamic_smem((const void*)xpass_tc_kernel<NV>, (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  xpass_tc_kernel<NV><<<ctas, kThreads, smem, s>>>(mX, mA, mB, P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool xpass_tc_available() {
+  static int avail = -1;
+  if (avail < 0) {
+    int dev = 0, major = 0, minor = 0;
+    avail = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
+      avail = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
+  }
+  return avail == 1;
+}
+
+// Region grid: the S_r x S_c split of the tile grid with at most `num_sms`
+// CTAs that minimises the largest region (tiles per CTA), subject to the
+// TMEM budget on column tiles per region.
+XPassPlan xpass_tc_plan(int n, int m, int nu, int num_sms) {
+  XPassPlan pl{};
+  pl.tile_r = kTM;
+  pl.tile_c = kTK;
+  pl.tiles_r = ceil_div(n, kTM);
+  pl.tiles_c = ceil_div(m, kTK);
+  pl.NV = round_up(nu, 16);
+  const int maxct = max_col_tiles(pl.NV);
+  long best = -1;
+  int bestr = 1, bestc = pl.tiles_c;
+  for (int S_c = 1; S_c <= pl.tiles_c; ++S_c) {
+    if (ceil_div(pl.tiles_c, S_c) > maxct) continue;
+    for (int S_r = 1; S_r <= pl.tiles_r && S_r * S_c <= num_sms; ++S_r) {
+      const long worst = (long)ceil_div(pl.tiles_r, S_r) * ceil_div(pl.tiles_c, S_c);
+      if (best < 0 || worst < best || (worst == best && S_r * S_c < bestr * bestc)) {
+        best = worst;
+        bestr = S_r;
+        bestc = S_c;
+      }
+    }
+  }
+  pl.S_r = bestr;
+  pl.S_c = bestc;
+  pl.ctas = bestr * bestc;
+  return pl;
+}
+
+cudaError_t xpass_tc_launch(const XPassPlan& pl, const XPassArgs& a, cudaStream_t s) {
+  CUtensorMap mX, mA, mB;
+  if (!make_map(&mX, a.X, a.ldx, a.n, kBoxK, kTM)) return cudaErrorInvalidValue;
+  if (!make_map(&mA, a.opA, a.lda, pl.NV, kBoxK, pl.NV)) return cudaErrorInvalidValue;
+  if (!make_map(&mB, a.opB, a.ldb, pl.NV, kBoxK, pl.NV)) return cudaErrorInvalidValue;
+  TcParams P{};
+  P.n = a.n;
+  P.m = a.m;
+  P.stages = tc_stages(pl.NV);
+  P.tiles_r = pl.tiles_r;
+  P.tiles_c = pl.tiles_c;
+  P.S_r = pl.S_r;
+  P.S_c = pl.S_c;
+  P.doN = a.doN;
+  P.doT = a.doT;
+  P.partN = a.partN;
+  P.partT = a.partT;
+  P.ctrl = a.ctrl;
+  P.tmem_cols = tmem_cols_for(pl.NV, ceil_div(pl.tiles_c, pl.S_c));
+  switch (pl.NV) {
+    case 16: return launch_nv<16>(mX, mA, mB, P, pl.ctas, s);
+    case 32: return launch_nv<32>(mX, mA, mB, P, pl.ctas, s);
+    case 48: return launch_nv<48>(mX, mA, mB, P, pl.ctas, s);
+    case 64: return launch_nv<64>(mX, mA, mB, P, pl.ctas, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace nmf

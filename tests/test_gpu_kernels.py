@@ -42,7 +42,8 @@ def _bf16_round(a):
     return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
 
 
-@pytest.mark.parametrize("n,m,k", [(300, 517, 20), (64, 64, 1), (129, 1000, 10), (1000, 77, 42), (5, 7, 3)])
+@pytest.mark.parametrize("n,m,k", [(300, 517, 20), (64, 64, 1), (129, 1000, 10), (1000, 77, 42), (5, 7, 3),
+                                   (2000, 3000, 20), (3100, 2600, 42), (2500, 4100, 64), (4000, 1000, 10)])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_dual_product(nmf, n, m, k, prec):
     rng = np.random.default_rng(n * 31 + m + k)
@@ -62,6 +63,25 @@ def test_dual_product(nmf, n, m, k, prec):
     YN2, YT2 = nmf.dual_product(_t(X), _t(A), None, prec=prec)
     assert YT2 is None
     np.testing.assert_array_equal(_np(YN2), _np(YN))
+
+
+@pytest.mark.parametrize("n,m,k", [(2000, 3000, 20), (1000, 77, 42), (3333, 2222, 64)])
+def test_tensor_core_path_matches_cuda_core_path(nmf, n, m, k):
+    # Same bfloat16 inputs on both kernels: only the float32 summation order differs.
+    rng = np.random.default_rng(k)
+    X = _t(rng.random((n, m)))
+    A = _t(rng.standard_normal((m, k)))
+    B = _t(rng.standard_normal((n, k)))
+    tcN, tcT = nmf.dual_product(X, A, B, prec=1)
+    nmf.set_kernel_path(True)
+    try:
+        scN, scT = nmf.dual_product(X, A, B, prec=1)
+    finally:
+        nmf.set_kernel_path(False)
+    for a, b, K in ((tcN, scN, m), (tcT, scT, n)):
+        a, b = _np(a), _np(b)
+        scale = np.abs(b).max()
+        assert np.max(np.abs(a - b)) <= 8 * np.sqrt(K) * 2.0 ** -24 * np.sqrt(K) * scale
 
 
 def test_dual_product_is_deterministic(nmf):
