@@ -201,16 +201,17 @@ struct SolveWs {
   float* beta;
   float* Gt;       // p x n
   int ctasG, ctasF;
-  Reduced* redG;   // W = F_R, H, L_c for the G update (written by the F side's tail)
-  Reduced* redF;   // W = G_L^T, H, L_c for the F update (written by the G side's tail)
-  float* partG;    // [ctasG][P] per-CTA partials of the G side's epilogue
-  float* partF;    // [ctasF][P]
-  float* groupG;   // [tail_groups(ctasG)][P]
-  float* groupF;
-  unsigned int* ctr;  // tail counters: G side [groupsG + 1], then F side [groupsF + 1]
+  int P;           // floats of one partial: p * nu (compressed) or p * p (plain)
+  int groupG, groupF;  // partial group sizes (1: the successor reads per-CTA partials)
+  float* partG;    // [ctasG][P]: the G side's share of the F update's W (or Gram)
+  float* partF;    // [ctasF][P]: the F side's share of the G update's W (or Gram)
+  float* groupOutG;  // [group_count(ctasG, groupG)][P] when groupG > 1
+  float* groupOutF;
+  unsigned int* ctr;  // group tickets: G side, then F side
   int nctr;
-  double* pg2G;    // [(kStopSlots + 1) * ctasG]
+  double* pg2G;    // [ctasG]
   double* pg2F;
+  unsigned long long* slots;  // stop-test slots: G side [kStopSlots][ctasG], then F side
   double* initG;   // [ctasG]
   double* initF;   // [ctasF]
   __nv_bfloat16* Xb;
@@ -232,21 +233,23 @@ SolveWs carve_solve(void* base, const nenmf_problem_t& pr) {
   const bool plain = pr.mode == NENMF_PLAIN;
   const int nu = plain ? 0 : pr.nu;
   const int P = plain ? p * p : p * nu;
+  w.P = P;
   w.ctrl = cv.take<Control>(1);
   w.beta = cv.take<float>(kMaxInner);
   w.Gt = cv.take<float>((size_t)p * n);
   w.ctasG = solve_ctas(n);
   w.ctasF = solve_ctas(m);
-  w.redG = cv.take<Reduced>(1);
-  w.redF = cv.take<Reduced>(1);
+  w.groupG = partial_group_size(w.ctasG, P);
+  w.groupF = partial_group_size(w.ctasF, P);
   w.partG = cv.take<float>((size_t)w.ctasG * P);
   w.partF = cv.take<float>((size_t)w.ctasF * P);
-  w.groupG = cv.take<float>((size_t)tail_groups(w.ctasG) * P);
-  w.groupF = cv.take<float>((size_t)tail_groups(w.ctasF) * P);
-  w.nctr = tail_groups(w.ctasG) + 1 + tail_groups(w.ctasF) + 1;
+  w.groupOutG = cv.take<float>((size_t)group_count(w.ctasG, w.groupG) * P);
+  w.groupOutF = cv.take<float>((size_t)group_count(w.ctasF, w.groupF) * P);
+  w.nctr = group_count(w.ctasG, w.groupG) + group_count(w.ctasF, w.groupF);
   w.ctr = cv.take<unsigned int>(w.nctr);
-  w.pg2G = cv.take<double>((size_t)(kStopSlots + 1) * w.ctasG);
-  w.pg2F = cv.take<double>((size_t)(kStopSlots + 1) * w.ctasF);
+  w.pg2G = cv.take<double>(w.ctasG);
+  w.pg2F = cv.take<double>(w.ctasF);
+  w.slots = cv.take<unsigned long long>((size_t)kStopSlots * kSolveWarps * (w.ctasG + w.ctasF));
   w.initG = cv.take<double>(w.ctasG);
   w.initF = cv.take<double>(w.ctasF);
   if (plain) {
@@ -440,7 +443,8 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
   if (!problem_ok(problem) || !params || !G || !F) return NMF_ERR_INVALID_ARG;
   const nenmf_problem_t pr = *problem;
   const nenmf_params_t pa = *params;
-  if (pa.max_outer < 0 || pa.max_inner < 1 || pa.max_inner > kMaxInner || pa.min_inner < 1) return NMF_ERR_INVALID_ARG;
+  if (pa.max_outer < 0 || pa.max_outer > 32000 || pa.max_inner < 1 || pa.max_inner > kMaxInner || pa.min_inner < 1)
+    return NMF_ERR_INVALID_ARG;
   if (pa.tol_mode != NENMF_TOL_REL && pa.tol_mode != NENMF_TOL_ABS) return NMF_ERR_INVALID_ARG;
   const SolveWs w = carve_solve(workspace, pr);
   if (!ws_ok(workspace, workspace_bytes, w.bytes)) return NMF_ERR_WORKSPACE;
@@ -449,7 +453,10 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
   const bool test = pa.tol > 0.0;
   const int epiG = plain ? EPI_GRAM : EPI_W_COLS;
   const int epiF = plain ? EPI_GRAM : EPI_W_ROWS;
-  if (test && (w.ctasG > solve_max_coresident(p, nu, epiG) || w.ctasF > solve_max_coresident(p, nu, epiF)))
+  const int groupsInG = w.groupF > 1 ? group_count(w.ctasF, w.groupF) : w.ctasF;  // read by the G update
+  const int groupsInF = w.groupG > 1 ? group_count(w.ctasG, w.groupG) : w.ctasG;  // read by the F update
+  if (test && (w.ctasG > solve_max_coresident(p, nu, epiG, groupsInG) ||
+               w.ctasF > solve_max_coresident(p, nu, epiF, groupsInF)))
     return NMF_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   Control* ctrl = w.ctrl;
@@ -459,6 +466,8 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
 
   NMF_CU(cudaMemsetAsync(ctrl, 0, sizeof(Control), s));
   NMF_CU(cudaMemsetAsync(w.ctr, 0, sizeof(unsigned int) * w.nctr, s));
+  if (test)
+    NMF_CU(cudaMemsetAsync(w.slots, 0, sizeof(unsigned long long) * kStopSlots * kSolveWarps * (w.ctasG + w.ctasF), s));
   if (stats) NMF_CU(cudaMemsetAsync(stats, 0, sizeof(nenmf_stats_t), s));
   if (times) {
     NMF_CU(cudaMemsetAsync(times, 0, sizeof(long long) * ((size_t)pa.max_outer + 1), s));
@@ -494,12 +503,18 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
   g.p = p; g.N = n; g.nu = nu; g.Y = w.Gt;
   g.max_inner = pa.max_inner; g.min_inner = pa.min_inner; g.stop_test = test; g.side = 0;
   g.pg2_init = w.initG; g.pg2_part = w.pg2G; g.stats = stats; g.ctrl = ctrl;
-  g.epi = epiG; g.red_in = w.redG; g.red_out = w.redF;
-  g.part_out = w.partG; g.group_out = w.groupG; g.tail_ctr = w.ctr;
+  g.epi = epiG;
+  g.part_in = w.groupF > 1 ? w.groupOutF : w.partF;
+  g.groups_in = groupsInG;
+  g.part_out = w.partG; g.group = w.groupG; g.group_out = w.groupOutG; g.tail_ctr = w.ctr;
+  g.stop_slots = w.slots;
   SolveArgs f = g;
   f.N = m; f.Y = F; f.side = 1; f.pg2_init = w.initF; f.pg2_part = w.pg2F; f.epi = epiF;
-  f.red_in = w.redF; f.red_out = w.redG;
-  f.part_out = w.partF; f.group_out = w.groupF; f.tail_ctr = w.ctr + tail_groups(w.ctasG) + 1;
+  f.part_in = w.groupG > 1 ? w.groupOutG : w.partG;
+  f.groups_in = groupsInF;
+  f.part_out = w.partF; f.group = w.groupF; f.group_out = w.groupOutF;
+  f.tail_ctr = w.ctr + group_count(w.ctasG, w.groupG);
+  f.stop_slots = w.slots + (size_t)kStopSlots * kSolveWarps * w.ctasG;
   if (plain) {
     g.bsrc = B_FROM_PARTIALS; g.Bpart = w.partN; g.Bparts = w.plan.S_c; g.Bld = w.plan.NV;
     g.op_out = w.opG; g.op_ld = w.ldG; g.op_bf16 = bf16;
@@ -534,6 +549,7 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
   for (int t = 0; t < pa.max_outer; ++t) {
     if (plain) NMF_CU(xpass_launch(w.plan, xN, prec, s));
     SolveArgs gt = g;
+    gt.epoch = 2 * t + 1;
     if (pa.record_G) {
       gt.record = pa.record_G + (size_t)t * n * p;
       gt.record_transposed = 1;
@@ -541,13 +557,14 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
     NMF_CU(solve_launch_mode(gt, w.beta, MODE_SOLVE, s));
     if (plain) NMF_CU(xpass_launch(w.plan, xT, prec, s));
     SolveArgs ft = f;
+    ft.epoch = 2 * t + 2;
     if (pa.record_F) ft.record = pa.record_F + (size_t)t * p * m;
     if (times) ft.time_out = times + t + 1;
     NMF_CU(solve_launch_mode(ft, w.beta, MODE_SOLVE, s));
   }
   if (stats || pa.max_outer > 0)
-    NMF_CU(stats_launch(stats, pa.max_outer > 0 ? w.pg2G + kStopSlots * w.ctasG : nullptr, w.ctasG,
-                        pa.max_outer > 0 ? w.pg2F + kStopSlots * w.ctasF : nullptr, w.ctasF, ctrl, pa.max_outer, s));
+    NMF_CU(stats_launch(stats, pa.max_outer > 0 ? w.pg2G : nullptr, w.ctasG, pa.max_outer > 0 ? w.pg2F : nullptr,
+                        w.ctasF, ctrl, pa.max_outer, s));
   NMF_CU(transpose_launch(w.Gt, p, n, G, p, 0, nullptr, s));
   return NMF_OK;
 }

@@ -111,20 +111,19 @@ inline int rows_ctas(int N) { return ceil_div(N, kOrthRows); }
 enum BSource { B_FROM_ROWS = 0, B_FROM_COLS = 1, B_FROM_PARTIALS = 2 };
 enum Epilogue { EPI_NONE = 0, EPI_W_ROWS = 1, EPI_W_COLS = 2, EPI_GRAM = 3 };
 constexpr int kSolveThreads = 128;
-constexpr int kStopSlots = 8;    // per-test partial-sum slots of the stop test
-constexpr int kTailGroup = 8;    // CTAs per first-level group of the tail reduction
+constexpr int kSolveWarps = kSolveThreads / 32;
+constexpr int kStopSlots = 16;   // per-test partial-sum slots of the stop test
 
-// What one solve hands the next: the reduced W (compressed modes), the Gram
-// matrix H and its largest eigenvalue L_c.
-struct Reduced {
-  float W[NMF_MAX_RANK * NMF_MAX_SKETCH];  // p x nu, row stride nu
-  float H[NMF_MAX_RANK * NMF_MAX_RANK];    // p x p, row stride p
-  float Lc;
-  int status;
-  double Lc_d;
-};
+constexpr int kMaxReduceFloats = 16384;  // per-CTA shared-memory budget for reducing the predecessor's partials
 
-__host__ __device__ inline int tail_groups(int ctas) { return ceil_div(ctas, kTailGroup); }
+// Group size of the epilogue partials: 1 (each CTA's partial is read by the
+// next kernel directly) unless ctas * P floats exceed the reduce budget, in
+// which case the last CTA of each group of `group` CTAs sums its group.
+inline int partial_group_size(int ctas, int P) {
+  const long total = (long)ctas * P;
+  return total <= kMaxReduceFloats ? 1 : (int)((total + kMaxReduceFloats - 1) / kMaxReduceFloats);
+}
+__host__ __device__ inline int group_count(int ctas, int group) { return ceil_div(ctas, group); }
 
 struct SolveArgs {
   int p, N, nu;
@@ -134,20 +133,24 @@ struct SolveArgs {
   const float* D;        // B_FROM_ROWS: N x nu; B_FROM_COLS: nu x N
   const float* Bpart;    // B_FROM_PARTIALS: [Bparts][N][Bld]
   int Bparts, Bld;
-  const Reduced* red_in; // W, H, L_c of this subproblem
+  // the predecessor's partials of W (compressed: p x nu) or H (plain: p x p)
+  const float* part_in;  // [groups_in][P]
+  int groups_in;
   // iteration
   int max_inner, min_inner;
-  bool stop_test;        // needs cooperative launch
+  bool stop_test;
   int side;              // 0 = G, 1 = F (stats slot)
   double* pg2_init;      // MODE_EVAL: per-CTA ||P grad(Y0)||^2
-  double* pg2_part;      // [kStopSlots + 1][ctas]: stop-test partials, then the final one
-  // epilogue: partial products for the next phase, reduced by the last CTA
+  double* pg2_part;      // [ctas]: ||P grad||^2 of the returned iterate, per CTA
+  unsigned long long* stop_slots;  // [kStopSlots][ctas * warps]: tagged stop-test partials (zeroed per call)
+  int epoch;             // distinct for every solve launch of one call (tags of stop_slots)
+  // epilogue: the next phase's W or Gram matrix, per CTA (and per group)
   int epi;               // Epilogue
   const float* E;        // EPI_W_ROWS: N x nu; EPI_W_COLS: nu x N
-  float* part_out;       // [ctas][p * (nu or p)]
-  float* group_out;      // [tail_groups(ctas)][p * (nu or p)]
-  unsigned int* tail_ctr;  // [tail_groups(ctas) + 1], zero, left zero
-  Reduced* red_out;
+  float* part_out;       // [ctas][P]
+  int group;             // partial_group_size(ctas, P)
+  float* group_out;      // [group_count(ctas, group)][P] when group > 1
+  unsigned int* tail_ctr;  // [group_count(ctas, group)], zero, left zero (group > 1)
   void* op_out;          // optional transposed operand NV x op_ld (float or bf16)
   int op_ld, op_bf16;
   float* record;         // optional snapshot: Y^T as N x p (G) or Y as p x N (F)
@@ -164,8 +167,9 @@ int solve_ctas(int N);
 // the inner loop. `beta` holds beta_k for k < max_inner.
 cudaError_t solve_launch_mode(const SolveArgs& a, const float* beta, int mode, cudaStream_t s);
 cudaError_t beta_launch(float* beta, int K, cudaStream_t s);
-// CTAs that can be co-resident for the solve kernel (cooperative launches).
-int solve_max_coresident(int p, int nu, int epi);
+// CTAs of the solve kernel that fit on the device at once (the stop test
+// needs every CTA of a launch resident).
+int solve_max_coresident(int p, int nu, int epi, int groups_in);
 // Sums final per-CTA partials into the stats struct (one thread).
 cudaError_t stats_launch(nenmf_stats_t* stats, const double* pg2_final_G, int ctasG,
                          const double* pg2_final_F, int ctasF, Control* ctrl, int outer, cudaStream_t s);

@@ -1,8 +1,15 @@
 // nesterov.cu -- the inner loop of NeNMF (Sec. 2) on the columns of a p x N
 // unknown Y, one column per thread, fused with what the loop needs:
 //
-// prologue  H, W and L_c of the subproblem, reduced by the previous kernel's
-//           tail (below); B of every column:
+// prologue  loads that do not depend on the previous kernel first (own
+//           factor, data and basis vectors), then griddepcontrol.wait
+//           (the kernel is launched as a programmatic dependent of the
+//           previous one, so this part overlaps its end); then every CTA sums
+//           the previous kernel's per-CTA partials of W (compressed: p x nu)
+//           or of the Gram matrix (plain) in a fixed order, forms H = W W^T
+//           and L_c = lambda_max(H) (one warp: repeated squaring of
+//           H / trace with trace renormalisation until the spectrum has
+//           collapsed to rank one, then a float64 Rayleigh quotient), and B:
 //             compressed (Alg. 1): B(:, j) = W d_j, d_j the j-th compressed
 //               data vector (G side: W = F_R = F R, d_j = row j of X_R;
 //               F side: W = G_L^T = (L G)^T, d_j = column j of X_L);
@@ -11,27 +18,26 @@
 //           Only the gradient at f is formed (H f - b); the gradient at the
 //           extrapolated y' follows by linearity,
 //           grad(y') = grad(f) + beta_k (grad(f) - grad(f_prev)).
-//           Optional stop test ||P grad(f_k)||_F <= eps: per-CTA float64
-//           partials, summed in a fixed order after all CTAs have published;
-//           the result of the test at iteration k is read at iteration
-//           k + kLag, so the cross-CTA wait overlaps compute, and the iterate
-//           f_k is kept until then (cooperative launch, bounded waits);
+//           Optional stop test ||P grad(f_k)||_F <= eps: every CTA publishes
+//           its partial as one tagged 64-bit word and every CTA sums all
+//           partials in the same fixed order; the result of the test at
+//           iteration k is read at iteration k + kLag, so the wait overlaps
+//           compute, and f_k is kept until then (bounded waits);
 // epilogue  the returned iterate is stored (and copied for the next X pass,
 //           the snapshot, the stats); the next phase's W (f times rows of R or
-//           columns of L) or Gram matrix f f^T is summed per CTA, then over
-//           groups of kTailGroup CTAs by the last CTA of each group, then over
-//           groups by the last group; that CTA forms H = W W^T and
-//           L_c = lambda_max(H) (one warp: repeated squaring of H / trace with
-//           the trace normalisation, stopping once the spectrum has collapsed
-//           to rank one, then a float64 Rayleigh quotient).
+//           columns of L) or Gram matrix f f^T is summed per CTA; for large
+//           grids the last CTA of each group also sums its group.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace nmf {
 namespace {
 
 constexpr int T = kSolveThreads;
-constexpr int kLag = 2;
+constexpr int kLag = 4;
 constexpr int kKeep = kLag + 1;
+static_assert(kStopSlots >= 2 * kLag + 1, "stop-test slots are reused after kStopSlots tests");
 constexpr int kMaxSquarings = 16;
 constexpr int kFs = T + 1;
 constexpr unsigned long long kWaitNs = 2000000000ull;
@@ -84,163 +90,252 @@ __device__ __forceinline__ float pg_sq(const float* f, const float* g) {
   return s;
 }
 
-// Waits (thread 0) until the stop-test arrival counter reaches `target`.
-__device__ __forceinline__ bool wait_arrivals(Control* c, unsigned int target) {
-  __shared__ int ok;
-  if (threadIdx.x == 0) {
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(c->bar_count);
-    cuda::atomic_ref<int, cuda::thread_scope_device> abrt(c->abort);
-    int good = 1;
-    const unsigned long long t0 = global_ns();
-    while (cnt.load(cuda::memory_order_acquire) < target) {
-      if (abrt.load(cuda::memory_order_relaxed)) { good = 0; break; }
+// Stop-test slots: one 64-bit word per warp and test, (tag << 32) | float
+// bits of the warp's ||P grad||^2. A single relaxed 64-bit store publishes
+// both, so no fence or counter is needed. Every warp of every CTA then reads
+// all words of the test, waits for their tags, and sums them in float-float
+// in one fixed order, so all warps reach the same decision without any
+// block-level synchronisation. Tags carry the launch epoch, so words left by
+// earlier launches of the same call never match.
+constexpr int kWarps = T / 32;
+
+__device__ __forceinline__ uint32_t stop_tag(int epoch, int j) { return ((uint32_t)epoch << 16) | (uint32_t)(j + 1); }
+
+__device__ __forceinline__ void publish_warp(unsigned long long* slots, int j, int epoch, float v) {
+  const int nw = gridDim.x * kWarps;
+  const int wi = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const unsigned long long w = ((unsigned long long)stop_tag(epoch, j) << 32) | (unsigned long long)__float_as_uint(v);
+  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(slots[(size_t)(j % kStopSlots) * nw + wi]);
+  r.store(w, cuda::memory_order_relaxed);
+}
+
+// Returns false on timeout or abort; *total is valid in every lane.
+__device__ __forceinline__ bool collect_warp(const unsigned long long* slots, int j, int epoch, Control* c,
+                                             double* total) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * kWarps;
+  const uint32_t tag = stop_tag(epoch, j);
+  const unsigned long long* sl = slots + (size_t)(j % kStopSlots) * nw;
+  DF s{0.f, 0.f};
+  int good = 1;
+  const unsigned long long t0 = global_ns();
+  for (int i = lane; i < nw && good; i += 32) {
+    cuda::atomic_ref<const unsigned long long, cuda::thread_scope_device> r(sl[i]);
+    unsigned long long w = r.load(cuda::memory_order_relaxed);
+    while ((uint32_t)(w >> 32) != tag) {
+      if (*((volatile int*)&c->abort)) { good = 0; break; }
       if (global_ns() - t0 > kWaitNs) {
         set_status(c, NMF_ERR_DEVICE_TIMEOUT);
-        abrt.store(1, cuda::memory_order_relaxed);
+        *((volatile int*)&c->abort) = 1;
         good = 0;
         break;
       }
-      __nanosleep(20);
+      w = r.load(cuda::memory_order_relaxed);
     }
-    ok = good;
+    df_add(s, __uint_as_float((uint32_t)w), 0.f);
   }
-  __syncthreads();
-  return ok != 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float hi = __shfl_xor_sync(0xffffffffu, s.hi, o);
+    const float lo = __shfl_xor_sync(0xffffffffu, s.lo, o);
+    // the pair sum is formed in the same order in both lanes (lower lane first)
+    DF a = (lane & o) ? DF{hi, lo} : s;
+    const DF b = (lane & o) ? s : DF{hi, lo};
+    df_add(a, b.hi, b.lo);
+    s = a;
+  }
+  *total = (double)s.hi + (double)s.lo;
+  return __all_sync(0xffffffffu, good) != 0;
 }
 
-// lambda_max of the symmetric PSD p x p matrix H (row stride p) in shared
-// memory, by the whole CTA: repeated squaring of M = H / trace(H) with the
-// trace renormalised each time, until trace(M^2) = 1 (rank one), then the
-// float64 Rayleigh quotient of M's dominant column. M0, M1: PM x PM scratch.
-// Returns 0 for H = 0 and a non-finite value for a non-finite H.
+// lambda_max of the symmetric PSD p x p matrix H (row stride p, shared
+// memory), by one warp: lane c holds row c of M = H / trace(H) in registers;
+// M is squared (row c of M^2 = sum_k M[c][k] row_k, row_k fetched by shuffles)
+// and renormalised to trace one until trace(M^2) reaches 1 (rank one), then
+// the float64 Rayleigh quotient of M's dominant column. Call with all 32
+// lanes of one warp; the result is valid in every lane. Returns 0 for H = 0
+// and a non-finite value for a non-finite H.
 template <int PM>
-__device__ double lambda_max_block(const float* H, int p, float* M0, float* M1, double* red) {
-  __shared__ float tr_s;
-  __shared__ double lam_s;
-  const int tid = threadIdx.x;
-  if (tid < 32) {
-    double tr = 0.0;
-    for (int c = tid; c < p; c += 32) tr += (double)H[c * p + c];
-    tr = warp_sum(tr);
-    if (tid == 0) red[0] = tr;
-  }
-  __syncthreads();
-  const double tr = red[0];
-  __syncthreads();
+__device__ double lambda_max_warp(const float* H, int p) {
+  const int lane = threadIdx.x & 31;
+  double tr = 0.0;
+  for (int c = lane; c < p; c += 32) tr += (double)H[c * p + c];
+  tr = warp_sum(tr);
   if (!(tr > 0.0) || !isfinite(tr)) return isfinite(tr) ? 0.0 : tr;
   const float inv = (float)(1.0 / tr);
-  for (int i = tid; i < PM * PM; i += T) {
-    const int c = i / PM, d = i % PM;
-    M0[i] = (c < p && d < p) ? H[c * p + d] * inv : 0.f;
-  }
-  __syncthreads();
-  float* M = M0;
-  float* M2 = M1;
-  for (int s = 0; s < kMaxSquarings; ++s) {
-    for (int i = tid; i < PM * PM; i += T) {
-      const int c = i / PM, d = i % PM;
-      float v = 0.f;
+  float row[PM];
 #pragma unroll
-      for (int k = 0; k < PM; ++k) v = fmaf(M[c * PM + k], M[k * PM + d], v);
-      M2[i] = v;
+  for (int d = 0; d < PM; ++d) row[d] = (lane < p && d < p) ? H[lane * p + d] * inv : 0.f;
+  for (int s = 0; s < kMaxSquarings; ++s) {
+    float nr[PM];
+#pragma unroll
+    for (int d = 0; d < PM; ++d) nr[d] = 0.f;
+#pragma unroll
+    for (int k = 0; k < PM; ++k) {
+      const float mck = row[k];
+#pragma unroll
+      for (int d = 0; d < PM; ++d) nr[d] = fmaf(mck, __shfl_sync(0xffffffffu, row[d], k), nr[d]);
     }
-    __syncthreads();
-    if (tid < 32) {
-      const float t = warp_sum(tid < PM ? M2[tid * PM + tid] : 0.f);
-      if (tid == 0) tr_s = t;
-    }
-    __syncthreads();
-    const float t2 = tr_s;
-    if (t2 > 0.f) {
-      const float it = 1.f / t2;
-      for (int i = tid; i < PM * PM; i += T) M2[i] *= it;
-    }
-    __syncthreads();
-    float* tmp = M;
-    M = M2;
-    M2 = tmp;
+    float diag = 0.f;
+#pragma unroll
+    for (int d = 0; d < PM; ++d) diag = (d == lane) ? nr[d] : diag;
+    const float t2 = warp_sum(diag);
+    const float it = t2 > 0.f ? 1.f / t2 : 0.f;
+#pragma unroll
+    for (int d = 0; d < PM; ++d) row[d] = nr[d] * it;
     // trace(M^2) of a trace-one M equals 1 exactly when M has rank one; at
     // 1 - trace(M^2) < 1e-5 the other eigenvectors' share in the chosen
     // column is < 1e-5, so the Rayleigh quotient is exact to ~1e-10.
     if (!(t2 > 0.f) || 1.f - t2 < 1e-5f) break;
   }
-  if (tid < 32) {
-    int jb = 0;
-    for (int c = 1; c < PM; ++c)
-      if (M[c * PM + c] > M[jb * PM + jb]) jb = c;
-    double hv = 0.0, vc = 0.0;
-    if (tid < p) {
-      vc = (double)M[tid * PM + jb];
-      for (int d = 0; d < p; ++d) hv = fma((double)H[tid * p + d], (double)M[d * PM + jb], hv);
+  // dominant column jb = argmax diag(M); v_c = M[c][jb] = row[jb] of lane c
+  float diag = 0.f;
+#pragma unroll
+  for (int d = 0; d < PM; ++d) diag = (d == lane) ? row[d] : diag;
+  float best = diag;
+  int jb = lane;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
+    if (ob > best || (ob == best && oj < jb)) {
+      best = ob;
+      jb = oj;
     }
-    const double num = warp_sum(vc * hv), den = warp_sum(vc * vc);
-    if (tid == 0) lam_s = den > 0.0 ? num / den : 0.0;
   }
-  __syncthreads();
-  return lam_s;
+  float vc = 0.f;
+#pragma unroll
+  for (int d = 0; d < PM; ++d) vc = (d == jb) ? row[d] : vc;
+  if (lane >= p) vc = 0.f;
+  double hv = 0.0;
+  for (int d = 0; d < p; ++d) {
+    const float vd = __shfl_sync(0xffffffffu, vc, d);
+    if (lane < p) hv = fma((double)H[lane * p + d], (double)vd, hv);
+  }
+  const double num = warp_sum((double)vc * hv), den = warp_sum((double)vc * (double)vc);
+  return den > 0.0 ? num / den : 0.0;
 }
 
-// Fixed-order total of the stop-test partials of test j (warp 0 sums; all read flag).
-__device__ __forceinline__ void test_total(const double* pg2_part, int j, int ctas, double eps2, double* tot,
-                                           int* flag) {
-  if (threadIdx.x < 32) {
-    double t = 0.0;
-    const double* sl = pg2_part + (size_t)(j % kStopSlots) * ctas;
-    for (int i = threadIdx.x; i < ctas; i += 32) t += __ldcg(sl + i);
-    t = warp_sum(t);
-    if (threadIdx.x == 0) {
-      *tot = t;
-      *flag = t <= eps2;
-    }
-  }
-  __syncthreads();
-}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
 
 template <int PM>
 __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
   const SolveArgs& a = kp.a;
   Control* ctrl = a.ctrl;
-  if (call_failed(ctrl)) return;
   const int p = a.p, nu = a.nu, N = a.N;
   const int tid = threadIdx.x;
   const int cta = blockIdx.x;
   const int ctas = gridDim.x;
   const int col = cta * T + tid;
   const bool active = col < N;
+  const int c0 = cta * T;
+  const int cols = min(T, N - c0);
+  const bool gram = a.bsrc == B_FROM_PARTIALS;  // plain mode: H comes reduced, no W
 
   __shared__ __align__(16) float Hs[PM * PM];
   __shared__ float Ws[PM * NMF_MAX_SKETCH];
   __shared__ double red[T / 32];
   __shared__ int flag_s;
-  __shared__ double tot_s;
+  __shared__ double lam_s;
   extern __shared__ __align__(16) float dyn[];
+  const bool epiW = a.epi == EPI_W_ROWS || a.epi == EPI_W_COLS;
+  const bool stageD = kp.mode != MODE_EPI_ONLY && !gram;
+  const int vecF = round_up(nu * kFs, 4);            // sub-buffers start on 16-byte boundaries
+  float* Es = dyn;                                   // [nu][kFs]: basis vectors of the epilogue
+  float* Ds = Es + (epiW ? vecF : 0);                // [nu][kFs]: data vectors of B
+  float* scratch = Ds + (stageD ? vecF : 0);         // partial sums, pending iterates, epilogue
 
+  // ---- independent of the previous kernel ----
   float y[PM], b[PM], f[PM];
 #pragma unroll
   for (int c = 0; c < PM; ++c) {
     y[c] = (active && c < p) ? a.Y[(size_t)c * N + col] : 0.f;
     b[c] = 0.f;
   }
+  if (a.epi == EPI_W_ROWS) {
+    const float* src = a.E + (size_t)c0 * nu;
+    for (int i = tid; i < T * nu; i += T) {
+      const int t = i / nu, k = i % nu;
+      Es[k * kFs + t] = t < cols ? __ldg(src + i) : 0.f;
+    }
+  } else if (a.epi == EPI_W_COLS) {
+    for (int i = tid; i < nu * T; i += T) {
+      const int k = i / T, t = i % T;
+      Es[k * kFs + t] = t < cols ? __ldg(a.E + (size_t)k * N + c0 + t) : 0.f;
+    }
+  }
+  if (stageD) {
+    if (a.bsrc == B_FROM_ROWS) {
+      const float* src = a.D + (size_t)c0 * nu;
+      for (int i = tid; i < T * nu; i += T) {
+        const int t = i / nu, k = i % nu;
+        Ds[k * kFs + t] = t < cols ? __ldg(src + i) : 0.f;
+      }
+    } else {
+      for (int i = tid; i < nu * T; i += T) {
+        const int k = i / T, t = i % T;
+        Ds[k * kFs + t] = t < cols ? __ldg(a.D + (size_t)k * N + c0 + t) : 0.f;
+      }
+    }
+  }
+
+  // ---- everything below may read what the previous kernel wrote ----
+  pdl_wait();
+  if (call_failed(ctrl)) return;
+  pdl_launch_dependents();
 
   int iters = 0;
   float Lc = 0.f;
   double Lc_d = 0.0;
   if (kp.mode != MODE_EPI_ONLY) {
-    const Reduced* R = a.red_in;
-    for (int i = tid; i < PM * PM; i += T) {
-      const int c = i / PM, d = i % PM;
-      Hs[i] = (c < p && d < p) ? R->H[c * p + d] : 0.f;
+    // Sum of the predecessor's partials, in a fixed order (same in every CTA).
+    const int P = gram ? p * p : p * nu;
+    const int G = a.groups_in;
+    float* Ps = scratch;  // [G][P]
+    {
+      const int total = G * P;
+      const float4* src4 = reinterpret_cast<const float4*>(a.part_in);
+      for (int i = tid; i < total / 4; i += T) reinterpret_cast<float4*>(Ps)[i] = __ldcg(src4 + i);
+      for (int i = (total / 4) * 4 + tid; i < total; i += T) Ps[i] = __ldcg(a.part_in + i);
     }
-    if (a.bsrc != B_FROM_PARTIALS)
+    __syncthreads();
+    float* Rw = Ps + round_up(G * P, 4);  // the reduced W (or H)
+    for (int o = tid; o < P; o += T) {
+      float s = 0.f;
+      for (int g = 0; g < G; ++g) s += Ps[(size_t)g * P + o];
+      Rw[o] = s;
+    }
+    __syncthreads();
+    if (gram) {
+      for (int i = tid; i < PM * PM; i += T) {
+        const int c = i / PM, d = i % PM;
+        Hs[i] = (c < p && d < p) ? Rw[c * p + d] : 0.f;
+      }
+    } else {
       for (int i = tid; i < PM * nu; i += T) {
         const int c = i / nu, k = i % nu;
-        Ws[c * NMF_MAX_SKETCH + k] = c < p ? R->W[c * nu + k] : 0.f;
+        Ws[c * NMF_MAX_SKETCH + k] = c < p ? Rw[c * nu + k] : 0.f;
       }
-    Lc = R->Lc;
-    Lc_d = R->Lc_d;
+      __syncthreads();
+      for (int i = tid; i < PM * PM; i += T) {
+        const int c = i / PM, d = i % PM;
+        float s = 0.f;
+        for (int k = 0; k < nu; ++k) s = fmaf(Ws[c * NMF_MAX_SKETCH + k], Ws[d * NMF_MAX_SKETCH + k], s);
+        Hs[i] = s;
+      }
+    }
     __syncthreads();
+    // L_c by warp 0 while the other warps form B.
+    if (kp.mode == MODE_SOLVE && tid < 32) {
+      float* Hp = Rw + P;  // H compacted to p x p for the eigenvalue routine
+      for (int i = tid; i < p * p; i += 32) Hp[i] = Hs[(i / p) * PM + i % p];
+      __syncwarp();
+      const double lam = lambda_max_warp<PM>(Hp, p);
+      if (tid == 0) lam_s = lam;
+    }
     if (active) {
-      if (a.bsrc == B_FROM_PARTIALS) {
+      if (gram) {
         // B(:, col) = sum over the X pass partials; a whole row of partials
         // per q, so the loads of all c are in flight together.
         for (int q = 0; q < a.Bparts; ++q) {
@@ -249,35 +344,22 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
           for (int c = 0; c < PM; ++c)
             if (c < p) b[c] += __ldcg(bp + c);
         }
-      }
-    }
-    if (a.bsrc != B_FROM_PARTIALS) {
-      // The CTA's T data vectors go through shared memory: Ds[k][t] for k < nu.
-      // Rows of X_R (N x nu) are contiguous for the whole CTA; columns of X_L
-      // (nu x N) are coalesced per k. Loads are independent, so they overlap.
-      float* Ds = dyn;
-      const int c0 = cta * T;
-      const int cols = min(T, N - c0);
-      if (a.bsrc == B_FROM_ROWS) {
-        const float* src = a.D + (size_t)c0 * nu;
-        for (int i = tid; i < cols * nu; i += T) {
-          const int t = i / nu, k = i % nu;
-          Ds[k * kFs + t] = __ldg(src + i);
-        }
       } else {
-        for (int i = tid; i < nu * T; i += T) {
-          const int k = i / T, t = i % T;
-          Ds[k * kFs + t] = t < cols ? __ldg(a.D + (size_t)k * N + c0 + t) : 0.f;
-        }
-      }
-      __syncthreads();
-      if (active)
         for (int k = 0; k < nu; ++k) {
           const float dk = Ds[k * kFs + tid];
 #pragma unroll
           for (int c = 0; c < PM; ++c) b[c] = fmaf(Ws[c * NMF_MAX_SKETCH + k], dk, b[c]);
         }
-      __syncthreads();  // dyn is reused below
+      }
+    }
+    __syncthreads();
+    if (kp.mode == MODE_SOLVE) {
+      Lc_d = lam_s;
+      if (!isfinite(Lc_d)) {
+        if (tid == 0) set_status(ctrl, NMF_ERR_NONFINITE);
+        Lc_d = 0.0;
+      }
+      Lc = (float)Lc_d;
     }
   }
 
@@ -298,11 +380,13 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
       fp[c] = y[c];
       gp[c] = g[c];
     }
-    float* keep = dyn;  // [kKeep][PM][T]: iterates whose stop test is pending
+    float* keep = scratch;  // [kKeep][PM][T]: iterates whose stop test is pending (per thread)
     const float inv_Lc = 1.f / Lc;
     const bool test = a.stop_test;
     const double eps2 = ctrl->eps2;
     int tests = 0, stop_j = -1;
+    double tot = 0.0;
+    bool aborted = false;
     for (int k = 0; k < a.max_inner; ++k) {
 #pragma unroll
       for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
@@ -318,44 +402,39 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
       }
       iters = k + 1;
       if (test && k + 1 >= a.min_inner) {
-        const double s = block_sum_double(active ? (double)pg_sq<PM>(f, gf) : 0.0, red);
-        if (tid == 0) {
-          a.pg2_part[(size_t)(tests % kStopSlots) * ctas + cta] = s;
-          __threadfence();
-          atomicAdd(&ctrl->bar_count, 1u);
-        }
+        const float ws = warp_sum(active ? pg_sq<PM>(f, gf) : 0.f);
+        if ((tid & 31) == 0) publish_warp(a.stop_slots, tests, a.epoch, ws);
         float* slot = keep + (size_t)(tests % kKeep) * PM * T;
 #pragma unroll
         for (int c = 0; c < PM; ++c) slot[c * T + tid] = f[c];
         ++tests;
         if (tests > kLag) {
           const int j = tests - 1 - kLag;
-          if (!wait_arrivals(ctrl, (unsigned int)(j + 1) * ctas)) return;
-          test_total(a.pg2_part, j, ctas, eps2, &tot_s, &flag_s);
-          if (flag_s) {
+          if (!collect_warp(a.stop_slots, j, a.epoch, ctrl, &tot)) { aborted = true; break; }
+          if (tot <= eps2) {
             stop_j = j;
             break;
           }
         }
       }
     }
-    if (test && stop_j < 0) {
+    if (test && stop_j < 0 && !aborted) {
       // tests still pending when the loop ended, in order
       for (int j = tests > kLag ? tests - kLag : 0; j < tests; ++j) {
-        if (!wait_arrivals(ctrl, (unsigned int)(j + 1) * ctas)) return;
-        test_total(a.pg2_part, j, ctas, eps2, &tot_s, &flag_s);
-        if (flag_s) {
+        if (!collect_warp(a.stop_slots, j, a.epoch, ctrl, &tot)) { aborted = true; break; }
+        if (tot <= eps2) {
           stop_j = j;
           break;
         }
       }
     }
+    if (__syncthreads_or(aborted)) return;
     if (stop_j >= 0) {
       const float* slot = keep + (size_t)(stop_j % kKeep) * PM * T;
 #pragma unroll
       for (int c = 0; c < PM; ++c) f[c] = slot[c * T + tid];
       iters = a.min_inner + stop_j;
-      pg2_final = cta == 0 ? tot_s : 0.0;  // the total is global: CTA 0 carries it
+      pg2_final = cta == 0 ? tot : 0.0;  // the total is global: CTA 0 carries it
     } else {
       pg2_final = block_sum_double(active ? (double)pg_sq<PM>(fp, gp) : 0.0, red);  // thread 0
     }
@@ -388,21 +467,24 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
         else static_cast<float*>(a.op_out)[(size_t)c * a.op_ld + col] = f[c];
       }
   }
-  if (kp.mode == MODE_SOLVE && tid == 0 && a.pg2_part) a.pg2_part[(size_t)kStopSlots * ctas + cta] = pg2_final;
+  if (kp.mode == MODE_SOLVE && tid == 0 && a.pg2_part) a.pg2_part[cta] = pg2_final;
+  if (kp.mode == MODE_SOLVE && cta == 0 && tid == 0) {
+    ctrl->iters[a.side] = iters;
+    ctrl->lipschitz[a.side] = Lc;
+    if (a.stats) {
+      a.stats->last_inner[a.side] = iters;
+      a.stats->total_inner[a.side] += iters;
+      a.stats->lipschitz[a.side] = Lc_d;
+    }
+  }
 
-  // ---- epilogue: the next phase's W or Gram matrix ----
+  // ---- epilogue: this CTA's share of the next phase's W or Gram matrix ----
   if (a.epi != EPI_NONE) {
-    __syncthreads();  // dyn (keep) is reused
+    __syncthreads();  // scratch (pending iterates) is reused
     const int P = a.epi == EPI_GRAM ? p * p : p * nu;
-    float* Fs = dyn;             // [PM][kFs]
-    float* Es = dyn + PM * kFs;  // [nu][kFs]
+    float* Fs = scratch;  // [PM][kFs]
 #pragma unroll
     for (int c = 0; c < PM; ++c) Fs[c * kFs + tid] = active ? f[c] : 0.f;
-    if (a.epi == EPI_W_ROWS) {
-      for (int k = 0; k < nu; ++k) Es[k * kFs + tid] = active ? a.E[(size_t)col * nu + k] : 0.f;
-    } else if (a.epi == EPI_W_COLS) {
-      for (int k = 0; k < nu; ++k) Es[k * kFs + tid] = active ? a.E[(size_t)k * N + col] : 0.f;
-    }
     __syncthreads();
     const float* Os = a.epi == EPI_GRAM ? Fs : Es;
     const int ow = a.epi == EPI_GRAM ? p : nu;
@@ -412,73 +494,23 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
       for (int t = 0; t < T; ++t) s = fmaf(Fs[c * kFs + t], Os[k * kFs + t], s);
       a.part_out[(size_t)cta * P + o] = s;
     }
-    // tail: the last CTA of each group sums the group, the last group sums all
-    __threadfence();
-    __syncthreads();
-    const int ngroups = tail_groups(ctas);
-    const int gi = cta / kTailGroup;
-    const int gsz = min(kTailGroup, ctas - gi * kTailGroup);
-    if (tid == 0) flag_s = atomicAdd(&a.tail_ctr[1 + gi], 1u) == (unsigned int)(gsz - 1);
-    __syncthreads();
-    if (flag_s) {
-      __threadfence();
-      for (int o = tid; o < P; o += T) {
-        float s = 0.f;
-        for (int i = 0; i < gsz; ++i) s += __ldcg(a.part_out + (size_t)(gi * kTailGroup + i) * P + o);
-        a.group_out[(size_t)gi * P + o] = s;
-      }
+    if (a.group > 1) {
+      // large grids: the last CTA of each group sums the group's partials
       __threadfence();
       __syncthreads();
-      if (tid == 0) {
-        a.tail_ctr[1 + gi] = 0u;
-        flag_s = atomicAdd(&a.tail_ctr[0], 1u) == (unsigned int)(ngroups - 1);
-      }
+      const int gi = cta / a.group;
+      const int gsz = min(a.group, ctas - gi * a.group);
+      if (tid == 0) flag_s = atomicAdd(&a.tail_ctr[gi], 1u) == (unsigned int)(gsz - 1);
       __syncthreads();
       if (flag_s) {
         __threadfence();
-        float* Rw = dyn;                                  // P
-        float* Rh = dyn + NMF_MAX_RANK * NMF_MAX_SKETCH;  // p x p
-        float* M0 = Rh + NMF_MAX_RANK * NMF_MAX_RANK;
-        float* M1 = M0 + PM * PM;
         for (int o = tid; o < P; o += T) {
           float s = 0.f;
-          for (int i = 0; i < ngroups; ++i) s += __ldcg(a.group_out + (size_t)i * P + o);
-          Rw[o] = s;
+          for (int i = 0; i < gsz; ++i) s += __ldcg(a.part_out + (size_t)(gi * a.group + i) * P + o);
+          a.group_out[(size_t)gi * P + o] = s;
         }
-        __syncthreads();
-        if (a.epi == EPI_GRAM) {
-          for (int o = tid; o < p * p; o += T) Rh[o] = Rw[o];
-        } else {
-          for (int o = tid; o < p * p; o += T) {
-            const int c = o / p, d = o % p;
-            float s = 0.f;
-            for (int k = 0; k < nu; ++k) s = fmaf(Rw[c * nu + k], Rw[d * nu + k], s);
-            Rh[o] = s;
-          }
-        }
-        __syncthreads();
-        Reduced* out = a.red_out;
-        for (int o = tid; o < p * p; o += T) out->H[o] = Rh[o];
-        if (a.epi != EPI_GRAM)
-          for (int o = tid; o < P; o += T) out->W[o] = Rw[o];
-        const double lam = lambda_max_block<PM>(Rh, p, M0, M1, red);
-        if (tid == 0) {
-          out->Lc_d = lam;
-          out->Lc = isfinite(lam) ? (float)lam : 0.f;
-          if (!isfinite(lam)) set_status(ctrl, NMF_ERR_NONFINITE);
-          a.tail_ctr[0] = 0u;
-          ctrl->bar_count = 0u;  // every CTA is past its stop-test waits
-        }
+        if (tid == 0) a.tail_ctr[gi] = 0u;
       }
-    }
-  }
-  if (kp.mode == MODE_SOLVE && cta == 0 && tid == 0) {
-    ctrl->iters[a.side] = iters;
-    ctrl->lipschitz[a.side] = Lc;
-    if (a.stats) {
-      a.stats->last_inner[a.side] = iters;
-      a.stats->total_inner[a.side] += iters;
-      a.stats->lipschitz[a.side] = Lc_d;
     }
   }
   if (a.time_out) {
@@ -492,16 +524,18 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
 
 template <int PM>
 size_t dyn_smem(const SolveArgs& a, int mode) {
-  const size_t keep = (mode == MODE_SOLVE && a.stop_test) ? (size_t)kKeep * PM * T : 0;
-  size_t stage = (mode != MODE_EPI_ONLY && a.bsrc != B_FROM_PARTIALS) ? (size_t)a.nu * kFs : 0;
-  if (a.epi != EPI_NONE) {
-    const int erows = a.epi == EPI_GRAM ? 0 : a.nu;
-    const size_t st = (size_t)(PM + erows) * kFs;
-    const size_t tail = NMF_MAX_RANK * NMF_MAX_SKETCH + NMF_MAX_RANK * NMF_MAX_RANK + 2 * PM * PM;
-    if (st > stage) stage = st;
-    if (tail > stage) stage = tail;
+  const bool epiW = a.epi == EPI_W_ROWS || a.epi == EPI_W_COLS;
+  const bool gram = a.bsrc == B_FROM_PARTIALS;
+  const bool stageD = mode != MODE_EPI_ONLY && !gram;
+  size_t scratch = 0;
+  if (mode != MODE_EPI_ONLY) {
+    const size_t P = gram ? (size_t)a.p * a.p : (size_t)a.p * a.nu;
+    scratch = round_up_sz((size_t)a.groups_in * P, 4) + 2 * P;  // partials, the sum, and H compacted
   }
-  return (keep > stage ? keep : stage) * sizeof(float);
+  if (mode == MODE_SOLVE && a.stop_test) scratch = std::max(scratch, (size_t)kKeep * PM * T);
+  if (a.epi != EPI_NONE) scratch = std::max(scratch, (size_t)PM * kFs);
+  const size_t vecF = round_up_sz((size_t)a.nu * kFs, 4);
+  return ((epiW ? vecF : 0) + (stageD ? vecF : 0) + scratch) * sizeof(float);
 }
 
 template <int PM>
@@ -516,15 +550,13 @@ cudaError_t launch_pm(const KParams& kp, cudaStream_t s) {
   cfg.blockDim = dim3(T);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
+  // Programmatic dependent launch: the kernel starts while its predecessor
+  // finishes and waits (griddepcontrol.wait) before touching its outputs.
   cudaLaunchAttribute attr[1];
-  int nattr = 0;
-  if (kp.mode == MODE_SOLVE && a.stop_test) {
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    nattr = 1;
-  }
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = nattr;
+  cfg.numAttrs = 1;
   count_launches(1);
   return cudaLaunchKernelEx(&cfg, solve_kernel<PM>, kp);
 }
@@ -621,7 +653,7 @@ cudaError_t eps_launch(Control* ctrl, const double* pgG, int cG, const double* p
   return cudaGetLastError();
 }
 
-int solve_max_coresident(int p, int nu, int epi) {
+int solve_max_coresident(int p, int nu, int epi, int groups_in) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -630,7 +662,8 @@ int solve_max_coresident(int p, int nu, int epi) {
   a.nu = nu;
   a.epi = epi;
   a.stop_test = true;
-  a.bsrc = B_FROM_ROWS;
+  a.bsrc = epi == EPI_GRAM ? B_FROM_PARTIALS : B_FROM_ROWS;
+  a.groups_in = groups_in;
   int per = 0;
   switch (pad_rank(p)) {
     case 4: per = occupancy_pm<4>(dyn_smem<4>(a, MODE_SOLVE)); break;
