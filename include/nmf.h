@@ -212,6 +212,37 @@ size_t nmf_rre_workspace_size(int n, int m, int p);
 nmf_status_t nmf_rre(nmf_stream_t stream, int n, int m, int p, const float* X, const float* G,
                      const float* F, double* out, void* workspace, size_t workspace_bytes);
 
+/* ------------------------------------------------------------------------ */
+/* Relative reconstruction error without a caller workspace                   */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory. Examples: a hook that evaluates the fit
+ * between solver calls inside a framework that owns all device memory
+ * through its own pool, code running while a stream is being captured into a
+ * CUDA graph (where a cudaMalloc would break or be barred from the capture),
+ * or a loop that must not call cudaMalloc because it can synchronise the
+ * device. Such callers still pass X, G, F and `out`, but no workspace.
+ *
+ * Same result as nmf_rre (same kernels, same fixed summation order). The
+ * per-block partial sums live in one fixed array inside the library
+ * (2 x NMF_RRE_STATIC_MAX_PARTS doubles, 1 MiB), which every GPU that loads
+ * the library keeps until the process exits.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress) with the device current; make that first call
+ *    before starting any stream capture.
+ *  - All calls share the array: calls that can overlap on the GPU (other
+ *    streams, other host threads) race and must be serialised by the caller.
+ *  - Every partial is written before it is read, so nothing has to start at
+ *    zero; the array keeps the last call's contents.
+ *  - Sizes needing more than NMF_RRE_STATIC_MAX_PARTS blocks, where blocks =
+ *    ceil(m / 256) * ceil(n / 64), return NMF_ERR_WORKSPACE before anything
+ *    is enqueued.
+ */
+#define NMF_RRE_STATIC_MAX_PARTS 65536
+nmf_status_t nmf_rre_static(nmf_stream_t stream, int n, int m, int p, const float* X, const float* G,
+                            const float* F, double* out);
+
 #ifdef __cplusplus
 }
 #endif

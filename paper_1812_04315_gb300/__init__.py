@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
         "nmf_dual_product": (i, [vp, i, i, i, i, vp, vp, vp, vp, vp, vp, sz]),
         "nmf_set_kernel_path": (None, [i]),
         "nmf_kernel_launches": (ctypes.c_longlong, []),
+        "nmf_rre_static": (i, [vp, i, i, i, vp, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -93,7 +94,7 @@ def exported_symbols():
     return ["nmf_status_string", "nmf_version", "nmf_workspace_status", "nmf_gaussian_sketch",
             "nmf_compress_workspace_size", "nmf_compress", "nenmf_solve_workspace_size", "nenmf_solve",
             "nmf_rre_workspace_size", "nmf_rre", "nmf_dual_product_workspace_size", "nmf_dual_product",
-            "nmf_set_kernel_path", "nmf_kernel_launches"]
+            "nmf_set_kernel_path", "nmf_kernel_launches", "nmf_rre_static"]
 
 
 # ---------------------------------------------------------------------------

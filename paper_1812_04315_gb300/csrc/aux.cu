@@ -1,6 +1,8 @@
 // aux.cu -- small kernels around the hot path: Gaussian sketches (Alg. 2,
 // "Draw Gaussian random matrices"), the one-time bfloat16 copy of X, layout
 // changes, timestamps, and the RRE of eq. (4).
+#include <mutex>
+
 #include "internal.h"
 
 namespace nmf {
@@ -235,3 +237,39 @@ cudaError_t rre_launch(int n, int m, int p, const float* X, const float* G, cons
 }
 
 }  // namespace nmf
+
+// ---------------------------------------------------------------------------
+// nmf_rre_static: nmf_rre with its partial sums in a fixed device array
+// instead of a caller workspace (for callers that cannot allocate).
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_rre_static_scratch[2 * NMF_RRE_STATIC_MAX_PARTS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_rre_static_mu;
+double* g_rre_static_ptr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" nmf_status_t nmf_rre_static(nmf_stream_t stream, int n, int m, int p, const float* X, const float* G,
+                                       const float* F, double* out) {
+  if (n < 1 || m < 1 || p < 1 || p > NMF_MAX_RANK || !X || !G || !F || !out) return NMF_ERR_INVALID_ARG;
+  const int parts = nmf::rre_parts(n, m);
+  if (parts > NMF_RRE_STATIC_MAX_PARTS) return NMF_ERR_WORKSPACE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NMF_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return NMF_ERR_UNSUPPORTED;
+  double* scratch = nullptr;
+  {
+    // Host code cannot use the array's name as a device address: look the
+    // address up once per device, with that device current.
+    std::lock_guard<std::mutex> lock(g_rre_static_mu);
+    if (!g_rre_static_ptr[dev]) {
+      void* addr = nullptr;
+      if (cudaGetSymbolAddress(&addr, g_rre_static_scratch) != cudaSuccess || addr == nullptr) return NMF_ERR_CUDA;
+      g_rre_static_ptr[dev] = static_cast<double*>(addr);
+    }
+    scratch = g_rre_static_ptr[dev];
+  }
+  if (nmf::rre_launch(n, m, p, X, G, F, out, scratch, parts, (cudaStream_t)stream) != cudaSuccess) return NMF_ERR_CUDA;
+  return NMF_OK;
+}
