@@ -194,7 +194,7 @@ nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16
 // ----------------------------------------------------------------------------
 // nenmf_solve workspace
 // ----------------------------------------------------------------------------
-constexpr int kMaxInner = 4096;
+constexpr int kMaxInner = kMaxInnerIters;
 
 struct SolveWs {
   Control* ctrl;
@@ -211,7 +211,7 @@ struct SolveWs {
   int nctr;
   double* pg2G;    // [ctasG]
   double* pg2F;
-  unsigned long long* slots;  // stop-test slots: G side [kStopSlots][ctasG], then F side
+  unsigned long long* slots;  // stop-test words: G side [kMaxInnerIters][ctasG], then F side
   double* initG;   // [ctasG]
   double* initF;   // [ctasF]
   __nv_bfloat16* Xb;
@@ -249,7 +249,7 @@ SolveWs carve_solve(void* base, const nenmf_problem_t& pr) {
   w.ctr = cv.take<unsigned int>(w.nctr);
   w.pg2G = cv.take<double>(w.ctasG);
   w.pg2F = cv.take<double>(w.ctasF);
-  w.slots = cv.take<unsigned long long>((size_t)kStopSlots * kSolveWarps * (w.ctasG + w.ctasF));
+  w.slots = cv.take<unsigned long long>((size_t)kMaxInnerIters * (w.ctasG + w.ctasF));
   w.initG = cv.take<double>(w.ctasG);
   w.initF = cv.take<double>(w.ctasF);
   if (plain) {
@@ -466,8 +466,12 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
 
   NMF_CU(cudaMemsetAsync(ctrl, 0, sizeof(Control), s));
   NMF_CU(cudaMemsetAsync(w.ctr, 0, sizeof(unsigned int) * w.nctr, s));
-  if (test)
-    NMF_CU(cudaMemsetAsync(w.slots, 0, sizeof(unsigned long long) * kStopSlots * kSolveWarps * (w.ctasG + w.ctasF), s));
+  if (test) {
+    // one row of words per test and side; tags from an earlier call could match, so clear the rows used
+    NMF_CU(cudaMemsetAsync(w.slots, 0, sizeof(unsigned long long) * pa.max_inner * w.ctasG, s));
+    NMF_CU(cudaMemsetAsync(w.slots + (size_t)kMaxInnerIters * w.ctasG, 0,
+                           sizeof(unsigned long long) * pa.max_inner * w.ctasF, s));
+  }
   if (stats) NMF_CU(cudaMemsetAsync(stats, 0, sizeof(nenmf_stats_t), s));
   if (times) {
     NMF_CU(cudaMemsetAsync(times, 0, sizeof(long long) * ((size_t)pa.max_outer + 1), s));
@@ -514,7 +518,7 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
   f.groups_in = groupsInF;
   f.part_out = w.partF; f.group = w.groupF; f.group_out = w.groupOutF;
   f.tail_ctr = w.ctr + group_count(w.ctasG, w.groupG);
-  f.stop_slots = w.slots + (size_t)kStopSlots * kSolveWarps * w.ctasG;
+  f.stop_slots = w.slots + (size_t)kMaxInnerIters * w.ctasG;
   if (plain) {
     g.bsrc = B_FROM_PARTIALS; g.Bpart = w.partN; g.Bparts = w.plan.S_c; g.Bld = w.plan.NV;
     g.op_out = w.opG; g.op_ld = w.ldG; g.op_bf16 = bf16;

@@ -112,7 +112,8 @@ enum BSource { B_FROM_ROWS = 0, B_FROM_COLS = 1, B_FROM_PARTIALS = 2 };
 enum Epilogue { EPI_NONE = 0, EPI_W_ROWS = 1, EPI_W_COLS = 2, EPI_GRAM = 3 };
 constexpr int kSolveThreads = 128;
 constexpr int kSolveWarps = kSolveThreads / 32;
-constexpr int kStopSlots = 16;   // per-test partial-sum slots of the stop test
+constexpr int kStopSlots = 16;   // shared-memory slots of the stop test (> kLag)
+constexpr int kMaxInnerIters = 4096;  // largest max_inner accepted
 
 constexpr int kMaxReduceFloats = 16384;  // per-CTA shared-memory budget for reducing the predecessor's partials
 
@@ -142,7 +143,7 @@ struct SolveArgs {
   int side;              // 0 = G, 1 = F (stats slot)
   double* pg2_init;      // MODE_EVAL: per-CTA ||P grad(Y0)||^2
   double* pg2_part;      // [ctas]: ||P grad||^2 of the returned iterate, per CTA
-  unsigned long long* stop_slots;  // [kStopSlots][ctas * warps]: tagged stop-test partials (zeroed per call)
+  unsigned long long* stop_slots;  // [max_inner][ctas]: tagged stop-test partials, one row per test (zeroed per call)
   int epoch;             // distinct for every solve launch of one call (tags of stop_slots)
   // epilogue: the next phase's W or Gram matrix, per CTA (and per group)
   int epi;               // Epilogue

@@ -48,6 +48,7 @@ struct KParams {
   int mode;
 };
 
+// Sum over the block (every warp, including the collector, which adds 0).
 __device__ __forceinline__ double block_sum_double(double v, double* red) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -56,7 +57,7 @@ __device__ __forceinline__ double block_sum_double(double v, double* red) {
   __syncthreads();
   double s = 0.0;
   if (threadIdx.x == 0)
-    for (int i = 0; i < T / 32; ++i) s += red[i];
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
   return s;  // valid in thread 0
 }
 
@@ -90,62 +91,120 @@ __device__ __forceinline__ float pg_sq(const float* f, const float* g) {
   return s;
 }
 
-// Stop-test slots: one 64-bit word per warp and test, (tag << 32) | float
-// bits of the warp's ||P grad||^2. A single relaxed 64-bit store publishes
-// both, so no fence or counter is needed. Every warp of every CTA then reads
-// all words of the test, waits for their tags, and sums them in float-float
-// in one fixed order, so all warps reach the same decision without any
-// block-level synchronisation. Tags carry the launch epoch, so words left by
-// earlier launches of the same call never match.
-constexpr int kWarps = T / 32;
+// Stop test. Compute warps post their ||P grad||^2 partial of test j in
+// shared memory; a dedicated collector warp (warp kWarps of the CTA) sums
+// them and publishes the CTA's partial as one 64-bit word (tag << 32 | float
+// bits) in global memory. If the CTA's own partial already exceeds eps^2 the
+// test fails everywhere (partials are nonnegative), and the collector posts
+// "go on" at once; otherwise it waits until every CTA's word for test j
+// carries the tag, sums them in float-float in one fixed order (identical in
+// every CTA) and posts the decision in shared memory. Compute warps read the decision of
+// test j at iteration j + kLag, so they never wait on global memory. A single
+// relaxed 64-bit store publishes value and tag together, so no fence or
+// counter is needed; tags carry the launch epoch, so words left by earlier
+// launches of the same call never match. Every test has its own row of words
+// (no reuse within a launch): a CTA that decides locally may run ahead of a
+// CTA that still polls.
+constexpr int kWarps = T / 32;          // compute warps
+constexpr int kThreadsAll = T + 32;     // plus the collector warp
 
 __device__ __forceinline__ uint32_t stop_tag(int epoch, int j) { return ((uint32_t)epoch << 16) | (uint32_t)(j + 1); }
 
-__device__ __forceinline__ void publish_warp(unsigned long long* slots, int j, int epoch, float v) {
-  const int nw = gridDim.x * kWarps;
-  const int wi = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const unsigned long long w = ((unsigned long long)stop_tag(epoch, j) << 32) | (unsigned long long)__float_as_uint(v);
-  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(slots[(size_t)(j % kStopSlots) * nw + wi]);
-  r.store(w, cuda::memory_order_relaxed);
+struct StopShared {
+  float part[kStopSlots][kWarps];
+  int part_tag[kStopSlots][kWarps];
+  int dec_tag[kStopSlots];
+  int dec_val[kStopSlots];
+  double dec_tot[kStopSlots];
+};
+
+// Collector warp: processes tests 0 .. ntests-1 in order until one passes.
+// Returns false on timeout or abort.
+__device__ bool collector_loop(StopShared& S, unsigned long long* slots, int ntests, int epoch, double eps2,
+                               Control* c) {
+  const int lane = threadIdx.x & 31;
+  const int ctas = gridDim.x;
+  const unsigned long long t0 = global_ns();
+  for (int j = 0; j < ntests; ++j) {
+    const int sl = j % kStopSlots;
+    // 1. the CTA's partial
+    int ok = 1;
+    if (lane < kWarps) {
+      while (*((volatile int*)&S.part_tag[sl][lane]) != j + 1) {
+        if (*((volatile int*)&c->abort) || global_ns() - t0 > kWaitNs) { ok = 0; break; }
+      }
+    }
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    __threadfence_block();
+    if (lane == 0) {
+      float s = 0.f;
+      for (int w = 0; w < kWarps; ++w) s += *((volatile float*)&S.part[sl][w]);
+      const unsigned long long word =
+          ((unsigned long long)stop_tag(epoch, j) << 32) | (unsigned long long)__float_as_uint(s);
+      cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(slots[(size_t)j * ctas + blockIdx.x]);
+      r.store(word, cuda::memory_order_relaxed);
+    }
+    // Partials are nonnegative and every sum below is monotone, so the total
+    // is at least this CTA's partial: when that already exceeds eps^2 the
+    // test fails in every CTA, and the decision needs no other CTA's word.
+    float own = 0.f;
+    if (lane == 0)
+      for (int w = 0; w < kWarps; ++w) own += *((volatile float*)&S.part[sl][w]);
+    own = __shfl_sync(0xffffffffu, own, 0);
+    if ((double)own > eps2) {
+      if (lane == 0) {
+        S.dec_val[sl] = 0;
+        S.dec_tot[sl] = (double)own;
+        __threadfence_block();
+        *((volatile int*)&S.dec_tag[sl]) = j + 1;
+      }
+      continue;
+    }
+    // 2. every CTA's partial, summed in float-float in a fixed order
+    const uint32_t tag = stop_tag(epoch, j);
+    DF acc{0.f, 0.f};
+    for (int i = lane; i < ctas && ok; i += 32) {
+      cuda::atomic_ref<const unsigned long long, cuda::thread_scope_device> r(slots[(size_t)j * ctas + i]);
+      unsigned long long w = r.load(cuda::memory_order_relaxed);
+      while ((uint32_t)(w >> 32) != tag) {
+        if (*((volatile int*)&c->abort) || global_ns() - t0 > kWaitNs) { ok = 0; break; }
+        w = r.load(cuda::memory_order_relaxed);
+      }
+      df_add(acc, __uint_as_float((uint32_t)w), 0.f);
+    }
+    if (!__all_sync(0xffffffffu, ok)) return false;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+      const float lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+      DF a = (lane & o) ? DF{hi, lo} : acc;  // lower lane's value first in both lanes
+      const DF b = (lane & o) ? acc : DF{hi, lo};
+      df_add(a, b.hi, b.lo);
+      acc = a;
+    }
+    const double total = (double)acc.hi + (double)acc.lo;
+    const int stop = total <= eps2;
+    if (lane == 0) {
+      S.dec_val[sl] = stop;
+      S.dec_tot[sl] = total;
+      __threadfence_block();
+      *((volatile int*)&S.dec_tag[sl]) = j + 1;
+    }
+    if (stop) return true;
+  }
+  return true;
 }
 
-// Returns false on timeout or abort; *total is valid in every lane.
-__device__ __forceinline__ bool collect_warp(const unsigned long long* slots, int j, int epoch, Control* c,
-                                             double* total) {
-  const int lane = threadIdx.x & 31;
-  const int nw = gridDim.x * kWarps;
-  const uint32_t tag = stop_tag(epoch, j);
-  const unsigned long long* sl = slots + (size_t)(j % kStopSlots) * nw;
-  DF s{0.f, 0.f};
-  int good = 1;
+// Compute warp: waits for the collector's decision on test j (1 = stop, 0 =
+// go on, -1 = timeout or abort).
+__device__ __forceinline__ int wait_decision(StopShared& S, int j, Control* c) {
+  const int sl = j % kStopSlots;
   const unsigned long long t0 = global_ns();
-  for (int i = lane; i < nw && good; i += 32) {
-    cuda::atomic_ref<const unsigned long long, cuda::thread_scope_device> r(sl[i]);
-    unsigned long long w = r.load(cuda::memory_order_relaxed);
-    while ((uint32_t)(w >> 32) != tag) {
-      if (*((volatile int*)&c->abort)) { good = 0; break; }
-      if (global_ns() - t0 > kWaitNs) {
-        set_status(c, NMF_ERR_DEVICE_TIMEOUT);
-        *((volatile int*)&c->abort) = 1;
-        good = 0;
-        break;
-      }
-      w = r.load(cuda::memory_order_relaxed);
-    }
-    df_add(s, __uint_as_float((uint32_t)w), 0.f);
+  while (*((volatile int*)&S.dec_tag[sl]) != j + 1) {
+    if (*((volatile int*)&c->abort) || global_ns() - t0 > kWaitNs) return -1;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float hi = __shfl_xor_sync(0xffffffffu, s.hi, o);
-    const float lo = __shfl_xor_sync(0xffffffffu, s.lo, o);
-    // the pair sum is formed in the same order in both lanes (lower lane first)
-    DF a = (lane & o) ? DF{hi, lo} : s;
-    const DF b = (lane & o) ? s : DF{hi, lo};
-    df_add(a, b.hi, b.lo);
-    s = a;
-  }
-  *total = (double)s.hi + (double)s.lo;
-  return __all_sync(0xffffffffu, good) != 0;
+  __threadfence_block();
+  return *((volatile int*)&S.dec_val[sl]);
 }
 
 // lambda_max of the symmetric PSD p x p matrix H (row stride p, shared
@@ -220,23 +279,26 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
 
 template <int PM>
-__global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
+__global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
   const SolveArgs& a = kp.a;
   Control* ctrl = a.ctrl;
   const int p = a.p, nu = a.nu, N = a.N;
   const int tid = threadIdx.x;
+  const int NT = blockDim.x;          // all threads, for cooperative loads
+  const bool colthr = tid < T;        // threads 0..T-1 own a column each; warp kWarps collects
   const int cta = blockIdx.x;
   const int ctas = gridDim.x;
   const int col = cta * T + tid;
-  const bool active = col < N;
+  const bool active = colthr && col < N;
   const int c0 = cta * T;
   const int cols = min(T, N - c0);
   const bool gram = a.bsrc == B_FROM_PARTIALS;  // plain mode: H comes reduced, no W
 
   __shared__ __align__(16) float Hs[PM * PM];
   __shared__ float Ws[PM * NMF_MAX_SKETCH];
-  __shared__ double red[T / 32];
+  __shared__ double red[kThreadsAll / 32];
   __shared__ int flag_s;
+  __shared__ StopShared stop_s;
   __shared__ double lam_s;
   extern __shared__ __align__(16) float dyn[];
   const bool epiW = a.epi == EPI_W_ROWS || a.epi == EPI_W_COLS;
@@ -255,12 +317,12 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
   }
   if (a.epi == EPI_W_ROWS) {
     const float* src = a.E + (size_t)c0 * nu;
-    for (int i = tid; i < T * nu; i += T) {
+    for (int i = tid; i < T * nu; i += NT) {
       const int t = i / nu, k = i % nu;
       Es[k * kFs + t] = t < cols ? __ldg(src + i) : 0.f;
     }
   } else if (a.epi == EPI_W_COLS) {
-    for (int i = tid; i < nu * T; i += T) {
+    for (int i = tid; i < nu * T; i += NT) {
       const int k = i / T, t = i % T;
       Es[k * kFs + t] = t < cols ? __ldg(a.E + (size_t)k * N + c0 + t) : 0.f;
     }
@@ -268,12 +330,12 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
   if (stageD) {
     if (a.bsrc == B_FROM_ROWS) {
       const float* src = a.D + (size_t)c0 * nu;
-      for (int i = tid; i < T * nu; i += T) {
+      for (int i = tid; i < T * nu; i += NT) {
         const int t = i / nu, k = i % nu;
         Ds[k * kFs + t] = t < cols ? __ldg(src + i) : 0.f;
       }
     } else {
-      for (int i = tid; i < nu * T; i += T) {
+      for (int i = tid; i < nu * T; i += NT) {
         const int k = i / T, t = i % T;
         Ds[k * kFs + t] = t < cols ? __ldg(a.D + (size_t)k * N + c0 + t) : 0.f;
       }
@@ -296,29 +358,29 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
     {
       const int total = G * P;
       const float4* src4 = reinterpret_cast<const float4*>(a.part_in);
-      for (int i = tid; i < total / 4; i += T) reinterpret_cast<float4*>(Ps)[i] = __ldcg(src4 + i);
-      for (int i = (total / 4) * 4 + tid; i < total; i += T) Ps[i] = __ldcg(a.part_in + i);
+      for (int i = tid; i < total / 4; i += NT) reinterpret_cast<float4*>(Ps)[i] = __ldcg(src4 + i);
+      for (int i = (total / 4) * 4 + tid; i < total; i += NT) Ps[i] = __ldcg(a.part_in + i);
     }
     __syncthreads();
     float* Rw = Ps + round_up(G * P, 4);  // the reduced W (or H)
-    for (int o = tid; o < P; o += T) {
+    for (int o = tid; o < P; o += NT) {
       float s = 0.f;
       for (int g = 0; g < G; ++g) s += Ps[(size_t)g * P + o];
       Rw[o] = s;
     }
     __syncthreads();
     if (gram) {
-      for (int i = tid; i < PM * PM; i += T) {
+      for (int i = tid; i < PM * PM; i += NT) {
         const int c = i / PM, d = i % PM;
         Hs[i] = (c < p && d < p) ? Rw[c * p + d] : 0.f;
       }
     } else {
-      for (int i = tid; i < PM * nu; i += T) {
+      for (int i = tid; i < PM * nu; i += NT) {
         const int c = i / nu, k = i % nu;
         Ws[c * NMF_MAX_SKETCH + k] = c < p ? Rw[c * nu + k] : 0.f;
       }
       __syncthreads();
-      for (int i = tid; i < PM * PM; i += T) {
+      for (int i = tid; i < PM * PM; i += NT) {
         const int c = i / PM, d = i % PM;
         float s = 0.f;
         for (int k = 0; k < nu; ++k) s = fmaf(Ws[c * NMF_MAX_SKETCH + k], Ws[d * NMF_MAX_SKETCH + k], s);
@@ -326,13 +388,14 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
       }
     }
     __syncthreads();
-    // L_c by warp 0 while the other warps form B.
-    if (kp.mode == MODE_SOLVE && tid < 32) {
+    // L_c by the collector warp while the compute warps form B.
+    if (kp.mode == MODE_SOLVE && !colthr) {
+      const int ln = tid & 31;
       float* Hp = Rw + P;  // H compacted to p x p for the eigenvalue routine
-      for (int i = tid; i < p * p; i += 32) Hp[i] = Hs[(i / p) * PM + i % p];
+      for (int i = ln; i < p * p; i += 32) Hp[i] = Hs[(i / p) * PM + i % p];
       __syncwarp();
       const double lam = lambda_max_warp<PM>(Hp, p);
-      if (tid == 0) lam_s = lam;
+      if (ln == 0) lam_s = lam;
     }
     if (active) {
       if (gram) {
@@ -385,56 +448,80 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
     const bool test = a.stop_test;
     const double eps2 = ctrl->eps2;
     int tests = 0, stop_j = -1;
-    double tot = 0.0;
     bool aborted = false;
-    for (int k = 0; k < a.max_inner; ++k) {
-#pragma unroll
-      for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
-      float gf[PM];
-      hmatvec<PM>(Hs, f, b, gf);
-      const float beta = __ldg(kp.beta + k);
-#pragma unroll
-      for (int c = 0; c < PM; ++c) {
-        y[c] = fmaf(beta, f[c] - fp[c], f[c]);
-        g[c] = fmaf(beta, gf[c] - gp[c], gf[c]);
-        fp[c] = f[c];
-        gp[c] = gf[c];
+    if (!colthr) {
+      // collector warp
+      const int ntests = test ? max(0, a.max_inner - a.min_inner + 1) : 0;
+      if (!collector_loop(stop_s, a.stop_slots, ntests, a.epoch, eps2, ctrl)) {
+        aborted = true;
+        if ((tid & 31) == 0) {
+          set_status(ctrl, NMF_ERR_DEVICE_TIMEOUT);
+          *((volatile int*)&ctrl->abort) = 1;
+        }
       }
-      iters = k + 1;
-      if (test && k + 1 >= a.min_inner) {
-        const float ws = warp_sum(active ? pg_sq<PM>(f, gf) : 0.f);
-        if ((tid & 31) == 0) publish_warp(a.stop_slots, tests, a.epoch, ws);
-        float* slot = keep + (size_t)(tests % kKeep) * PM * T;
+    } else {
+      for (int k = 0; k < a.max_inner; ++k) {
 #pragma unroll
-        for (int c = 0; c < PM; ++c) slot[c * T + tid] = f[c];
-        ++tests;
-        if (tests > kLag) {
-          const int j = tests - 1 - kLag;
-          if (!collect_warp(a.stop_slots, j, a.epoch, ctrl, &tot)) { aborted = true; break; }
-          if (tot <= eps2) {
+        for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
+        float gf[PM];
+        hmatvec<PM>(Hs, f, b, gf);
+        const float beta = __ldg(kp.beta + k);
+#pragma unroll
+        for (int c = 0; c < PM; ++c) {
+          y[c] = fmaf(beta, f[c] - fp[c], f[c]);
+          g[c] = fmaf(beta, gf[c] - gp[c], gf[c]);
+          fp[c] = f[c];
+          gp[c] = gf[c];
+        }
+        iters = k + 1;
+        if (test && k + 1 >= a.min_inner) {
+          const float ws = warp_sum(active ? pg_sq<PM>(f, gf) : 0.f);
+          const int sl = tests % kStopSlots;
+          if ((tid & 31) == 0) {
+            stop_s.part[sl][tid >> 5] = ws;
+            __threadfence_block();
+            *((volatile int*)&stop_s.part_tag[sl][tid >> 5]) = tests + 1;
+          }
+          float* slot = keep + (size_t)(tests % kKeep) * PM * T;
+#pragma unroll
+          for (int c = 0; c < PM; ++c) slot[c * T + tid] = f[c];
+          ++tests;
+          if (tests > kLag) {
+            const int j = tests - 1 - kLag;
+            const int d = wait_decision(stop_s, j, ctrl);
+            if (d < 0) { aborted = true; break; }
+            if (d) {
+              stop_j = j;
+              break;
+            }
+          }
+        }
+      }
+      if (test && stop_j < 0 && !aborted) {
+        // tests still pending when the loop ended, in order
+        for (int j = tests > kLag ? tests - kLag : 0; j < tests; ++j) {
+          const int d = wait_decision(stop_s, j, ctrl);
+          if (d < 0) { aborted = true; break; }
+          if (d) {
             stop_j = j;
             break;
           }
         }
       }
     }
-    if (test && stop_j < 0 && !aborted) {
-      // tests still pending when the loop ended, in order
-      for (int j = tests > kLag ? tests - kLag : 0; j < tests; ++j) {
-        if (!collect_warp(a.stop_slots, j, a.epoch, ctrl, &tot)) { aborted = true; break; }
-        if (tot <= eps2) {
-          stop_j = j;
-          break;
-        }
-      }
-    }
     if (__syncthreads_or(aborted)) return;
-    if (stop_j >= 0) {
+    if (colthr && stop_j >= 0) {
       const float* slot = keep + (size_t)(stop_j % kKeep) * PM * T;
 #pragma unroll
       for (int c = 0; c < PM; ++c) f[c] = slot[c * T + tid];
       iters = a.min_inner + stop_j;
-      pg2_final = cta == 0 ? tot : 0.0;  // the total is global: CTA 0 carries it
+    }
+    // every compute thread reached the same decision; broadcast it to the collector
+    if (tid == 0) flag_s = stop_j;
+    __syncthreads();
+    stop_j = flag_s;
+    if (stop_j >= 0) {
+      pg2_final = cta == 0 ? stop_s.dec_tot[stop_j % kStopSlots] : 0.0;  // the total is global: CTA 0 carries it
     } else {
       pg2_final = block_sum_double(active ? (double)pg_sq<PM>(fp, gp) : 0.0, red);  // thread 0
     }
@@ -483,12 +570,14 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
     __syncthreads();  // scratch (pending iterates) is reused
     const int P = a.epi == EPI_GRAM ? p * p : p * nu;
     float* Fs = scratch;  // [PM][kFs]
+    if (colthr) {
 #pragma unroll
-    for (int c = 0; c < PM; ++c) Fs[c * kFs + tid] = active ? f[c] : 0.f;
+      for (int c = 0; c < PM; ++c) Fs[c * kFs + tid] = active ? f[c] : 0.f;
+    }
     __syncthreads();
     const float* Os = a.epi == EPI_GRAM ? Fs : Es;
     const int ow = a.epi == EPI_GRAM ? p : nu;
-    for (int o = tid; o < P; o += T) {
+    for (int o = tid; o < P; o += NT) {
       const int c = o / ow, k = o % ow;
       float s = 0.f;
       for (int t = 0; t < T; ++t) s = fmaf(Fs[c * kFs + t], Os[k * kFs + t], s);
@@ -504,7 +593,7 @@ __global__ void __launch_bounds__(T) solve_kernel(KParams kp) {
       __syncthreads();
       if (flag_s) {
         __threadfence();
-        for (int o = tid; o < P; o += T) {
+        for (int o = tid; o < P; o += NT) {
           float s = 0.f;
           for (int i = 0; i < gsz; ++i) s += __ldcg(a.part_out + (size_t)(gi * a.group + i) * P + o);
           a.group_out[(size_t)gi * P + o] = s;
@@ -547,7 +636,7 @@ cudaError_t launch_pm(const KParams& kp, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(ctas);
-  cfg.blockDim = dim3(T);
+  cfg.blockDim = dim3(kThreadsAll);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   // Programmatic dependent launch: the kernel starts while its predecessor
@@ -613,7 +702,7 @@ int occupancy_pm(size_t smem) {
   int per = 0;
   if (allow_dynamic_smem((const void*)solve_kernel<PM>, (int)smem) != cudaSuccess)
     return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<PM>, T, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<PM>, kThreadsAll, smem) != cudaSuccess) return 0;
   return per;
 }
 
