@@ -92,10 +92,8 @@ struct CompressWs {
   float* partT;
   float* YN[2];
   float* YT[2];
-  float2* gramN;
-  float2* gramT;
-  float* rinvN[3];
-  float* rinvT[3];
+  float2* gramN[2];  // ping-pong Gram partials of the N job
+  float2* gramT[2];
   float* omega;
   XPassPlan plan;
   size_t bytes;
@@ -123,11 +121,10 @@ CompressWs carve_compress(void* base, int n, int m, int nu, nmf_prec_t prec) {
     w.YT[i] = cv.take<float>((size_t)m * nu);
   }
   const int E = nu * (nu + 1) / 2;
-  w.gramN = cv.take<float2>((size_t)rows_ctas(n) * E);
-  w.gramT = cv.take<float2>((size_t)rows_ctas(m) * E);
-  for (int i = 0; i < 3; ++i) {
-    w.rinvN[i] = cv.take<float>((size_t)nu * nu);
-    w.rinvT[i] = cv.take<float>((size_t)nu * nu);
+  const int E2 = (E + 1) & ~1;  // Gram partials use an even float2 stride
+  for (int i = 0; i < 2; ++i) {
+    w.gramN[i] = cv.take<float2>((size_t)rows_ctas(n) * E2);
+    w.gramT[i] = cv.take<float2>((size_t)rows_ctas(m) * E2);
   }
   w.omega = cv.take<float>((size_t)(n > m ? n : m) * nu);
   w.bytes = cv.size();
@@ -143,53 +140,45 @@ nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16
   int* flagN = &ctrl->flags[0];
   int* flagT = &ctrl->flags[1];
   const int NV = w.plan.NV;
-  // K1: reduce the partials, Gram 1
+  NMF_CU(cudaMemsetAsync(ctrl->flags, 0, 2 * sizeof(int), s));
+  // reduce: Y = sum of the X pass partials, Gram 1
   RowJob r1[2] = {};
   r1[0].part = w.partN; r1[0].S = w.plan.S_c; r1[0].ldp = NV; r1[0].N = n; r1[0].nu = nu;
-  r1[0].Y = w.YN[0]; r1[0].gram_part = w.gramN;
+  r1[0].Y = w.YN[0]; r1[0].gram_part = w.gramN[0]; r1[0].gram_always = 1;
   r1[1].part = w.partT; r1[1].S = w.plan.S_r; r1[1].ldp = NV; r1[1].N = m; r1[1].nu = nu;
-  r1[1].Y = w.YT[0]; r1[1].gram_part = w.gramT;
+  r1[1].Y = w.YT[0]; r1[1].gram_part = w.gramT[0]; r1[1].gram_always = 1;
   NMF_CU(rows_launch(r1, 2, ctrl, s));
-  // K2
-  CholJob c1[2] = {};
-  c1[0].gram_part = w.gramN; c1[0].parts = rows_ctas(n); c1[0].nu = nu; c1[0].rinv = w.rinvN[0];
-  c1[0].shift_flag = flagN; c1[0].reset_flag = 1;
-  c1[1].gram_part = w.gramT; c1[1].parts = rows_ctas(m); c1[1].nu = nu; c1[1].rinv = w.rinvT[0];
-  c1[1].shift_flag = flagT; c1[1].reset_flag = 1;
-  NMF_CU(chol_launch(c1, 2, ctrl, s));
-  // K3: Q1 = Y R1^-1, Gram 2
+  // apply 1: factor Gram 1 (shift if needed), Q1 = Y R1^-1, Gram 2
   RowJob r2[2] = {};
-  r2[0].src = w.YN[0]; r2[0].rinv = w.rinvN[0]; r2[0].N = n; r2[0].nu = nu; r2[0].Y = w.YN[1]; r2[0].gram_part = w.gramN;
-  r2[1].src = w.YT[0]; r2[1].rinv = w.rinvT[0]; r2[1].N = m; r2[1].nu = nu; r2[1].Y = w.YT[1]; r2[1].gram_part = w.gramT;
+  r2[0].src = w.YN[0]; r2[0].gram_in = w.gramN[0]; r2[0].gram_parts = rows_ctas(n); r2[0].N = n; r2[0].nu = nu;
+  r2[0].Y = w.YN[1]; r2[0].gram_part = w.gramN[1]; r2[0].gram_always = 1; r2[0].shift_flag = flagN;
+  r2[1].src = w.YT[0]; r2[1].gram_in = w.gramT[0]; r2[1].gram_parts = rows_ctas(m); r2[1].N = m; r2[1].nu = nu;
+  r2[1].Y = w.YT[1]; r2[1].gram_part = w.gramT[1]; r2[1].gram_always = 1; r2[1].shift_flag = flagT;
   NMF_CU(rows_launch(r2, 2, ctrl, s));
-  // K4
-  CholJob c2[2] = {c1[0], c1[1]};
-  c2[0].rinv = w.rinvN[1]; c2[0].reset_flag = 0;
-  c2[1].rinv = w.rinvT[1]; c2[1].reset_flag = 0;
-  NMF_CU(chol_launch(c2, 2, ctrl, s));
-  // K5: Q2 = Q1 R2^-1 -> outputs; Gram 3 only if a shift was taken.
+  // apply 2: Q2 = Q1 R2^-1 -> outputs; Gram 3 only if some factorisation shifted
   float* QN = w.YN[0];
   float* QT = Rout ? Rout : w.YT[0];
   RowJob r3[2] = {};
-  r3[0].src = w.YN[1]; r3[0].rinv = w.rinvN[1]; r3[0].N = n; r3[0].nu = nu; r3[0].Y = QN;
-  r3[0].op = w.opB; r3[0].ldop = w.ldb; r3[0].op_bf16 = bf16; r3[0].Yt = Lout;
-  r3[0].gram_part = w.gramN; r3[0].gram_flag = flagN;
-  r3[1].src = w.YT[1]; r3[1].rinv = w.rinvT[1]; r3[1].N = m; r3[1].nu = nu; r3[1].Y = QT;
-  r3[1].op = w.opA; r3[1].ldop = w.lda; r3[1].op_bf16 = bf16;
-  r3[1].gram_part = w.gramT; r3[1].gram_flag = flagT;
+  r3[0].src = w.YN[1]; r3[0].gram_in = w.gramN[1]; r3[0].gram_parts = rows_ctas(n); r3[0].N = n; r3[0].nu = nu;
+  r3[0].Y = QN; r3[0].op = w.opB; r3[0].ldop = w.ldb; r3[0].op_bf16 = bf16; r3[0].Yt = Lout;
+  r3[0].gram_part = w.gramN[0]; r3[0].gram_on_shift = 1; r3[0].shift_flag = flagN;
+  r3[1].src = w.YT[1]; r3[1].gram_in = w.gramT[1]; r3[1].gram_parts = rows_ctas(m); r3[1].N = m; r3[1].nu = nu;
+  r3[1].Y = QT; r3[1].op = w.opA; r3[1].ldop = w.lda; r3[1].op_bf16 = bf16;
+  r3[1].gram_part = w.gramT[0]; r3[1].gram_on_shift = 1; r3[1].shift_flag = flagT;
   NMF_CU(rows_launch(r3, 2, ctrl, s));
-  // K6, K7: third pass, in place, only where a shift was taken.
-  CholJob c3[2] = {c1[0], c1[1]};
-  c3[0].rinv = w.rinvN[2]; c3[0].shift_flag = nullptr; c3[0].run_flag = flagN;
-  c3[1].rinv = w.rinvT[2]; c3[1].shift_flag = nullptr; c3[1].run_flag = flagT;
-  NMF_CU(chol_launch(c3, 2, ctrl, s));
+  // apply 3, in place, only where a shift was taken
   RowJob r4[2] = {r3[0], r3[1]};
-  r4[0].src = QN; r4[0].rinv = w.rinvN[2]; r4[0].gram_part = nullptr; r4[0].gram_flag = nullptr; r4[0].run_flag = flagN;
-  r4[1].src = QT; r4[1].rinv = w.rinvT[2]; r4[1].gram_part = nullptr; r4[1].gram_flag = nullptr; r4[1].run_flag = flagT;
+  r4[0].src = QN; r4[0].gram_in = w.gramN[0]; r4[0].gram_part = nullptr; r4[0].gram_on_shift = 0;
+  r4[0].shift_flag = nullptr; r4[0].run_flag = flagN;
+  r4[1].src = QT; r4[1].gram_in = w.gramT[0]; r4[1].gram_part = nullptr; r4[1].gram_on_shift = 0;
+  r4[1].shift_flag = nullptr; r4[1].run_flag = flagT;
   NMF_CU(rows_launch(r4, 2, ctrl, s));
   return NMF_OK;
 }
 
+}  // namespace
+
+namespace {
 
 // ----------------------------------------------------------------------------
 // nenmf_solve workspace

@@ -70,39 +70,33 @@ cudaError_t xpass_tc_launch(const XPassPlan& plan, const XPassArgs& a, cudaStrea
 bool xpass_tc_available();
 
 // ---------------------------------------------------------------------------
-// Row kernels of the orthonormalisation (CholeskyQR with float-float Gram).
-// A "job" is one tall matrix of N rows and nu columns.
+// Row kernels of the orthonormalisation (CholeskyQR2, float-float Gram and
+// Cholesky). A "job" is one tall matrix of N rows and nu columns.
 // ---------------------------------------------------------------------------
-constexpr int kOrthRows = 128;  // rows per CTA in the row kernels
+constexpr int kOrthRows = 256;  // rows per CTA in the row kernels (one per thread)
 
 struct RowJob {
-  // source: partial sums (part != null) or a dense N x nu matrix times Rinv
-  const float* part;    // S x N x ldp
+  // source: X pass partials (reduce step) or a dense N x nu matrix whose Gram
+  // partials are given (apply step: factor the Gram, q R = y row by row)
+  const float* part;    // S x N x ldp (reduce step)
   int S, ldp;
-  const float* src;     // N x nu (used when part == null)
-  const float* rinv;    // nu x nu upper-triangular inverse (float), with src
+  const float* src;     // N x nu (apply step)
+  const float2* gram_in;  // apply step: [gram_parts][nu*(nu+1)/2] float-float partials of src^T src
+  int gram_parts;
   int N, nu;
   // outputs (each optional)
-  float* Y;             // N x nu row-major
+  float* Y;             // N x nu row-major (may alias src: rows are read before written)
   float* Yt;            // nu x N row-major (transpose)
   void* op;             // NV x ldop transposed operand (float or bf16)
   int ldop, op_bf16;
   float2* gram_part;    // [ctas][nu*(nu+1)/2] float-float partial Gram of the output rows
-  const int* gram_flag; // optional: compute gram_part only if *gram_flag != 0
+  int gram_always;      // form gram_part unconditionally
+  int gram_on_shift;    // form gram_part when *shift_flag (as read) or this factorisation shifted
+  int* shift_flag;      // apply step: raised (by CTA 0) when the factorisation needed the shift
   const int* run_flag;  // optional: skip the job unless *run_flag != 0
 };
 
-struct CholJob {
-  const float2* gram_part;
-  int parts, nu;
-  float* rinv;          // out: nu x nu, inverse of the upper Cholesky factor
-  int* shift_flag;      // out: 1 when the shifted factorisation was needed
-  int reset_flag;       // 1: write 0/1 to *shift_flag; 0: only raise it
-  const int* run_flag;  // optional
-};
-
 cudaError_t rows_launch(const RowJob* jobs, int njobs, Control* ctrl, cudaStream_t s);
-cudaError_t chol_launch(const CholJob* jobs, int njobs, Control* ctrl, cudaStream_t s);
 inline int rows_ctas(int N) { return ceil_div(N, kOrthRows); }
 
 // ---------------------------------------------------------------------------
