@@ -190,7 +190,7 @@ struct SolveWs {
   float* beta;
   float* Gt;       // p x n
   int ctasG, ctasF;
-  int P;           // floats of one partial: p * nu (compressed) or p * p (plain)
+  int P;           // floats between partials: p * nu (compressed) or p * p (plain), padded to 4
   int groupG, groupF;  // partial group sizes (1: the successor reads per-CTA partials)
   float* partG;    // [ctasG][P]: the G side's share of the F update's W (or Gram)
   float* partF;    // [ctasF][P]: the F side's share of the G update's W (or Gram)
@@ -221,7 +221,7 @@ SolveWs carve_solve(void* base, const nenmf_problem_t& pr) {
   const int n = pr.n, m = pr.m, p = pr.p;
   const bool plain = pr.mode == NENMF_PLAIN;
   const int nu = plain ? 0 : pr.nu;
-  const int P = plain ? p * p : p * nu;
+  const int P = partial_stride(plain ? p * p : p * nu);
   w.P = P;
   w.ctrl = cv.take<Control>(1);
   w.beta = cv.take<float>(kMaxInner);

@@ -119,6 +119,9 @@ inline int partial_group_size(int ctas, int P) {
   return total <= kMaxReduceFloats ? 1 : (int)((total + kMaxReduceFloats - 1) / kMaxReduceFloats);
 }
 __host__ __device__ inline int group_count(int ctas, int group) { return ceil_div(ctas, group); }
+// Floats between consecutive per-CTA partials: P rounded up to a multiple of
+// four, so every partial starts on a 16-byte boundary (bulk copies, float4).
+__host__ __device__ inline int partial_stride(int P) { return (P + 3) & ~3; }
 
 struct SolveArgs {
   int p, N, nu;
@@ -129,7 +132,7 @@ struct SolveArgs {
   const float* Bpart;    // B_FROM_PARTIALS: [Bparts][N][Bld]
   int Bparts, Bld;
   // the predecessor's partials of W (compressed: p x nu) or H (plain: p x p)
-  const float* part_in;  // [groups_in][P]
+  const float* part_in;  // [groups_in][partial_stride(P)]
   int groups_in;
   // iteration
   int max_inner, min_inner;
@@ -142,9 +145,9 @@ struct SolveArgs {
   // epilogue: the next phase's W or Gram matrix, per CTA (and per group)
   int epi;               // Epilogue
   const float* E;        // EPI_W_ROWS: N x nu; EPI_W_COLS: nu x N
-  float* part_out;       // [ctas][P]
-  int group;             // partial_group_size(ctas, P)
-  float* group_out;      // [group_count(ctas, group)][P] when group > 1
+  float* part_out;       // [ctas][partial_stride(P)], padding zero
+  int group;             // partial_group_size(ctas, partial_stride(P))
+  float* group_out;      // [group_count(ctas, group)][partial_stride(P)] when group > 1
   unsigned int* tail_ctr;  // [group_count(ctas, group)], zero, left zero (group > 1)
   void* op_out;          // optional transposed operand NV x op_ld (float or bf16)
   int op_ld, op_bf16;

@@ -4,12 +4,13 @@
 // prologue  loads that do not depend on the previous kernel first (own
 //           factor, data and basis vectors), then griddepcontrol.wait
 //           (the kernel is launched as a programmatic dependent of the
-//           previous one, so this part overlaps its end); then every CTA sums
-//           the previous kernel's per-CTA partials of W (compressed: p x nu)
-//           or of the Gram matrix (plain) in a fixed order, forms H = W W^T
-//           and L_c = lambda_max(H) (one warp: repeated squaring of
-//           H / trace with trace renormalisation until the spectrum has
-//           collapsed to rank one, then a float64 Rayleigh quotient), and B:
+//           previous one, so this part overlaps its end); then every CTA
+//           copies the previous kernel's per-CTA partials of W (compressed:
+//           p x nu) or of the Gram matrix (plain) into shared memory with one
+//           bulk copy and sums them in a fixed order, forms H = W W^T and
+//           L_c = lambda_max(H) (one warp: repeated squaring of H / trace
+//           with trace renormalisation until the spectrum has collapsed to
+//           rank one, then a float-float Rayleigh quotient), and B:
 //             compressed (Alg. 1): B(:, j) = W d_j, d_j the j-th compressed
 //               data vector (G side: W = F_R = F R, d_j = row j of X_R;
 //               F side: W = G_L^T = (L G)^T, d_j = column j of X_L);
@@ -39,7 +40,8 @@ constexpr int kLag = 4;
 constexpr int kKeep = kLag + 1;
 static_assert(kStopSlots >= 2 * kLag + 1, "stop-test slots are reused after kStopSlots tests");
 constexpr int kMaxSquarings = 16;
-constexpr int kFs = T + 1;
+constexpr int kFs = T + 4;                  // column-vector rows: 16-byte aligned, rows 4 banks apart
+constexpr int kWs = NMF_MAX_SKETCH + 1;     // rows of W: consecutive rows in different banks
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 struct KParams {
@@ -48,35 +50,49 @@ struct KParams {
   int mode;
 };
 
-// Sum over the block (every warp, including the collector, which adds 0).
-__device__ __forceinline__ double block_sum_double(double v, double* red) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+// Sum over the block (every warp, including the collector, which adds 0), in
+// float-float arithmetic (float64 is slow on this part); the result is valid
+// in thread 0.
+__device__ __forceinline__ double block_sum_df(float v, float2* red) {
+  DF s{v, 0.f};
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, s.hi, o), l = __shfl_xor_sync(0xffffffffu, s.lo, o);
+    DF a = (lane & o) ? DF{h, l} : s;
+    const DF b = (lane & o) ? s : DF{h, l};
+    df_add(a, b.hi, b.lo);
+    s = a;
+  }
+  const int w = threadIdx.x >> 5;
   __syncthreads();
-  if (l == 0) red[w] = v;
+  if (lane == 0) red[w] = make_float2(s.hi, s.lo);
   __syncthreads();
-  double s = 0.0;
+  DF t{0.f, 0.f};
   if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-  return s;  // valid in thread 0
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) df_add(t, red[i].x, red[i].y);
+  return (double)t.hi + (double)t.lo;
 }
 
-// g = H y - b with H (PM x PM, zero padded) in shared memory, rows read as float4.
+// g = H y - b with the symmetric H (PM x PM, zero padded) in shared memory:
+// row d of H is column d, so g accumulates y_d times row d (read as float4)
+// over d; the PM sums advance together and hide each other's latency.
 template <int PM>
 __device__ __forceinline__ void hmatvec(const float* Hs, const float* y, const float* b, float* g) {
 #pragma unroll
-  for (int c = 0; c < PM; ++c) {
-    float s = -b[c];
-    const float4* h = reinterpret_cast<const float4*>(Hs + c * PM);
+  for (int c = 0; c < PM; ++c) g[c] = -b[c];
 #pragma unroll
-    for (int d = 0; d < PM / 4; ++d) {
-      const float4 v = h[d];
-      s = fmaf(v.x, y[4 * d + 0], s);
-      s = fmaf(v.y, y[4 * d + 1], s);
-      s = fmaf(v.z, y[4 * d + 2], s);
-      s = fmaf(v.w, y[4 * d + 3], s);
+  for (int d = 0; d < PM; ++d) {
+    const float4* h = reinterpret_cast<const float4*>(Hs + d * PM);
+    const float yd = y[d];
+#pragma unroll
+    for (int c4 = 0; c4 < PM / 4; ++c4) {
+      const float4 v = h[c4];
+      g[4 * c4 + 0] = fmaf(v.x, yd, g[4 * c4 + 0]);
+      g[4 * c4 + 1] = fmaf(v.y, yd, g[4 * c4 + 1]);
+      g[4 * c4 + 2] = fmaf(v.z, yd, g[4 * c4 + 2]);
+      g[4 * c4 + 3] = fmaf(v.w, yd, g[4 * c4 + 3]);
     }
-    g[c] = s;
   }
 }
 
@@ -207,51 +223,83 @@ __device__ __forceinline__ int wait_decision(StopShared& S, int j, Control* c) {
   return *((volatile int*)&S.dec_val[sl]);
 }
 
-// lambda_max of the symmetric PSD p x p matrix H (row stride p, shared
-// memory), by one warp: lane c holds row c of M = H / trace(H) in registers;
-// M is squared (row c of M^2 = sum_k M[c][k] row_k, row_k fetched by shuffles)
-// and renormalised to trace one until trace(M^2) reaches 1 (rank one), then
-// the float64 Rayleigh quotient of M's dominant column. Call with all 32
-// lanes of one warp; the result is valid in every lane. Returns 0 for H = 0
-// and a non-finite value for a non-finite H.
+// Row stride of the squaring buffers: PM or PM + 4, whichever is an odd
+// number of float4s, so rows read as float4 by eight lanes hit eight
+// different bank groups.
 template <int PM>
-__device__ double lambda_max_warp(const float* H, int p) {
+__host__ __device__ constexpr int lam_stride() { return ((PM / 4) & 1) ? PM : PM + 4; }
+
+// lambda_max of the symmetric PSD matrix H (PM x PM in shared memory, zero
+// outside p x p), by one warp. Repeated squaring with trace normalisation:
+// A_0 = H, A_{s+1} = (A_s / tr A_s)^2; the lanes share the PM (PM + 1) / 2
+// entries of the upper triangle (A stays symmetric), each a dot product of
+// two rows. tr(A_{s+1}) = tr(M^2) for the trace-one M = A_s / tr(A_s), which
+// reaches 1 exactly when M has rank one; at 1 - tr(M^2) < 1e-5 the other
+// eigenvectors' share in the dominant column is < 1e-5, so its Rayleigh
+// quotient (float-float arithmetic) is exact to ~1e-10. Ms is 2 PM
+// lam_stride<PM>() floats of 16-byte aligned scratch. The result is valid in
+// every lane; 0 for H = 0, non-finite for a non-finite H.
+template <int PM>
+__device__ double lambda_max_warp(const float* Hs, float* Ms, int p) {
+  constexpr int LS = lam_stride<PM>();
+  constexpr int E = PM * (PM + 1) / 2;
+  constexpr int NPL = (E + 31) / 32;
   const int lane = threadIdx.x & 31;
-  double tr = 0.0;
-  for (int c = lane; c < p; c += 32) tr += (double)H[c * p + c];
-  tr = warp_sum(tr);
-  if (!(tr > 0.0) || !isfinite(tr)) return isfinite(tr) ? 0.0 : tr;
-  const float inv = (float)(1.0 / tr);
-  float row[PM];
+  const float tr = warp_sum(lane < p ? Hs[lane * PM + lane] : 0.f);
+  if (!(tr > 0.f) || !isfinite(tr)) return isfinite(tr) ? 0.0 : (double)tr;
+  float* A = Ms;
+  float* B = Ms + PM * LS;
+  for (int i = lane; i < PM * PM; i += 32) A[(i / PM) * LS + i % PM] = Hs[i];
+  // this lane's upper-triangle entries (i << 8 | j), -1 past the end
+  int pr[NPL];
+  {
+    int i = 0, e = lane;
 #pragma unroll
-  for (int d = 0; d < PM; ++d) row[d] = (lane < p && d < p) ? H[lane * p + d] * inv : 0.f;
-  for (int s = 0; s < kMaxSquarings; ++s) {
-    float nr[PM];
-#pragma unroll
-    for (int d = 0; d < PM; ++d) nr[d] = 0.f;
-#pragma unroll
-    for (int k = 0; k < PM; ++k) {
-      const float mck = row[k];
-#pragma unroll
-      for (int d = 0; d < PM; ++d) nr[d] = fmaf(mck, __shfl_sync(0xffffffffu, row[d], k), nr[d]);
+    for (int q = 0; q < NPL; ++q) {
+      while (i < PM && e >= PM - i) {
+        e -= PM - i;
+        ++i;
+      }
+      pr[q] = i < PM ? (i << 8) | (i + e) : -1;
+      e += 32;
     }
-    float diag = 0.f;
+  }
+  __syncwarp();
+  float t = tr;
+  for (int s = 0; s < kMaxSquarings; ++s) {
+    const float sc = __fdividef(1.f, t);  // any positive scale normalises; t2 below is measured
+    const float sc2 = sc * sc;
+    float dsum = 0.f;
 #pragma unroll
-    for (int d = 0; d < PM; ++d) diag = (d == lane) ? nr[d] : diag;
-    const float t2 = warp_sum(diag);
-    const float it = t2 > 0.f ? 1.f / t2 : 0.f;
+    for (int q = 0; q < NPL; ++q) {
+      if (pr[q] < 0) continue;
+      const int i = pr[q] >> 8, j = pr[q] & 255;
+      const float4* ri = reinterpret_cast<const float4*>(A + i * LS);
+      const float4* rj = reinterpret_cast<const float4*>(A + j * LS);
+      float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-    for (int d = 0; d < PM; ++d) row[d] = nr[d] * it;
-    // trace(M^2) of a trace-one M equals 1 exactly when M has rank one; at
-    // 1 - trace(M^2) < 1e-5 the other eigenvectors' share in the chosen
-    // column is < 1e-5, so the Rayleigh quotient is exact to ~1e-10.
+      for (int d4 = 0; d4 < PM / 4; ++d4) {
+        const float4 x = ri[d4], z = rj[d4];
+        s0 = fmaf(x.x, z.x, s0);
+        s1 = fmaf(x.y, z.y, s1);
+        s0 = fmaf(x.z, z.z, s0);
+        s1 = fmaf(x.w, z.w, s1);
+      }
+      const float v = (s0 + s1) * sc2;
+      B[i * LS + j] = v;
+      B[j * LS + i] = v;
+      if (i == j) dsum += v;
+    }
+    const float t2 = warp_sum(dsum);  // trace of the new A (= tr(M^2), tr(M) = 1 to rounding)
+    __syncwarp();                      // every lane has read A and written B
+    float* tmp = A;
+    A = B;
+    B = tmp;
+    t = t2;
     if (!(t2 > 0.f) || 1.f - t2 < 1e-5f) break;
   }
-  // dominant column jb = argmax diag(M); v_c = M[c][jb] = row[jb] of lane c
-  float diag = 0.f;
-#pragma unroll
-  for (int d = 0; d < PM; ++d) diag = (d == lane) ? row[d] : diag;
-  float best = diag;
+  // dominant column jb = argmax diag(A); v_c = A[c][jb] = A[jb][c]
+  float best = lane < p ? A[lane * LS + lane] : -1.f;
   int jb = lane;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -262,17 +310,71 @@ __device__ double lambda_max_warp(const float* H, int p) {
       jb = oj;
     }
   }
-  float vc = 0.f;
+  const float* vrow = A + jb * LS;  // v (broadcast reads)
+  const float vc = lane < p ? vrow[lane] : 0.f;
+  // (H v)_c, then v^T H v and v^T v, all in float-float
+  DF hv{0.f, 0.f};
+  if (lane < p) {
 #pragma unroll
-  for (int d = 0; d < PM; ++d) vc = (d == jb) ? row[d] : vc;
-  if (lane >= p) vc = 0.f;
-  double hv = 0.0;
-  for (int d = 0; d < p; ++d) {
-    const float vd = __shfl_sync(0xffffffffu, vc, d);
-    if (lane < p) hv = fma((double)H[lane * p + d], (double)vd, hv);
+    for (int d = 0; d < PM; ++d) df_add_product(hv, Hs[lane * PM + d], vrow[d]);
   }
-  const double num = warp_sum((double)vc * hv), den = warp_sum((double)vc * (double)vc);
-  return den > 0.0 ? num / den : 0.0;
+  DF num{0.f, 0.f}, den{0.f, 0.f};
+  df_add_product(num, vc, hv.hi);
+  num.lo = fmaf(vc, hv.lo, num.lo);
+  df_add_product(den, vc, vc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float nh = __shfl_xor_sync(0xffffffffu, num.hi, o), nl = __shfl_xor_sync(0xffffffffu, num.lo, o);
+    const float dh = __shfl_xor_sync(0xffffffffu, den.hi, o), dl = __shfl_xor_sync(0xffffffffu, den.lo, o);
+    // the lower lane's value first, so both lanes compute the same sum
+    DF a = (lane & o) ? DF{nh, nl} : num, b = (lane & o) ? num : DF{nh, nl};
+    df_add(a, b.hi, b.lo);
+    num = a;
+    a = (lane & o) ? DF{dh, dl} : den;
+    b = (lane & o) ? den : DF{dh, dl};
+    df_add(a, b.hi, b.lo);
+    den = a;
+  }
+  df_norm(num);
+  df_norm(den);
+  if (!(den.hi > 0.f)) return 0.0;
+  // num / den in float-float: q0, then one correction from the exact residual
+  const float q0 = num.hi / den.hi;
+  const float ph = q0 * den.hi;
+  const float pe = fmaf(q0, den.hi, -ph);
+  const float r = ((num.hi - ph) - pe) + (num.lo - q0 * den.lo);
+  return (double)q0 + (double)(r / den.hi);
+}
+
+// Bulk copy global -> shared (async proxy), completion counted on an mbarrier.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_done(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, P1;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity`; false after kWaitNs or on abort.
+__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, Control* c) {
+  const unsigned long long t0 = global_ns();
+  while (!mbar_done(bar, parity)) {
+    if (*((volatile int*)&c->abort) || global_ns() - t0 > kWaitNs) return false;
+  }
+  return true;
 }
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -295,8 +397,9 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
   const bool gram = a.bsrc == B_FROM_PARTIALS;  // plain mode: H comes reduced, no W
 
   __shared__ __align__(16) float Hs[PM * PM];
-  __shared__ float Ws[PM * NMF_MAX_SKETCH];
-  __shared__ double red[kThreadsAll / 32];
+  __shared__ float Ws[PM * kWs];
+  __shared__ __align__(8) uint64_t pbar;
+  __shared__ float2 red[kThreadsAll / 32];
   __shared__ int flag_s;
   __shared__ StopShared stop_s;
   __shared__ double lam_s;
@@ -309,6 +412,10 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
   float* scratch = Ds + (stageD ? vecF : 0);         // partial sums, pending iterates, epilogue
 
   // ---- independent of the previous kernel ----
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&pbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   float y[PM], b[PM], f[PM];
 #pragma unroll
   for (int c = 0; c < PM; ++c) {
@@ -344,29 +451,66 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
 
   // ---- everything below may read what the previous kernel wrote ----
   pdl_wait();
-  if (call_failed(ctrl)) return;
+  if (__syncthreads_or(call_failed(ctrl))) return;  // also: the mbarrier is initialised
   pdl_launch_dependents();
 
   int iters = 0;
   float Lc = 0.f;
   double Lc_d = 0.0;
   if (kp.mode != MODE_EPI_ONLY) {
-    // Sum of the predecessor's partials, in a fixed order (same in every CTA).
+    // Sum of the predecessor's partials, in a fixed order (same in every CTA):
+    // one bulk copy of all partials into shared memory, then float4 sums over
+    // `slices` contiguous ranges of partials, then over the slices.
     const int P = gram ? p * p : p * nu;
+    const int P4 = partial_stride(P);
     const int G = a.groups_in;
-    float* Ps = scratch;  // [G][P]
-    {
-      const int total = G * P;
-      const float4* src4 = reinterpret_cast<const float4*>(a.part_in);
-      for (int i = tid; i < total / 4; i += NT) reinterpret_cast<float4*>(Ps)[i] = __ldcg(src4 + i);
-      for (int i = (total / 4) * 4 + tid; i < total; i += NT) Ps[i] = __ldcg(a.part_in + i);
+    float* Ps = scratch;          // [G][P4]
+    float* Rw = Ps + G * P4;      // [P4]: the reduced W (or H)
+    float* Red = Rw + P4;         // [slices][P4]
+    if (tid == 0) bulk_load(Ps, a.part_in, (uint32_t)(G * P4) * 4u, &pbar);
+    const bool got = mbar_wait_bounded(&pbar, 0u, ctrl);
+    if (__syncthreads_or(!got)) {
+      if (tid == 0) {
+        set_status(ctrl, NMF_ERR_DEVICE_TIMEOUT);
+        *((volatile int*)&ctrl->abort) = 1;
+        // the copy is in flight: wait for it (bounded) before leaving
+        const unsigned long long t0 = global_ns();
+        while (!mbar_done(&pbar, 0u) && global_ns() - t0 < kWaitNs) {
+        }
+      }
+      __syncthreads();
+      return;
     }
-    __syncthreads();
-    float* Rw = Ps + round_up(G * P, 4);  // the reduced W (or H)
-    for (int o = tid; o < P; o += NT) {
-      float s = 0.f;
-      for (int g = 0; g < G; ++g) s += Ps[(size_t)g * P + o];
-      Rw[o] = s;
+    {
+      const int Q = P4 / 4;
+      const int slices = max(1, min(G, NT / Q));
+      for (int idx = tid; idx < slices * Q; idx += NT) {
+        const int q = idx % Q, sl = idx / Q;
+        const int g0 = sl * G / slices, g1 = (sl + 1) * G / slices;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4* src = reinterpret_cast<const float4*>(Ps) + q;
+#pragma unroll 4
+        for (int g = g0; g < g1; ++g) {
+          const float4 v = src[(size_t)g * Q];
+          acc.x += v.x;
+          acc.y += v.y;
+          acc.z += v.z;
+          acc.w += v.w;
+        }
+        reinterpret_cast<float4*>(Red)[sl * Q + q] = acc;
+      }
+      __syncthreads();
+      for (int q = tid; q < Q; q += NT) {
+        float4 acc = reinterpret_cast<const float4*>(Red)[q];
+        for (int sl = 1; sl < slices; ++sl) {
+          const float4 v = reinterpret_cast<const float4*>(Red)[sl * Q + q];
+          acc.x += v.x;
+          acc.y += v.y;
+          acc.z += v.z;
+          acc.w += v.w;
+        }
+        reinterpret_cast<float4*>(Rw)[q] = acc;
+      }
     }
     __syncthreads();
     if (gram) {
@@ -377,13 +521,13 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
     } else {
       for (int i = tid; i < PM * nu; i += NT) {
         const int c = i / nu, k = i % nu;
-        Ws[c * NMF_MAX_SKETCH + k] = c < p ? Rw[c * nu + k] : 0.f;
+        Ws[c * kWs + k] = c < p ? Rw[c * nu + k] : 0.f;
       }
       __syncthreads();
       for (int i = tid; i < PM * PM; i += NT) {
         const int c = i / PM, d = i % PM;
         float s = 0.f;
-        for (int k = 0; k < nu; ++k) s = fmaf(Ws[c * NMF_MAX_SKETCH + k], Ws[d * NMF_MAX_SKETCH + k], s);
+        for (int k = 0; k < nu; ++k) s = fmaf(Ws[c * kWs + k], Ws[d * kWs + k], s);
         Hs[i] = s;
       }
     }
@@ -391,10 +535,8 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
     // L_c by the collector warp while the compute warps form B.
     if (kp.mode == MODE_SOLVE && !colthr) {
       const int ln = tid & 31;
-      float* Hp = Rw + P;  // H compacted to p x p for the eigenvalue routine
-      for (int i = ln; i < p * p; i += 32) Hp[i] = Hs[(i / p) * PM + i % p];
-      __syncwarp();
-      const double lam = lambda_max_warp<PM>(Hp, p);
+      float* Ms = Red;  // the slice sums are consumed: 2 PM lam_stride<PM>() scratch
+      const double lam = lambda_max_warp<PM>(Hs, Ms, p);
       if (ln == 0) lam_s = lam;
     }
     if (active) {
@@ -411,7 +553,7 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
         for (int k = 0; k < nu; ++k) {
           const float dk = Ds[k * kFs + tid];
 #pragma unroll
-          for (int c = 0; c < PM; ++c) b[c] = fmaf(Ws[c * NMF_MAX_SKETCH + k], dk, b[c]);
+          for (int c = 0; c < PM; ++c) b[c] = fmaf(Ws[c * kWs + k], dk, b[c]);
         }
       }
     }
@@ -433,7 +575,7 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
   if (kp.mode == MODE_EVAL) {
     float g[PM];
     hmatvec<PM>(Hs, f, b, g);
-    const double s = block_sum_double(active ? (double)pg_sq<PM>(f, g) : 0.0, red);
+    const double s = block_sum_df(active ? pg_sq<PM>(f, g) : 0.f, red);
     if (tid == 0) a.pg2_init[cta] = s;
   } else if (kp.mode == MODE_SOLVE && Lc > 0.f) {
     float g[PM], fp[PM], gp[PM];
@@ -443,6 +585,7 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
       fp[c] = y[c];
       gp[c] = g[c];
     }
+    float beta_next = __ldg(kp.beta);
     float* keep = scratch;  // [kKeep][PM][T]: iterates whose stop test is pending (per thread)
     const float inv_Lc = 1.f / Lc;
     const bool test = a.stop_test;
@@ -463,9 +606,10 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
       for (int k = 0; k < a.max_inner; ++k) {
 #pragma unroll
         for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
+        const float beta = beta_next;
+        if (k + 1 < a.max_inner) beta_next = __ldg(kp.beta + k + 1);  // in flight during the product
         float gf[PM];
         hmatvec<PM>(Hs, f, b, gf);
-        const float beta = __ldg(kp.beta + k);
 #pragma unroll
         for (int c = 0; c < PM; ++c) {
           y[c] = fmaf(beta, f[c] - fp[c], f[c]);
@@ -523,7 +667,7 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
     if (stop_j >= 0) {
       pg2_final = cta == 0 ? stop_s.dec_tot[stop_j % kStopSlots] : 0.0;  // the total is global: CTA 0 carries it
     } else {
-      pg2_final = block_sum_double(active ? (double)pg_sq<PM>(fp, gp) : 0.0, red);  // thread 0
+      pg2_final = block_sum_df(active ? pg_sq<PM>(fp, gp) : 0.f, red);  // thread 0
     }
   }
 
@@ -569,6 +713,7 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
   if (a.epi != EPI_NONE) {
     __syncthreads();  // scratch (pending iterates) is reused
     const int P = a.epi == EPI_GRAM ? p * p : p * nu;
+    const int P4 = partial_stride(P);
     float* Fs = scratch;  // [PM][kFs]
     if (colthr) {
 #pragma unroll
@@ -577,11 +722,24 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
     __syncthreads();
     const float* Os = a.epi == EPI_GRAM ? Fs : Es;
     const int ow = a.epi == EPI_GRAM ? p : nu;
-    for (int o = tid; o < P; o += NT) {
-      const int c = o / ow, k = o % ow;
+    for (int o = tid; o < P4; o += NT) {
       float s = 0.f;
-      for (int t = 0; t < T; ++t) s = fmaf(Fs[c * kFs + t], Os[k * kFs + t], s);
-      a.part_out[(size_t)cta * P + o] = s;
+      if (o < P) {
+        const int c = o / ow, k = o % ow;
+        const float4* fa = reinterpret_cast<const float4*>(Fs + c * kFs);
+        const float4* ob = reinterpret_cast<const float4*>(Os + k * kFs);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 8
+        for (int t4 = 0; t4 < T / 4; ++t4) {
+          const float4 x = fa[t4], z = ob[t4];
+          s0 = fmaf(x.x, z.x, s0);
+          s1 = fmaf(x.y, z.y, s1);
+          s2 = fmaf(x.z, z.z, s2);
+          s3 = fmaf(x.w, z.w, s3);
+        }
+        s = (s0 + s1) + (s2 + s3);
+      }
+      a.part_out[(size_t)cta * P4 + o] = s;
     }
     if (a.group > 1) {
       // large grids: the last CTA of each group sums the group's partials
@@ -593,10 +751,10 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
       __syncthreads();
       if (flag_s) {
         __threadfence();
-        for (int o = tid; o < P; o += NT) {
+        for (int o = tid; o < P4; o += NT) {
           float s = 0.f;
-          for (int i = 0; i < gsz; ++i) s += __ldcg(a.part_out + (size_t)(gi * a.group + i) * P + o);
-          a.group_out[(size_t)gi * P + o] = s;
+          for (int i = 0; i < gsz; ++i) s += __ldcg(a.part_out + (size_t)(gi * a.group + i) * P4 + o);
+          a.group_out[(size_t)gi * P4 + o] = s;
         }
         if (tid == 0) a.tail_ctr[gi] = 0u;
       }
@@ -618,8 +776,9 @@ size_t dyn_smem(const SolveArgs& a, int mode) {
   const bool stageD = mode != MODE_EPI_ONLY && !gram;
   size_t scratch = 0;
   if (mode != MODE_EPI_ONLY) {
-    const size_t P = gram ? (size_t)a.p * a.p : (size_t)a.p * a.nu;
-    scratch = round_up_sz((size_t)a.groups_in * P, 4) + 2 * P;  // partials, the sum, and H compacted
+    const size_t P4 = partial_stride(gram ? a.p * a.p : a.p * a.nu);
+    // partials, their sum, and the slice sums (reused as the eigenvalue scratch)
+    scratch = (size_t)a.groups_in * P4 + P4 + std::max({(size_t)4 * kThreadsAll, P4, (size_t)2 * PM * lam_stride<PM>()});
   }
   if (mode == MODE_SOLVE && a.stop_test) scratch = std::max(scratch, (size_t)kKeep * PM * T);
   if (a.epi != EPI_NONE) scratch = std::max(scratch, (size_t)PM * kFs);
