@@ -168,6 +168,50 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
                          size_t workspace_bytes);
 
 /* ------------------------------------------------------------------------ */
+/* Many independent compressed problems of different sizes (Alg. 1)          */
+/* ------------------------------------------------------------------------ */
+/*
+ * The same method as nenmf_solve in compressed mode, applied to `count`
+ * unrelated problems (each its own n, m, p, nu and L, R, X_L, X_R from
+ * nmf_compress) in one persistent launch: thread-block clusters of
+ * `cluster` CTAs each take a list of problems (assigned on the host,
+ * longest first, by an estimate of each problem's device time) and run all
+ * of a problem's outer iterations before the next. Results per problem are
+ * those of nenmf_solve with the same arguments up to float32 summation order.
+ */
+typedef struct nenmf_batch_config {
+  int cluster; /* CTAs per problem: 0 = chosen by the planner, else 1, 2, 4 or 8 */
+} nenmf_batch_config_t;
+
+/* Workspace bytes for nenmf_solve_batched with these arguments (0 on invalid
+ * arguments). problems, params and config (may be NULL) are host pointers. */
+size_t nenmf_solve_batched_workspace_size(int count, const nenmf_problem_t* problems,
+                                          const nenmf_params_t* params, const nenmf_batch_config_t* config);
+
+/* The plan nenmf_solve_batched would use: chosen->cluster and the number of
+ * clusters launched. Host-only; needs the device current for occupancy. */
+nmf_status_t nenmf_batch_plan_info(int count, const nenmf_problem_t* problems, const nenmf_params_t* params,
+                                   const nenmf_batch_config_t* config, nenmf_batch_config_t* chosen,
+                                   int* clusters);
+
+/*
+ *  problems  host array of `count` problems, all NENMF_COMPRESSED (plain
+ *            mode: NMF_ERR_UNSUPPORTED); 1 <= p <= nu <= NMF_MAX_SKETCH.
+ *  G, F      host arrays of `count` device pointers: G[i] n_i x p_i and
+ *            F[i] p_i x m_i, row-major, updated in place.
+ *  params    host pointer, shared by all problems; record_* must be NULL.
+ *            tol_mode NENMF_TOL_REL takes eps per problem from that
+ *            problem's initial projected gradient.
+ *  stats     device array of `count` entries (may be NULL).
+ * Stream-ordered; capturable in a CUDA graph (descriptors travel as kernel
+ * parameters). count == 0 returns NMF_OK without launching.
+ */
+nmf_status_t nenmf_solve_batched(nmf_stream_t stream, int count, const nenmf_problem_t* problems,
+                                 float* const* G, float* const* F, const nenmf_params_t* params,
+                                 const nenmf_batch_config_t* config, nenmf_stats_t* stats, void* workspace,
+                                 size_t workspace_bytes);
+
+/* ------------------------------------------------------------------------ */
 /* One pass over X, two products (the building block of Alg. 2)              */
 /* ------------------------------------------------------------------------ */
 size_t nmf_dual_product_workspace_size(int n, int m, int k, nmf_prec_t prec);

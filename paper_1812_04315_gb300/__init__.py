@@ -46,6 +46,10 @@ class Params(ctypes.Structure):
                 ("record_F", ctypes.c_void_p), ("record_time_ns", ctypes.c_void_p)]
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("cluster", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer_done", ctypes.c_int), ("last_inner", ctypes.c_int * 2),
                 ("total_inner", ctypes.c_longlong * 2), ("eps", ctypes.c_double), ("pg_norm", ctypes.c_double * 2),
@@ -80,6 +84,11 @@ def lib() -> ctypes.CDLL:
         "nmf_set_kernel_path": (None, [i]),
         "nmf_kernel_launches": (ctypes.c_longlong, []),
         "nmf_rre_static": (i, [vp, i, i, i, vp, vp, vp, vp]),
+        "nenmf_solve_batched_workspace_size": (sz, [i, vp, ctypes.POINTER(Params), ctypes.POINTER(BatchConfig)]),
+        "nenmf_batch_plan_info": (i, [i, vp, ctypes.POINTER(Params), ctypes.POINTER(BatchConfig),
+                                      ctypes.POINTER(BatchConfig), ctypes.POINTER(i)]),
+        "nenmf_solve_batched": (i, [vp, i, vp, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(BatchConfig), vp,
+                                    vp, sz]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -94,7 +103,8 @@ def exported_symbols():
     return ["nmf_status_string", "nmf_version", "nmf_workspace_status", "nmf_gaussian_sketch",
             "nmf_compress_workspace_size", "nmf_compress", "nenmf_solve_workspace_size", "nenmf_solve",
             "nmf_rre_workspace_size", "nmf_rre", "nmf_dual_product_workspace_size", "nmf_dual_product",
-            "nmf_set_kernel_path", "nmf_kernel_launches", "nmf_rre_static"]
+            "nmf_set_kernel_path", "nmf_kernel_launches", "nmf_rre_static",
+            "nenmf_solve_batched_workspace_size", "nenmf_batch_plan_info", "nenmf_solve_batched"]
 
 
 # ---------------------------------------------------------------------------
@@ -244,6 +254,56 @@ def solve(problem: Problem, G, F, max_outer: int, max_inner: int, min_inner: int
     _ok(lib().nenmf_solve(_stream(), ctypes.byref(problem), _ptr(G), _ptr(F), ctypes.byref(pa), _ptr(stats),
                           _ptr(ws), ws.numel()), "nenmf_solve")
     return stats
+
+
+def _batch_args(problems, max_outer, max_inner, min_inner, tol, tol_mode, cluster):
+    arr = (Problem * max(1, len(problems)))(*problems)
+    pa = Params()
+    pa.max_outer, pa.max_inner, pa.min_inner, pa.tol_mode, pa.tol = max_outer, max_inner, min_inner, tol_mode, tol
+    cfg = BatchConfig()
+    cfg.cluster = cluster
+    return arr, pa, cfg
+
+
+def batch_plan(problems, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
+               tol_mode: int = TOL_REL, cluster: int = 0):
+    """(CTAs per problem, clusters launched) that nenmf_solve_batched would use."""
+    arr, pa, cfg = _batch_args(problems, max_outer, max_inner, min_inner, tol, tol_mode, cluster)
+    out = BatchConfig()
+    ncl = ctypes.c_int(0)
+    _ok(lib().nenmf_batch_plan_info(len(problems), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(pa),
+                                    ctypes.byref(cfg), ctypes.byref(out), ctypes.byref(ncl)), "nenmf_batch_plan_info")
+    return out.cluster, ncl.value
+
+
+def solve_batched(problems, Gs, Fs, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
+                  tol_mode: int = TOL_REL, cluster: int = 0, stats=None, ws=None):
+    """Runs nenmf_solve_batched in place on every (G_i, F_i); returns the device stats buffer (count entries)."""
+    torch = _torch()
+    count = len(problems)
+    if len(Gs) != count or len(Fs) != count:
+        raise ValueError("one G and one F per problem")
+    for pr, G, F in zip(problems, Gs, Fs):
+        _check_f32("G", G, (pr.n, pr.p))
+        _check_f32("F", F, (pr.p, pr.m))
+    arr, pa, cfg = _batch_args(problems, max_outer, max_inner, min_inner, tol, tol_mode, cluster)
+    gp = (ctypes.c_void_p * max(1, count))(*[G.data_ptr() for G in Gs])
+    fp = (ctypes.c_void_p * max(1, count))(*[F.data_ptr() for F in Fs])
+    if stats is None:
+        stats = torch.zeros(max(1, count) * ctypes.sizeof(Stats), dtype=torch.uint8, device="cuda")
+    if ws is None:
+        ws = workspace(lib().nenmf_solve_batched_workspace_size(count, ctypes.cast(arr, ctypes.c_void_p),
+                                                                ctypes.byref(pa), ctypes.byref(cfg)))
+    _ok(lib().nenmf_solve_batched(_stream(), count, ctypes.cast(arr, ctypes.c_void_p), ctypes.cast(gp, ctypes.c_void_p),
+                                  ctypes.cast(fp, ctypes.c_void_p), ctypes.byref(pa), ctypes.byref(cfg), _ptr(stats),
+                                  _ptr(ws), ws.numel()), "nenmf_solve_batched")
+    return stats
+
+
+def read_batch_stats(stats, count: int):
+    raw = bytes(stats.cpu().numpy().tobytes())
+    k = ctypes.sizeof(Stats)
+    return [Stats.from_buffer_copy(raw[i * k:(i + 1) * k]) for i in range(count)]
 
 
 def read_stats(stats) -> Stats:

@@ -14,11 +14,6 @@ using namespace nmf;
 
 namespace {
 
-#define NMF_CU(call)                                   \
-  do {                                                 \
-    cudaError_t e_ = (call);                           \
-    if (e_ != cudaSuccess) return NMF_ERR_CUDA;        \
-  } while (0)
 
 int g_force_simt = 0;  // nmf_set_kernel_path
 

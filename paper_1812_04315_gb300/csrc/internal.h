@@ -7,6 +7,13 @@
 
 #include "common.cuh"
 
+// Returns NMF_ERR_CUDA from the enclosing entry point when a runtime call fails.
+#define NMF_CU(call)                                   \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return NMF_ERR_CUDA;        \
+  } while (0)
+
 namespace nmf {
 
 // ---------------------------------------------------------------------------

@@ -31,6 +31,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "nnls_device.cuh"
 
 namespace nmf {
 namespace {
@@ -39,7 +40,6 @@ constexpr int T = kSolveThreads;
 constexpr int kLag = 4;
 constexpr int kKeep = kLag + 1;
 static_assert(kStopSlots >= 2 * kLag + 1, "stop-test slots are reused after kStopSlots tests");
-constexpr int kMaxSquarings = 16;
 constexpr int kFs = T + 4;                  // column-vector rows: 16-byte aligned, rows 4 banks apart
 constexpr int kWs = NMF_MAX_SKETCH + 1;     // rows of W: consecutive rows in different banks
 constexpr unsigned long long kWaitNs = 2000000000ull;
@@ -72,39 +72,6 @@ __device__ __forceinline__ double block_sum_df(float v, float2* red) {
   if (threadIdx.x == 0)
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) df_add(t, red[i].x, red[i].y);
   return (double)t.hi + (double)t.lo;
-}
-
-// g = H y - b with the symmetric H (PM x PM, zero padded) in shared memory:
-// row d of H is column d, so g accumulates y_d times row d (read as float4)
-// over d; the PM sums advance together and hide each other's latency.
-template <int PM>
-__device__ __forceinline__ void hmatvec(const float* Hs, const float* y, const float* b, float* g) {
-#pragma unroll
-  for (int c = 0; c < PM; ++c) g[c] = -b[c];
-#pragma unroll
-  for (int d = 0; d < PM; ++d) {
-    const float4* h = reinterpret_cast<const float4*>(Hs + d * PM);
-    const float yd = y[d];
-#pragma unroll
-    for (int c4 = 0; c4 < PM / 4; ++c4) {
-      const float4 v = h[c4];
-      g[4 * c4 + 0] = fmaf(v.x, yd, g[4 * c4 + 0]);
-      g[4 * c4 + 1] = fmaf(v.y, yd, g[4 * c4 + 1]);
-      g[4 * c4 + 2] = fmaf(v.z, yd, g[4 * c4 + 2]);
-      g[4 * c4 + 3] = fmaf(v.w, yd, g[4 * c4 + 3]);
-    }
-  }
-}
-
-template <int PM>
-__device__ __forceinline__ float pg_sq(const float* f, const float* g) {
-  float s = 0.f;
-#pragma unroll
-  for (int c = 0; c < PM; ++c) {
-    const float v = f[c] > 0.f ? g[c] : fminf(g[c], 0.f);
-    s = fmaf(v, v, s);
-  }
-  return s;
 }
 
 // Stop test. Compute warps post their ||P grad||^2 partial of test j in
@@ -221,129 +188,6 @@ __device__ __forceinline__ int wait_decision(StopShared& S, int j, Control* c) {
   }
   __threadfence_block();
   return *((volatile int*)&S.dec_val[sl]);
-}
-
-// Row stride of the squaring buffers: PM or PM + 4, whichever is an odd
-// number of float4s, so rows read as float4 by eight lanes hit eight
-// different bank groups.
-template <int PM>
-__host__ __device__ constexpr int lam_stride() { return ((PM / 4) & 1) ? PM : PM + 4; }
-
-// lambda_max of the symmetric PSD matrix H (PM x PM in shared memory, zero
-// outside p x p), by one warp. Repeated squaring with trace normalisation:
-// A_0 = H, A_{s+1} = (A_s / tr A_s)^2; the lanes share the PM (PM + 1) / 2
-// entries of the upper triangle (A stays symmetric), each a dot product of
-// two rows. tr(A_{s+1}) = tr(M^2) for the trace-one M = A_s / tr(A_s), which
-// reaches 1 exactly when M has rank one; at 1 - tr(M^2) < 1e-5 the other
-// eigenvectors' share in the dominant column is < 1e-5, so its Rayleigh
-// quotient (float-float arithmetic) is exact to ~1e-10. Ms is 2 PM
-// lam_stride<PM>() floats of 16-byte aligned scratch. The result is valid in
-// every lane; 0 for H = 0, non-finite for a non-finite H.
-template <int PM>
-__device__ double lambda_max_warp(const float* Hs, float* Ms, int p) {
-  constexpr int LS = lam_stride<PM>();
-  constexpr int E = PM * (PM + 1) / 2;
-  constexpr int NPL = (E + 31) / 32;
-  const int lane = threadIdx.x & 31;
-  const float tr = warp_sum(lane < p ? Hs[lane * PM + lane] : 0.f);
-  if (!(tr > 0.f) || !isfinite(tr)) return isfinite(tr) ? 0.0 : (double)tr;
-  float* A = Ms;
-  float* B = Ms + PM * LS;
-  for (int i = lane; i < PM * PM; i += 32) A[(i / PM) * LS + i % PM] = Hs[i];
-  // this lane's upper-triangle entries (i << 8 | j), -1 past the end
-  int pr[NPL];
-  {
-    int i = 0, e = lane;
-#pragma unroll
-    for (int q = 0; q < NPL; ++q) {
-      while (i < PM && e >= PM - i) {
-        e -= PM - i;
-        ++i;
-      }
-      pr[q] = i < PM ? (i << 8) | (i + e) : -1;
-      e += 32;
-    }
-  }
-  __syncwarp();
-  float t = tr;
-  for (int s = 0; s < kMaxSquarings; ++s) {
-    const float sc = __fdividef(1.f, t);  // any positive scale normalises; t2 below is measured
-    const float sc2 = sc * sc;
-    float dsum = 0.f;
-#pragma unroll
-    for (int q = 0; q < NPL; ++q) {
-      if (pr[q] < 0) continue;
-      const int i = pr[q] >> 8, j = pr[q] & 255;
-      const float4* ri = reinterpret_cast<const float4*>(A + i * LS);
-      const float4* rj = reinterpret_cast<const float4*>(A + j * LS);
-      float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-      for (int d4 = 0; d4 < PM / 4; ++d4) {
-        const float4 x = ri[d4], z = rj[d4];
-        s0 = fmaf(x.x, z.x, s0);
-        s1 = fmaf(x.y, z.y, s1);
-        s0 = fmaf(x.z, z.z, s0);
-        s1 = fmaf(x.w, z.w, s1);
-      }
-      const float v = (s0 + s1) * sc2;
-      B[i * LS + j] = v;
-      B[j * LS + i] = v;
-      if (i == j) dsum += v;
-    }
-    const float t2 = warp_sum(dsum);  // trace of the new A (= tr(M^2), tr(M) = 1 to rounding)
-    __syncwarp();                      // every lane has read A and written B
-    float* tmp = A;
-    A = B;
-    B = tmp;
-    t = t2;
-    if (!(t2 > 0.f) || 1.f - t2 < 1e-5f) break;
-  }
-  // dominant column jb = argmax diag(A); v_c = A[c][jb] = A[jb][c]
-  float best = lane < p ? A[lane * LS + lane] : -1.f;
-  int jb = lane;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
-    if (ob > best || (ob == best && oj < jb)) {
-      best = ob;
-      jb = oj;
-    }
-  }
-  const float* vrow = A + jb * LS;  // v (broadcast reads)
-  const float vc = lane < p ? vrow[lane] : 0.f;
-  // (H v)_c, then v^T H v and v^T v, all in float-float
-  DF hv{0.f, 0.f};
-  if (lane < p) {
-#pragma unroll
-    for (int d = 0; d < PM; ++d) df_add_product(hv, Hs[lane * PM + d], vrow[d]);
-  }
-  DF num{0.f, 0.f}, den{0.f, 0.f};
-  df_add_product(num, vc, hv.hi);
-  num.lo = fmaf(vc, hv.lo, num.lo);
-  df_add_product(den, vc, vc);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float nh = __shfl_xor_sync(0xffffffffu, num.hi, o), nl = __shfl_xor_sync(0xffffffffu, num.lo, o);
-    const float dh = __shfl_xor_sync(0xffffffffu, den.hi, o), dl = __shfl_xor_sync(0xffffffffu, den.lo, o);
-    // the lower lane's value first, so both lanes compute the same sum
-    DF a = (lane & o) ? DF{nh, nl} : num, b = (lane & o) ? num : DF{nh, nl};
-    df_add(a, b.hi, b.lo);
-    num = a;
-    a = (lane & o) ? DF{dh, dl} : den;
-    b = (lane & o) ? den : DF{dh, dl};
-    df_add(a, b.hi, b.lo);
-    den = a;
-  }
-  df_norm(num);
-  df_norm(den);
-  if (!(den.hi > 0.f)) return 0.0;
-  // num / den in float-float: q0, then one correction from the exact residual
-  const float q0 = num.hi / den.hi;
-  const float ph = q0 * den.hi;
-  const float pe = fmaf(q0, den.hi, -ph);
-  const float r = ((num.hi - ph) - pe) + (num.lo - q0 * den.lo);
-  return (double)q0 + (double)(r / den.hi);
 }
 
 // Bulk copy global -> shared (async proxy), completion counted on an mbarrier.

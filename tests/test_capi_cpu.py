@@ -76,3 +76,28 @@ def test_argument_errors_are_host_side(L):
     assert L.nenmf_solve(None, None, None, None, None, None, None, 0) == 1
     assert L.nmf_rre(None, 10, 10, 0, v(256), v(256), v(256), v(256), v(256), 1 << 20) == 1
     assert L.nmf_dual_product(None, 10, 10, 4, 0, v(256), None, None, None, None, v(256), 1 << 30) == 1
+
+
+def test_batched_argument_errors_are_host_side(L):
+    import paper_1812_04315_gb300 as pkg
+    pr = pkg._problem(pkg.COMPRESSED, 100, 90, 4, 8, 0)
+    pr.L = pr.R = pr.XL = pr.XR = 256
+    arr, pa, cfg = pkg._batch_args([pr], 5, 10, 1, 0.0, pkg.TOL_REL, 0)
+    ptrs = (ctypes.c_void_p * 1)(256)
+    args = lambda arr_, n=1: (None, n, ctypes.cast(arr_, ctypes.c_void_p), ctypes.cast(ptrs, ctypes.c_void_p),
+                              ctypes.cast(ptrs, ctypes.c_void_p), ctypes.byref(pa), ctypes.byref(cfg), None,
+                              ctypes.c_void_p(256), 1 << 30)
+    assert L.nenmf_solve_batched(*args(arr, -1)) == 1
+    plain = pkg._problem(pkg.PLAIN, 100, 90, 4, 0, 0)
+    plain.X = 256
+    arr2, _, _ = pkg._batch_args([plain], 5, 10, 1, 0.0, pkg.TOL_REL, 0)
+    assert L.nenmf_solve_batched(*args(arr2)) == 7          # plain mode: unsupported in a batch
+    bad = pkg._problem(pkg.COMPRESSED, 100, 90, 9, 8, 0)    # nu < p
+    bad.L = bad.R = bad.XL = bad.XR = 256
+    arr3, _, _ = pkg._batch_args([bad], 5, 10, 1, 0.0, pkg.TOL_REL, 0)
+    assert L.nenmf_solve_batched(*args(arr3)) == 1
+    pa.record_G = 256                                        # snapshots are single-problem only
+    assert L.nenmf_solve_batched(*args(arr)) == 1
+    pa.record_G = None
+    cfg.cluster = 3
+    assert L.nenmf_solve_batched(*args(arr)) == 1

@@ -1,0 +1,135 @@
+"""GPU parity of nenmf_solve_batched (many compressed problems, Alg. 1) against the FP64 oracle.
+
+Every problem of a batch gets its own float32 L, R, X_L, X_R (the oracle's
+Alg. 2 on the problem's X) and initial factors. Per problem the batched
+result is compared with the oracle's compressed NeNMF on the same float32
+inputs: final RRE (eq. 4) within 1e-5 (the float32 tolerance); after one
+outer iteration the factors within 1e-4 relative (float32 rounding through
+<= 10 Nesterov steps); with the stop test on, eps and the inner-iteration
+counts (a count may move by one where a test sits at the threshold).
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import metrics, nenmf, subspace
+
+pytestmark = pytest.mark.gpu
+
+# uneven shapes: (n, m, p, nu, q)
+SHAPES = [(120, 90, 3, 8, 1), (333, 200, 6, 10, 2), (64, 500, 5, 9, 1), (257, 129, 12, 20, 2),
+          (40, 41, 1, 4, 1), (300, 310, 16, 26, 1), (1, 37, 1, 1, 1)]
+
+
+def _t(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def _np(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _problem_inputs(n, m, p, nu, q, seed):
+    X, _, _ = synth.lowrank_data(n, m, p, seed=seed, snr_db=20.0, dtype=np.float32)
+    G0, F0 = synth.initial_factors(n, m, p, seed=seed + 1)
+    OmL, OmR = synth.gaussian_sketches(n, m, nu, seed=seed + 2)
+    L, R, XL, XR = (a.astype(np.float32) for a in subspace.compress(X.astype(np.float64), nu, q, OmL, OmR))
+    return dict(X=X, G0=G0.astype(np.float32), F0=F0.astype(np.float32), L=L, R=R, XL=XL, XR=XR, p=p)
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return [_problem_inputs(*s, seed=17 * i + 3) for i, s in enumerate(SHAPES)]
+
+
+def _run(nmf, batch, T, inner, tol=0.0, cluster=0, min_inner=1):
+    probs, Gs, Fs = [], [], []
+    for b in batch:
+        probs.append(nmf.compressed_problem(_t(b["L"]), _t(b["R"]), _t(b["XL"]), _t(b["XR"]), b["p"]))
+        Gs.append(_t(b["G0"]))
+        Fs.append(_t(b["F0"]))
+    st = nmf.solve_batched(probs, Gs, Fs, T, inner, min_inner=min_inner, tol=tol, cluster=cluster)
+    return Gs, Fs, nmf.read_batch_stats(st, len(batch))
+
+
+def _oracle(b, T, inner, tol=0.0, min_inner=1):
+    return nenmf.nenmf_compressed(b["L"], b["R"], b["XL"], b["XR"], b["G0"], b["F0"], T, inner,
+                                  min_inner=min_inner, tol=tol)
+
+
+@pytest.mark.parametrize("T,inner,tol", [(8, 10, 0.0), (8, 10, 1e-3), (5, 40, 1e-6), (4, 20, 0.0), (6, 1, 0.0)])
+def test_batched_matches_oracle(nmf, batch, T, inner, tol):
+    Gs, Fs, stats = _run(nmf, batch, T, inner, tol)
+    for b, G, F, st in zip(batch, Gs, Fs, stats):
+        assert st.status == 0 and st.outer_done == T
+        Go, Fo, info = _oracle(b, T, inner, tol)
+        Xd = b["X"].astype(np.float64)
+        r_gpu = metrics.rre(Xd, _np(G), _np(F))
+        r_ora = metrics.rre(Xd, Go, Fo)
+        assert abs(r_gpu - r_ora) <= 1e-5, (b["X"].shape, r_gpu, r_ora)
+        assert (_np(G) >= 0).all() and (_np(F) >= 0).all()
+        if tol > 0:
+            assert st.eps == pytest.approx(info["eps"], rel=1e-4)
+            ora = sum(a + c for a, c in info["inner"])
+            assert abs(st.total_inner[0] + st.total_inner[1] - ora) <= 2
+        else:
+            assert st.total_inner[0] == T * inner and st.total_inner[1] == T * inner
+
+
+def test_batched_first_outer_iteration_factors(nmf, batch):
+    Gs, Fs, _ = _run(nmf, batch, 1, 10)
+    for b, G, F in zip(batch, Gs, Fs):
+        Go, Fo, _ = _oracle(b, 1, 10)
+        assert np.linalg.norm(_np(G) - Go) <= 1e-4 * np.linalg.norm(Go) + 1e-7
+        assert np.linalg.norm(_np(F) - Fo) <= 1e-4 * np.linalg.norm(Fo) + 1e-7
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+def test_cluster_sizes_agree(nmf, batch, cluster):
+    # a different cluster size splits the sums differently: float32 rounding only
+    Gs, Fs, stats = _run(nmf, batch, 6, 10, cluster=cluster)
+    for b, G, F, st in zip(batch, Gs, Fs, stats):
+        assert st.status == 0
+        Go, Fo, _ = _oracle(b, 6, 10)
+        Xd = b["X"].astype(np.float64)
+        assert abs(metrics.rre(Xd, _np(G), _np(F)) - metrics.rre(Xd, Go, Fo)) <= 1e-5
+
+
+def test_batched_is_deterministic(nmf, batch):
+    G1, F1, _ = _run(nmf, batch, 5, 10, tol=1e-4)
+    G2, F2, _ = _run(nmf, batch, 5, 10, tol=1e-4)
+    for a, b in zip(G1 + F1, G2 + F2):
+        assert bool((a == b).all())
+
+
+def test_batched_matches_single_problem_solver(nmf, batch):
+    T, inner = 6, 10
+    Gs, Fs, _ = _run(nmf, batch, T, inner, tol=1e-5)
+    for b, G, F in zip(batch, Gs, Fs):
+        G1, F1 = _t(b["G0"]), _t(b["F0"])
+        pr = nmf.compressed_problem(_t(b["L"]), _t(b["R"]), _t(b["XL"]), _t(b["XR"]), b["p"])
+        nmf.solve(pr, G1, F1, T, inner, tol=1e-5)
+        Xd = b["X"].astype(np.float64)
+        assert abs(metrics.rre(Xd, _np(G), _np(F)) - metrics.rre(Xd, _np(G1), _np(F1))) <= 1e-5
+
+
+def test_empty_batch_and_zero_outer(nmf, batch):
+    nmf.solve_batched([], [], [], 5, 10)
+    Gs, Fs, stats = _run(nmf, batch[:3], 0, 10)
+    for b, G, F, st in zip(batch[:3], Gs, Fs, stats):
+        np.testing.assert_array_equal(_np(G), b["G0"])
+        np.testing.assert_array_equal(_np(F), b["F0"])
+        assert st.outer_done == 0
+
+
+def test_zero_factor_keeps_the_other(nmf, batch):
+    # F = 0 makes H_G = 0 (L_c = 0): the G update keeps G, as in the oracle
+    b = dict(batch[1])
+    b["F0"] = np.zeros_like(b["F0"])
+    Gs, Fs, stats = _run(nmf, [b], 1, 10)
+    Go, Fo, _ = _oracle(b, 1, 10)
+    np.testing.assert_allclose(_np(Gs[0]), Go, rtol=1e-4, atol=1e-6)
+    np.testing.assert_allclose(_np(Fs[0]), Fo, rtol=1e-4, atol=1e-6)
+    assert stats[0].status == 0
