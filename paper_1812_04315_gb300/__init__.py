@@ -276,6 +276,13 @@ def batch_plan(problems, max_outer: int, max_inner: int, min_inner: int = 1, tol
     return out.cluster, ncl.value
 
 
+def batch_workspace_size(problems, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
+                         tol_mode: int = TOL_REL, cluster: int = 0) -> int:
+    arr, pa, cfg = _batch_args(problems, max_outer, max_inner, min_inner, tol, tol_mode, cluster)
+    return int(lib().nenmf_solve_batched_workspace_size(len(problems), ctypes.cast(arr, ctypes.c_void_p),
+                                                        ctypes.byref(pa), ctypes.byref(cfg)))
+
+
 def solve_batched(problems, Gs, Fs, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
                   tol_mode: int = TOL_REL, cluster: int = 0, stats=None, ws=None):
     """Runs nenmf_solve_batched in place on every (G_i, F_i); returns the device stats buffer (count entries)."""
@@ -292,8 +299,7 @@ def solve_batched(problems, Gs, Fs, max_outer: int, max_inner: int, min_inner: i
     if stats is None:
         stats = torch.zeros(max(1, count) * ctypes.sizeof(Stats), dtype=torch.uint8, device="cuda")
     if ws is None:
-        ws = workspace(lib().nenmf_solve_batched_workspace_size(count, ctypes.cast(arr, ctypes.c_void_p),
-                                                                ctypes.byref(pa), ctypes.byref(cfg)))
+        ws = workspace(batch_workspace_size(problems, max_outer, max_inner, min_inner, tol, tol_mode, cluster))
     _ok(lib().nenmf_solve_batched(_stream(), count, ctypes.cast(arr, ctypes.c_void_p), ctypes.cast(gp, ctypes.c_void_p),
                                   ctypes.cast(fp, ctypes.c_void_p), ctypes.byref(pa), ctypes.byref(cfg), _ptr(stats),
                                   _ptr(ws), ws.numel()), "nenmf_solve_batched")

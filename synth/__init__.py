@@ -81,6 +81,33 @@ def lowrank_data(n: int, m: int, p: int, seed: int, snr_db: float | None = None,
     return X, G0, F0
 
 
+def lowrank_data_device(n: int, m: int, p: int, seed: int, snr_db: float | None = None,
+                        zero_frac: float = 0.0, device: str = "cuda"):
+    """Device-resident float32 X with the recipe of lowrank_data, for batches too large to draw on the host.
+
+    G0 and F0 are the host streams of source_factors (identical to
+    lowrank_data's); the noise Z is drawn by torch's generator on `device`,
+    seeded from (seed, noise tag), so X is reproducible but its noise is not
+    lowrank_data's bytes. c is set from the float64 norms so that the SNR is
+    exact. Returns (X, G0, F0) with X a torch tensor.
+    """
+    import torch
+    G0, F0 = source_factors(n, m, p, seed, zero_frac)
+    Gd = torch.from_numpy(G0).to(device)
+    Fd = torch.from_numpy(F0).to(device)
+    X = Gd @ Fd
+    if snr_db is not None:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(int(rng(seed, _TAG_NOISE).integers(0, 2**63 - 1)))
+        Z = torch.randn((n, m), generator=gen, device=device, dtype=torch.float32).abs_()
+        signal_sq = float(np.sum((G0.T @ G0) * (F0 @ F0.T)))
+        noise_sq = float(torch.sum(Z.double() ** 2))
+        c = np.sqrt(signal_sq / noise_sq) * 10.0 ** (-snr_db / 20.0)
+        X += c * Z.double()
+        del Z
+    return X.float().contiguous(), G0, F0
+
+
 def initial_factors(n: int, m: int, p: int, seed: int):
     """Initial G (n x p) and F (p x m), iid Uniform[0,1], float64."""
     return rng(seed, _TAG_INIT_G).random((n, p)), rng(seed, _TAG_INIT_F).random((p, m))

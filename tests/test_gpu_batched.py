@@ -133,3 +133,46 @@ def test_zero_factor_keeps_the_other(nmf, batch):
     np.testing.assert_allclose(_np(Gs[0]), Go, rtol=1e-4, atol=1e-6)
     np.testing.assert_allclose(_np(Fs[0]), Fo, rtol=1e-4, atol=1e-6)
     assert stats[0].status == 0
+
+
+def test_full_size_batch(nmf):
+    # The batched workload at full size: 256 problems, n ~ U[1000, 8000],
+    # m ~ U[500, 4000], p ~ U{4..16}, nu = p + 10, q = 2, 20 dB, bfloat16
+    # compression, 50 outer iterations (inner <= 10, tol 1e-6). X is drawn on
+    # the device; sampled problems keep theirs for the checks.
+    import torch
+    shapes = synth.batched_shapes(256, seed=0)
+    sizes = [s["n"] * s["m"] for s in shapes]
+    sample = {int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 128}
+    probs, Gs, Fs, G0s, F0s, kept = [], [], [], [], [], {}
+    for i, sh in enumerate(shapes):
+        X, _, _ = synth.lowrank_data_device(sh["n"], sh["m"], sh["p"], seed=1000 + i, snr_db=20.0)
+        L, R, XL, XR = nmf.compress(X, sh["nu"], 2, prec=1, seed=5000 + i)
+        G0, F0 = synth.initial_factors(sh["n"], sh["m"], sh["p"], seed=9000 + i)
+        probs.append(nmf.compressed_problem(L, R, XL, XR, sh["p"]))
+        G0s.append(G0.astype(np.float32))
+        F0s.append(F0.astype(np.float32))
+        Gs.append(_t(G0))
+        Fs.append(_t(F0))
+        if i in sample:
+            kept[i] = (X, L, R, XL, XR)
+        else:
+            del X
+    T, inner, tol = 50, 10, 1e-6
+    stats = nmf.read_batch_stats(nmf.solve_batched(probs, Gs, Fs, T, inner, tol=tol), len(probs))
+    torch.cuda.synchronize()
+    for st, G, F in zip(stats, Gs, Fs):
+        assert st.status == 0 and st.outer_done == T
+        assert bool(torch.isfinite(G).all()) and bool((G >= 0).all()) and bool((F >= 0).all())
+    for i, (X, L, R, XL, XR) in kept.items():
+        G1, F1 = _t(G0s[i]), _t(F0s[i])
+        nmf.solve(probs[i], G1, F1, T, inner, tol=tol)
+        r_b, r_s = nmf.rre(X, Gs[i], Fs[i]), nmf.rre(X, G1, F1)
+        assert abs(r_b - r_s) <= 1e-5, (i, r_b, r_s)
+        assert r_b < 0.5 * nmf.rre(X, _t(G0s[i]), _t(F0s[i]))
+    # the smallest problem against the oracle on the same float32 compressed inputs
+    i = int(np.argmin(sizes))
+    X, L, R, XL, XR = kept[i]
+    Go, Fo, _ = nenmf.nenmf_compressed(_np(L), _np(R), _np(XL), _np(XR), G0s[i], F0s[i], T, inner, tol=tol)
+    Xd = _np(X)
+    assert abs(metrics.rre(Xd, _np(Gs[i]), _np(Fs[i])) - metrics.rre(Xd, Go, Fo)) <= 1e-5
