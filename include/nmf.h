@@ -212,6 +212,40 @@ nmf_status_t nenmf_solve_batched(nmf_stream_t stream, int count, const nenmf_pro
                                  size_t workspace_bytes);
 
 /* ------------------------------------------------------------------------ */
+/* Reverse-mode derivative of the compressed solve (Alg. 1, Sec. 2)          */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper defines no derivative; this differentiates the map
+ * (X_L, X_R, G0, F0) -> (G_T, F_T) of nenmf_solve in compressed mode with
+ * the stop test off (every inner solve runs max_inner iterations), holding
+ * L and R fixed. Conventions: max(0, z) has derivative 1[z > 0];
+ * L_c = lambda_max(H) has derivative v v^T (v its unit eigenvector). The
+ * forward's inner iterations are recomputed from the per-outer snapshots.
+ *
+ * Workspace bytes for nenmf_backward (0 on invalid arguments).
+ */
+size_t nenmf_backward_workspace_size(const nenmf_problem_t* problem, const nenmf_params_t* params);
+
+/*
+ *  problem             host pointer, NENMF_COMPRESSED (else NMF_ERR_UNSUPPORTED).
+ *  params              host pointer: max_outer T and max_inner K of the forward;
+ *                      tol must be <= 0 (NMF_ERR_INVALID_ARG otherwise).
+ *  G0, F0              the forward's initial factors (n x p, p x m).
+ *  record_G, record_F  the forward's snapshots [T][n][p] and [T][p][m]
+ *                      (nenmf_solve with params->record_G / record_F set).
+ *  dG_T, dF_T          cotangents of the returned G_T and F_T.
+ *  dXL, dXR            out: cotangents of X_L (nu x m) and X_R (n x nu).
+ *  dG0, dF0            out: cotangents of G0 and F0.
+ *  dX                  optional out (may be NULL): n x m, L^T dXL + dXR R^T,
+ *                      the cotangent of X through X_L = L X and X_R = X R.
+ * All device pointers, row-major, distinct buffers; stream-ordered.
+ */
+nmf_status_t nenmf_backward(nmf_stream_t stream, const nenmf_problem_t* problem, const nenmf_params_t* params,
+                            const float* G0, const float* F0, const float* record_G, const float* record_F,
+                            const float* dG_T, const float* dF_T, float* dXL, float* dXR, float* dG0,
+                            float* dF0, float* dX, void* workspace, size_t workspace_bytes);
+
+/* ------------------------------------------------------------------------ */
 /* One pass over X, two products (the building block of Alg. 2)              */
 /* ------------------------------------------------------------------------ */
 size_t nmf_dual_product_workspace_size(int n, int m, int k, nmf_prec_t prec);

@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(BatchConfig), ctypes.POINTER(i)]),
         "nenmf_solve_batched": (i, [vp, i, vp, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(BatchConfig), vp,
                                     vp, sz]),
+        "nenmf_backward_workspace_size": (sz, [ctypes.POINTER(Problem), ctypes.POINTER(Params)]),
+        "nenmf_backward": (i, [vp, ctypes.POINTER(Problem), ctypes.POINTER(Params)] + [vp] * 11 + [vp, sz]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -104,7 +106,8 @@ def exported_symbols():
             "nmf_compress_workspace_size", "nmf_compress", "nenmf_solve_workspace_size", "nenmf_solve",
             "nmf_rre_workspace_size", "nmf_rre", "nmf_dual_product_workspace_size", "nmf_dual_product",
             "nmf_set_kernel_path", "nmf_kernel_launches", "nmf_rre_static",
-            "nenmf_solve_batched_workspace_size", "nenmf_batch_plan_info", "nenmf_solve_batched"]
+            "nenmf_solve_batched_workspace_size", "nenmf_batch_plan_info", "nenmf_solve_batched",
+            "nenmf_backward_workspace_size", "nenmf_backward"]
 
 
 # ---------------------------------------------------------------------------
@@ -304,6 +307,35 @@ def solve_batched(problems, Gs, Fs, max_outer: int, max_inner: int, min_inner: i
                                   ctypes.cast(fp, ctypes.c_void_p), ctypes.byref(pa), ctypes.byref(cfg), _ptr(stats),
                                   _ptr(ws), ws.numel()), "nenmf_solve_batched")
     return stats
+
+
+def backward(problem: Problem, G0, F0, record: SolveRecord, dG_T, dF_T, max_outer: int, max_inner: int,
+             want_dX: bool = False, ws=None):
+    """nenmf_backward: cotangents (dXL, dXR, dG0, dF0, dX or None) of the compressed solve's
+    inputs, given those of its outputs and the forward's snapshots (fixed inner iterations)."""
+    torch = _torch()
+    n, m, p, nu = problem.n, problem.m, problem.p, problem.nu
+    for name, t, shp in (("G0", G0, (n, p)), ("F0", F0, (p, m)), ("dG_T", dG_T, (n, p)), ("dF_T", dF_T, (p, m))):
+        _check_f32(name, t, shp)
+    if max_outer > 0:
+        _check_f32("record.G", record.G, (max_outer, n, p))
+        _check_f32("record.F", record.F, (max_outer, p, m))
+    pa = Params()
+    pa.max_outer, pa.max_inner, pa.min_inner, pa.tol_mode, pa.tol = max_outer, max_inner, 1, TOL_REL, 0.0
+    dev = G0.device
+    dXL = torch.empty((nu, m), dtype=torch.float32, device=dev)
+    dXR = torch.empty((n, nu), dtype=torch.float32, device=dev)
+    dG0 = torch.empty((n, p), dtype=torch.float32, device=dev)
+    dF0 = torch.empty((p, m), dtype=torch.float32, device=dev)
+    dX = torch.empty((n, m), dtype=torch.float32, device=dev) if want_dX else None
+    if ws is None:
+        ws = workspace(lib().nenmf_backward_workspace_size(ctypes.byref(problem), ctypes.byref(pa)))
+    rg = _ptr(record.G) if max_outer > 0 else None
+    rf = _ptr(record.F) if max_outer > 0 else None
+    _ok(lib().nenmf_backward(_stream(), ctypes.byref(problem), ctypes.byref(pa), _ptr(G0), _ptr(F0), rg, rf,
+                             _ptr(dG_T), _ptr(dF_T), _ptr(dXL), _ptr(dXR), _ptr(dG0), _ptr(dF0), _ptr(dX),
+                             _ptr(ws), ws.numel()), "nenmf_backward")
+    return dXL, dXR, dG0, dF0, dX
 
 
 def read_batch_stats(stats, count: int):

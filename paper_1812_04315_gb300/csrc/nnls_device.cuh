@@ -82,9 +82,11 @@ __host__ __device__ constexpr int lam_stride() { return ((PM / 4) & 1) ? PM : PM
 // eigenvectors' share in the dominant column is < 1e-5, so its Rayleigh
 // quotient (float-float arithmetic) is exact to ~1e-10. Ms is 2 PM
 // lam_stride<PM>() floats of 16-byte aligned scratch. The result is valid in
-// every lane; 0 for H = 0, non-finite for a non-finite H.
+// every lane; 0 for H = 0, non-finite for a non-finite H. With v set, lanes
+// c < p also store the unit eigenvector's entry v[c] (the dominant column,
+// normalised).
 template <int PM>
-__device__ double lambda_max_warp(const float* Hs, float* Ms, int p) {
+__device__ double lambda_max_warp(const float* Hs, float* Ms, int p, float* v = nullptr) {
   constexpr int LS = lam_stride<PM>();
   constexpr int E = PM * (PM + 1) / 2;
   constexpr int NPL = (E + 31) / 32;
@@ -182,6 +184,7 @@ __device__ double lambda_max_warp(const float* Hs, float* Ms, int p) {
   df_norm(num);
   df_norm(den);
   if (!(den.hi > 0.f)) return 0.0;
+  if (v != nullptr && lane < p) v[lane] = vc * rsqrtf(den.hi + den.lo);
   // num / den in float-float: q0, then one correction from the exact residual
   const float q0 = num.hi / den.hi;
   const float ph = q0 * den.hi;
