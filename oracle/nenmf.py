@@ -29,7 +29,13 @@ Readings of points the paper leaves open (each is listed in the design doc):
   * eps = tol * ||[P grad_G ; P grad_F]||_F at the initial (G0, F0) of the
     objective being solved ("rel"), or eps = tol ("abs");
   * if H == 0 (lambda_max = 0) the subproblem is constant and Y_0 is returned
-    after zero iterations.
+    after zero iterations;
+  * adaptive restart (the remedy the paper suggests for non-monotone RRE,
+    after O'Donoghue and Candes 2015), optional, function-value scheme per
+    column: the columns are independent problems, so each column tracks its
+    own objective f_j(F_k) = 1/2 F_k^T H F_k - B_j^T F_k and, when it rises
+    (k >= 1), drops its momentum: that extrapolation uses beta_0 = 0 and
+    the column's weights start again from beta_1.
 """
 
 from __future__ import annotations
@@ -61,10 +67,14 @@ def projected_gradient(F: np.ndarray, grad: np.ndarray) -> np.ndarray:
     return np.where(F > 0.0, grad, np.minimum(grad, 0.0))
 
 
-def nesterov_nnls(H, B, Y0, max_inner: int, min_inner: int = 1, eps: float | None = None):
+def nesterov_nnls(H, B, Y0, max_inner: int, min_inner: int = 1, eps: float | None = None,
+                  restart: bool = False, trace: list | None = None):
     """Inner Nesterov loop of NeNMF (Sec. 2) for min_{F>=0} 1/2 ||X - G F||^2.
 
     H = G^T G (p x p), B = G^T X (p x N), Y0 = F^t (p x N).
+    With `restart`, a column whose objective rises drops its momentum (see
+    the module docstring). `trace`, if given, receives per iteration the
+    column objectives and the restart mask.
     Returns (F, iterations, ||P grad(F)||_F).
     """
     if max_inner < 1:
@@ -78,10 +88,20 @@ def nesterov_nnls(H, B, Y0, max_inner: int, min_inner: int = 1, eps: float | Non
     beta = extrapolation_weights(max_inner)   # beta_k = (alpha_k - 1) / alpha_{k+1}
     F_prev = Y.copy()            # F_{-1}; irrelevant because beta_0 = 0
     F_k = Y
+    r = np.zeros(Y.shape[1], dtype=np.int64)   # per column: iterations since its last restart
+    obj_prev = None
     for k in range(max_inner):
         grad_Y = H @ Y - B                           # gradient at Y_k
         F_k = np.maximum(0.0, Y - grad_Y / Lc)       # one projected gradient step
-        Y = F_k + beta[k] * (F_k - F_prev)           # slide away from F_{k-1}
+        if restart:
+            obj = 0.5 * np.sum(F_k * (H @ F_k), axis=0) - np.sum(B * F_k, axis=0)
+            rising = (obj > obj_prev) if obj_prev is not None else np.zeros_like(obj, dtype=bool)
+            r[rising] = 0
+            if trace is not None:
+                trace.append((obj, rising))
+            obj_prev = obj
+        Y = F_k + beta[r] * (F_k - F_prev)           # slide away from F_{k-1}
+        r += 1
         F_prev = F_k
         if eps is not None and k + 1 >= min_inner:
             pg = float(np.linalg.norm(projected_gradient(F_k, H @ F_k - B)))
@@ -118,7 +138,7 @@ def initial_pg_compressed(L, R, XL, XR, G, F) -> float:
 
 
 def nenmf_plain(X, G0, F0, max_outer: int, max_inner: int, min_inner: int = 1,
-                tol: float = 0.0, tol_mode: str = "rel", record: bool = False):
+                tol: float = 0.0, tol_mode: str = "rel", record: bool = False, restart: bool = False):
     """Plain NeNMF: alternate eq. (2) then eq. (3), each by the Nesterov loop.
 
     Returns (G, F, info); info["history"] holds (G, F) after every outer
@@ -131,10 +151,10 @@ def nenmf_plain(X, G0, F0, max_outer: int, max_inner: int, min_inner: int = 1,
     info = {"eps": eps, "inner": [], "history": []}
     for _ in range(max_outer):
         # eq. (2) with F fixed, as a problem in G^T: H = F F^T, B = F X^T.
-        Gt, kG, _ = nesterov_nnls(F @ F.T, F @ X.T, G.T, max_inner, min_inner, eps)
+        Gt, kG, _ = nesterov_nnls(F @ F.T, F @ X.T, G.T, max_inner, min_inner, eps, restart)
         G = Gt.T
         # eq. (3) with G fixed: H = G^T G, B = G^T X.
-        F, kF, _ = nesterov_nnls(G.T @ G, G.T @ X, F, max_inner, min_inner, eps)
+        F, kF, _ = nesterov_nnls(G.T @ G, G.T @ X, F, max_inner, min_inner, eps, restart)
         info["inner"].append((kG, kF))
         if record:
             info["history"].append((G.copy(), F.copy()))
@@ -142,7 +162,7 @@ def nenmf_plain(X, G0, F0, max_outer: int, max_inner: int, min_inner: int = 1,
 
 
 def nenmf_compressed(L, R, XL, XR, G0, F0, max_outer: int, max_inner: int, min_inner: int = 1,
-                     tol: float = 0.0, tol_mode: str = "rel", record: bool = False):
+                     tol: float = 0.0, tol_mode: str = "rel", record: bool = False, restart: bool = False):
     """Compressed NeNMF, Alg. 1: X_L = L X and X_R = X R are given.
 
     repeat: F_R = F R; solve eq. (2) with (X, F) -> (X_R, F_R);
@@ -159,10 +179,10 @@ def nenmf_compressed(L, R, XL, XR, G0, F0, max_outer: int, max_inner: int, min_i
     info = {"eps": eps, "inner": [], "history": []}
     for _ in range(max_outer):
         FR = F @ R                                                   # p x nu
-        Gt, kG, _ = nesterov_nnls(FR @ FR.T, FR @ XR.T, G.T, max_inner, min_inner, eps)
+        Gt, kG, _ = nesterov_nnls(FR @ FR.T, FR @ XR.T, G.T, max_inner, min_inner, eps, restart)
         G = Gt.T
         GL = L @ G                                                   # nu x p
-        F, kF, _ = nesterov_nnls(GL.T @ GL, GL.T @ XL, F, max_inner, min_inner, eps)
+        F, kF, _ = nesterov_nnls(GL.T @ GL, GL.T @ XL, F, max_inner, min_inner, eps, restart)
         info["inner"].append((kG, kF))
         if record:
             info["history"].append((G.copy(), F.copy()))
