@@ -90,8 +90,8 @@ size_t nmf_compress_workspace_size(int n, int m, int nu, nmf_prec_t prec);
 
 /*
  * Alg. 2 with q power steps, each orthonormalisation a CholeskyQR2 whose Gram
- * matrix is accumulated in extended (float-float) precision and factorised in
- * float64; then X_L = L X and X_R = X R (first line of Alg. 1).
+ * matrix is accumulated, factorised and inverted in extended (float-float)
+ * precision; then X_L = L X and X_R = X R (first line of Alg. 1).
  *
  *  X        n x m input, nonnegative (not checked).
  *  omega_L  m x nu Gaussian sketch, or NULL to draw it from `seed` (stream 0).
@@ -137,6 +137,10 @@ typedef struct nenmf_params {
   float* record_G;     /* optional device [max_outer][n][p]: G after each outer iteration */
   float* record_F;     /* optional device [max_outer][p][m]: F after each outer iteration */
   long long* record_time_ns; /* optional device [max_outer + 1]: %globaltimer at the start and after each outer iteration */
+  int restart;         /* 1: adaptive restart of the inner loop (per vector, when its objective
+                          1/2 y^T H y - b^T y rises by more than 1e-5 of sum |y| (|grad| + |b|),
+                          that extrapolation uses beta_0 = 0 and the vector's weights start
+                          again from beta_1); 0: off */
 } nenmf_params_t;
 
 typedef struct nenmf_stats {

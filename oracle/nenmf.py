@@ -35,12 +35,18 @@ Readings of points the paper leaves open (each is listed in the design doc):
     column: the columns are independent problems, so each column tracks its
     own objective f_j(F_k) = 1/2 F_k^T H F_k - B_j^T F_k and, when it rises
     (k >= 1), drops its momentum: that extrapolation uses beta_0 = 0 and
-    the column's weights start again from beta_1.
+    the column's weights start again from beta_1. A rise counts when it
+    exceeds RESTART_TOL times the objective's term scale
+    sum_c |F_c| (|grad_c| + |B_c|), so that rounding of a float32
+    evaluation near convergence does not trigger it.
 """
 
 from __future__ import annotations
 
 import numpy as np
+
+
+RESTART_TOL = 1e-5
 
 
 def alpha_sequence(K: int) -> np.ndarray:
@@ -94,8 +100,11 @@ def nesterov_nnls(H, B, Y0, max_inner: int, min_inner: int = 1, eps: float | Non
         grad_Y = H @ Y - B                           # gradient at Y_k
         F_k = np.maximum(0.0, Y - grad_Y / Lc)       # one projected gradient step
         if restart:
+            grad_F = H @ F_k - B
             obj = 0.5 * np.sum(F_k * (H @ F_k), axis=0) - np.sum(B * F_k, axis=0)
-            rising = (obj > obj_prev) if obj_prev is not None else np.zeros_like(obj, dtype=bool)
+            scale = np.sum(np.abs(F_k) * (np.abs(grad_F) + np.abs(B)), axis=0)
+            rising = ((obj - obj_prev > RESTART_TOL * scale) if obj_prev is not None
+                      else np.zeros_like(obj, dtype=bool))
             r[rising] = 0
             if trace is not None:
                 trace.append((obj, rising))

@@ -43,7 +43,7 @@ class Problem(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int), ("min_inner", ctypes.c_int),
                 ("tol_mode", ctypes.c_int), ("tol", ctypes.c_double), ("record_G", ctypes.c_void_p),
-                ("record_F", ctypes.c_void_p), ("record_time_ns", ctypes.c_void_p)]
+                ("record_F", ctypes.c_void_p), ("record_time_ns", ctypes.c_void_p), ("restart", ctypes.c_int)]
 
 
 class BatchConfig(ctypes.Structure):
@@ -238,7 +238,7 @@ class SolveRecord:
 
 
 def solve(problem: Problem, G, F, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
-          tol_mode: int = TOL_REL, record: SolveRecord | None = None, stats=None, ws=None):
+          tol_mode: int = TOL_REL, record: SolveRecord | None = None, stats=None, ws=None, restart: bool = False):
     """Runs nenmf_solve in place on G (n x p) and F (p x m); returns the device stats buffer."""
     torch = _torch()
     n, m, p = problem.n, problem.m, problem.p
@@ -246,6 +246,7 @@ def solve(problem: Problem, G, F, max_outer: int, max_inner: int, min_inner: int
     _check_f32("F", F, (p, m))
     pa = Params()
     pa.max_outer, pa.max_inner, pa.min_inner, pa.tol_mode, pa.tol = max_outer, max_inner, min_inner, tol_mode, tol
+    pa.restart = int(bool(restart))
     if record is not None:
         pa.record_G = record.G.data_ptr() if record.G is not None else None
         pa.record_F = record.F.data_ptr() if record.F is not None else None
@@ -259,10 +260,11 @@ def solve(problem: Problem, G, F, max_outer: int, max_inner: int, min_inner: int
     return stats
 
 
-def _batch_args(problems, max_outer, max_inner, min_inner, tol, tol_mode, cluster):
+def _batch_args(problems, max_outer, max_inner, min_inner, tol, tol_mode, cluster, restart=False):
     arr = (Problem * max(1, len(problems)))(*problems)
     pa = Params()
     pa.max_outer, pa.max_inner, pa.min_inner, pa.tol_mode, pa.tol = max_outer, max_inner, min_inner, tol_mode, tol
+    pa.restart = int(bool(restart))
     cfg = BatchConfig()
     cfg.cluster = cluster
     return arr, pa, cfg
@@ -287,7 +289,7 @@ def batch_workspace_size(problems, max_outer: int, max_inner: int, min_inner: in
 
 
 def solve_batched(problems, Gs, Fs, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
-                  tol_mode: int = TOL_REL, cluster: int = 0, stats=None, ws=None):
+                  tol_mode: int = TOL_REL, cluster: int = 0, stats=None, ws=None, restart: bool = False):
     """Runs nenmf_solve_batched in place on every (G_i, F_i); returns the device stats buffer (count entries)."""
     torch = _torch()
     count = len(problems)
@@ -296,7 +298,7 @@ def solve_batched(problems, Gs, Fs, max_outer: int, max_inner: int, min_inner: i
     for pr, G, F in zip(problems, Gs, Fs):
         _check_f32("G", G, (pr.n, pr.p))
         _check_f32("F", F, (pr.p, pr.m))
-    arr, pa, cfg = _batch_args(problems, max_outer, max_inner, min_inner, tol, tol_mode, cluster)
+    arr, pa, cfg = _batch_args(problems, max_outer, max_inner, min_inner, tol, tol_mode, cluster, restart)
     gp = (ctypes.c_void_p * max(1, count))(*[G.data_ptr() for G in Gs])
     fp = (ctypes.c_void_p * max(1, count))(*[F.data_ptr() for F in Fs])
     if stats is None:

@@ -513,7 +513,7 @@ extern "C" nmf_status_t nenmf_backward(nmf_stream_t stream, const nenmf_problem_
   if (pr->mode != NENMF_COMPRESSED) return NMF_ERR_UNSUPPORTED;
   const int n = pr->n, m = pr->m, p = pr->p, nu = pr->nu, T = pa->max_outer, K = pa->max_inner;
   if (n < 1 || m < 1 || p < 1 || p > NMF_MAX_RANK || nu < p || nu > NMF_MAX_SKETCH || T < 0 || K < 1 ||
-      K > kMaxInnerIters || pa->tol > 0.0)
+      K > kMaxInnerIters || pa->tol > 0.0 || pa->restart)
     return NMF_ERR_INVALID_ARG;
   if (!pr->L || !pr->R || !pr->XL || !pr->XR || !G0 || !F0 || !dG_T || !dF_T || !dXL || !dXR || !dG0 || !dF0)
     return NMF_ERR_INVALID_ARG;

@@ -55,7 +55,7 @@ struct BatchArgs {
   size_t scratch_stride;
   int max_j;              // largest n or m of the batch (scratch row length)
   int pcap, nucap;        // largest padded p and largest nu of the batch (shared-memory carve)
-  int max_outer, max_inner, min_inner, tol_mode;
+  int max_outer, max_inner, min_inner, tol_mode, restart;
   double tol;
   nenmf_stats_t* stats;   // [count] or null
   Control* ctrl;
@@ -193,8 +193,8 @@ __device__ __forceinline__ void store_u(const Side& s, int p, int j, const float
 }
 
 struct LoopState {
-  float* S_in;   // [4 PM][max_j] state at the block's start (blocks after the first)
-  float* S_out;  // [4 PM][max_j] state at the block's end
+  float* S_in;   // [4 PM + 2][max_j] state at the block's start (blocks after the first)
+  float* S_out;  // [4 PM + 2][max_j] state at the block's end
   float* res;    // [PM][max_j] iterate at the block's end (stop test on)
   int max_j;
 };
@@ -202,16 +202,34 @@ struct LoopState {
 // Iterations k0 .. k1-1 of the inner loop on one vector; with pgt set,
 // pgt[(k - k0) * threads + tid] accumulates ||P grad(f_k)||^2. State: y (the
 // extrapolated point), g = grad at y, fp and gp = previous iterate and its
-// gradient; f returns the last iterate.
+// gradient; with restart on, rs (iterations since the vector's last
+// restart) and objp (its previous objective); f returns the last iterate.
 template <int PM>
 __device__ __forceinline__ void iterate(const float* Hs, const float* b, const float* beta, float invL, int k0, int k1,
-                                        float* y, float* g, float* fp, float* gp, float* f, float* pgt) {
+                                        float* y, float* g, float* fp, float* gp, float* f, float* pgt, int restart,
+                                        int& rs, float& objp) {
   for (int k = k0; k < k1; ++k) {
 #pragma unroll
     for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], invL, y[c]));
     float gf[PM];
     hmatvec_rolled<PM>(Hs, f, b, gf);
-    const float bk = __ldg(beta + k);
+    float bk;
+    if (restart) {
+      // the vector's objective 1/2 f^T H f - b^T f = 1/2 f^T (gf - b); a rise drops the momentum
+      float obj = 0.f, sc = 0.f;
+#pragma unroll
+      for (int c = 0; c < PM; ++c) {
+        obj = fmaf(f[c], gf[c] - b[c], obj);
+        sc = fmaf(fabsf(f[c]), fabsf(gf[c]) + fabsf(b[c]), sc);
+      }
+      obj *= 0.5f;
+      if (k >= 1 && obj - objp > kRestartTol * sc) rs = 0;
+      objp = obj;
+      bk = __ldg(beta + rs);
+      ++rs;
+    } else {
+      bk = __ldg(beta + k);
+    }
     if (pgt) pgt[(k - k0) * blockDim.x + threadIdx.x] += pg_sq<PM>(f, gf);
 #pragma unroll
     for (int c = 0; c < PM; ++c) {
@@ -315,6 +333,8 @@ __device__ PhaseOut phase(const Side& s, int p, int nu, int mode, double eps2, c
     if (kind != 2) clear_pgt(S);
     for (int j = j0 + tid; j < j1; j += TB) {
       float b[PM], y[PM], g[PM], fp[PM], gp[PM], f[PM];
+      int rs = 0;
+      float objp = 0.f;
       form_b<PM>(s, S.Ws, nu, j, b);
       if (kb == 0) {
         load_u<PM>(s, p, j, y);
@@ -332,12 +352,15 @@ __device__ PhaseOut phase(const Side& s, int p, int nu, int mode, double eps2, c
           fp[c] = S_in[(size_t)(2 * PM + c) * MJ + j];
           gp[c] = S_in[(size_t)(3 * PM + c) * MJ + j];
         }
+        rs = (int)S_in[(size_t)(4 * PM) * MJ + j];
+        objp = S_in[(size_t)(4 * PM + 1) * MJ + j];
       }
       if (kind == 0) {
         S.pgt[tid] += pg_sq<PM>(y, g);
         continue;
       }
-      iterate<PM>(S.Hs, b, A.beta, invL, kb, kend, y, g, fp, gp, f, kind == 1 ? S.pgt : nullptr);
+      iterate<PM>(S.Hs, b, A.beta, invL, kb, kend, y, g, fp, gp, f, kind == 1 ? S.pgt : nullptr, A.restart, rs,
+                  objp);
       if (kind == 2) {
         store_u<PM>(s, p, j, f, out.bad);
         continue;
@@ -350,6 +373,8 @@ __device__ PhaseOut phase(const Side& s, int p, int nu, int mode, double eps2, c
           S_out[(size_t)(2 * PM + c) * MJ + j] = fp[c];
           S_out[(size_t)(3 * PM + c) * MJ + j] = gp[c];
         }
+        S_out[(size_t)(4 * PM) * MJ + j] = (float)rs;
+        S_out[(size_t)(4 * PM + 1) * MJ + j] = objp;
       }
       if (test) {
 #pragma unroll
@@ -489,7 +514,7 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs A) {
   float* base = A.scratch ? A.scratch + (size_t)cl * A.scratch_stride : nullptr;
   LS.res = base;
   LS.S_in = base ? base + (size_t)pc * A.max_j : nullptr;
-  LS.S_out = base ? LS.S_in + (size_t)4 * pc * A.max_j : nullptr;
+  LS.S_out = base ? LS.S_in + (size_t)(4 * pc + 2) * A.max_j : nullptr;
   int ph = 0;
   for (int ii = A.start[cl]; ii < A.start[cl + 1]; ++ii) {
     const int inst = A.order[ii];
@@ -658,7 +683,7 @@ nmf_status_t make_plan(int count, const nenmf_problem_t* pr, const nenmf_params_
   const bool test = pa.tol > 0.0;
   const bool blocks = pa.max_inner > kBlockIters;
   pl.scratch_stride = round_up_sz((size_t)(test ? pl.pmax : 0) * pl.max_j, 64) +
-                      (blocks ? round_up_sz((size_t)8 * pl.pmax * pl.max_j, 64) : 0);
+                      (blocks ? round_up_sz((size_t)2 * (4 * pl.pmax + 2) * pl.max_j, 64) : 0);
   if (blocks && !test) pl.scratch_stride += round_up_sz((size_t)pl.pmax * pl.max_j, 64);
   return NMF_OK;
 }
@@ -794,6 +819,7 @@ extern "C" nmf_status_t nenmf_solve_batched(nmf_stream_t stream, int count, cons
   a.max_inner = params->max_inner;
   a.min_inner = params->min_inner;
   a.tol_mode = params->tol_mode;
+  a.restart = params->restart ? 1 : 0;
   a.tol = params->tol;
   a.stats = stats;
   a.ctrl = w.ctrl;

@@ -490,6 +490,7 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
   SolveArgs g{};
   g.p = p; g.N = n; g.nu = nu; g.Y = w.Gt;
   g.max_inner = pa.max_inner; g.min_inner = pa.min_inner; g.stop_test = test; g.side = 0;
+  g.restart = pa.restart ? 1 : 0;
   g.pg2_init = w.initG; g.pg2_part = w.pg2G; g.stats = stats; g.ctrl = ctrl;
   g.epi = epiG;
   g.part_in = w.groupF > 1 ? w.groupOutF : w.partF;

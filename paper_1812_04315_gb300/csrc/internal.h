@@ -144,6 +144,7 @@ struct SolveArgs {
   // iteration
   int max_inner, min_inner;
   bool stop_test;
+  int restart;           // adaptive restart of the inner loop (per vector)
   int side;              // 0 = G, 1 = F (stats slot)
   double* pg2_init;      // MODE_EVAL: per-CTA ||P grad(Y0)||^2
   double* pg2_part;      // [ctas]: ||P grad||^2 of the returned iterate, per CTA

@@ -430,6 +430,8 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
       gp[c] = g[c];
     }
     float beta_next = __ldg(kp.beta);
+    int rs = 0;            // restart: iterations since this vector's last restart
+    float obj_prev = 0.f;  // restart: this vector's previous objective
     float* keep = scratch;  // [kKeep][PM][T]: iterates whose stop test is pending (per thread)
     const float inv_Lc = 1.f / Lc;
     const bool test = a.stop_test;
@@ -450,10 +452,26 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
       for (int k = 0; k < a.max_inner; ++k) {
 #pragma unroll
         for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
-        const float beta = beta_next;
+        float beta = beta_next;
         if (k + 1 < a.max_inner) beta_next = __ldg(kp.beta + k + 1);  // in flight during the product
         float gf[PM];
         hmatvec<PM>(Hs, f, b, gf);
+        if (a.restart) {
+          // adaptive restart: this vector's objective 1/2 f^T H f - b^T f = 1/2 f^T (gf - b);
+          // when it rises the vector drops its momentum (beta_0 = 0 now, beta_1 next)
+          // a rise counts beyond kRestartTol of the terms' scale (float32 rounding stays below it)
+          float obj = 0.f, sc = 0.f;
+#pragma unroll
+          for (int c = 0; c < PM; ++c) {
+            obj = fmaf(f[c], gf[c] - b[c], obj);
+            sc = fmaf(fabsf(f[c]), fabsf(gf[c]) + fabsf(b[c]), sc);
+          }
+          obj *= 0.5f;
+          if (k >= 1 && obj - obj_prev > kRestartTol * sc) rs = 0;
+          obj_prev = obj;
+          beta = __ldg(kp.beta + rs);
+          ++rs;
+        }
 #pragma unroll
         for (int c = 0; c < PM; ++c) {
           y[c] = fmaf(beta, f[c] - fp[c], f[c]);

@@ -9,6 +9,11 @@
 namespace nmf {
 
 constexpr int kMaxSquarings = 16;
+// Adaptive restart: a vector's objective counts as risen when the rise
+// exceeds this fraction of sum_c |f_c| (|grad_c| + |b_c|), the scale of the
+// terms it is computed from, so float32 rounding near convergence does not
+// restart the momentum.
+constexpr float kRestartTol = 1e-5f;
 
 // g = H y - b with the symmetric H (PM x PM, zero padded) in shared memory:
 // row d of H is column d, so g accumulates y_d times row d (read as float4)

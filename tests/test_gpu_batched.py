@@ -44,19 +44,19 @@ def batch():
     return [_problem_inputs(*s, seed=17 * i + 3) for i, s in enumerate(SHAPES)]
 
 
-def _run(nmf, batch, T, inner, tol=0.0, cluster=0, min_inner=1):
+def _run(nmf, batch, T, inner, tol=0.0, cluster=0, min_inner=1, restart=False):
     probs, Gs, Fs = [], [], []
     for b in batch:
         probs.append(nmf.compressed_problem(_t(b["L"]), _t(b["R"]), _t(b["XL"]), _t(b["XR"]), b["p"]))
         Gs.append(_t(b["G0"]))
         Fs.append(_t(b["F0"]))
-    st = nmf.solve_batched(probs, Gs, Fs, T, inner, min_inner=min_inner, tol=tol, cluster=cluster)
+    st = nmf.solve_batched(probs, Gs, Fs, T, inner, min_inner=min_inner, tol=tol, cluster=cluster, restart=restart)
     return Gs, Fs, nmf.read_batch_stats(st, len(batch))
 
 
-def _oracle(b, T, inner, tol=0.0, min_inner=1):
+def _oracle(b, T, inner, tol=0.0, min_inner=1, restart=False):
     return nenmf.nenmf_compressed(b["L"], b["R"], b["XL"], b["XR"], b["G0"], b["F0"], T, inner,
-                                  min_inner=min_inner, tol=tol)
+                                  min_inner=min_inner, tol=tol, restart=restart)
 
 
 @pytest.mark.parametrize("T,inner,tol", [(8, 10, 0.0), (8, 10, 1e-3), (5, 40, 1e-6), (4, 20, 0.0), (6, 1, 0.0)])
@@ -76,6 +76,16 @@ def test_batched_matches_oracle(nmf, batch, T, inner, tol):
             assert abs(st.total_inner[0] + st.total_inner[1] - ora) <= 2
         else:
             assert st.total_inner[0] == T * inner and st.total_inner[1] == T * inner
+
+
+@pytest.mark.parametrize("T,inner,tol", [(6, 10, 0.0), (4, 40, 1e-6)])
+def test_batched_adaptive_restart_matches_oracle(nmf, batch, T, inner, tol):
+    Gs, Fs, stats = _run(nmf, batch, T, inner, tol, restart=True)
+    for b, G, F, st in zip(batch, Gs, Fs, stats):
+        assert st.status == 0
+        Go, Fo, _ = _oracle(b, T, inner, tol, restart=True)
+        Xd = b["X"].astype(np.float64)
+        assert abs(metrics.rre(Xd, _np(G), _np(F)) - metrics.rre(Xd, Go, Fo)) <= 1e-5
 
 
 def test_batched_first_outer_iteration_factors(nmf, batch):

@@ -103,6 +103,31 @@ def test_compressed_solve_matches_oracle(nmf, n, m, p, nu, q, T, inner, tol):
     assert st.total_inner[0] + st.total_inner[1] == pytest.approx(sum(a + b for a, b in info["inner"]), abs=2)
 
 
+@pytest.mark.parametrize("mode", ["plain", "compressed"])
+@pytest.mark.parametrize("inner,tol", [(10, 0.0), (30, 1e-6)])
+def test_adaptive_restart_matches_oracle(nmf, mode, inner, tol):
+    # NMF Gram matrices are ill-conditioned (one dominant eigenvalue), so the
+    # momentum overshoots and restarts happen; the trajectories agree per outer iteration.
+    n, m, p, nu, T = 300, 240, 12, 22, 8
+    X, G0, F0 = _inputs(n, m, p, seed=31)
+    Xd = X.astype(np.float64)
+    G, F = _t(G0), _t(F0)
+    rec = _record(nmf, T, n, m, p)
+    if mode == "plain":
+        prob = nmf.plain_problem(_t(X), p, 0)
+        _, _, info = nenmf.nenmf_plain(Xd, G0, F0, T, inner, tol=tol, record=True, restart=True)
+    else:
+        OmL, OmR = synth.gaussian_sketches(n, m, nu, seed=3)
+        L, R, XL, XR = (a.astype(np.float32) for a in subspace.compress(Xd, nu, 2, OmL, OmR))
+        prob = nmf.compressed_problem(_t(L), _t(R), _t(XL), _t(XR), p)
+        _, _, info = nenmf.nenmf_compressed(L, R, XL, XR, G0, F0, T, inner, tol=tol, record=True, restart=True)
+    st = nmf.read_stats(nmf.solve(prob, G, F, T, inner, tol=tol, record=rec, restart=True))
+    assert st.status == 0
+    r_gpu = _gpu_rre_history(Xd, rec)
+    r_ora = metrics.rre_history(Xd, info["history"])
+    assert np.max(np.abs(r_gpu - r_ora)) <= 1e-5, (r_gpu - r_ora)
+
+
 def test_timestamps_are_monotone(nmf):
     n, m, p = 256, 256, 4
     X, G0, F0 = _inputs(n, m, p, seed=5)
