@@ -111,6 +111,38 @@ nmf_status_t nmf_compress(nmf_stream_t stream, int n, int m, int nu, int q, nmf_
                           float* L, float* R, float* XL, float* XR, void* workspace,
                           size_t workspace_bytes);
 
+/*
+ * Compression variants (the paper's Sec. 3 names the alternatives; Alg. 2 is
+ * the one it studies):
+ *  NMF_VARIANT_SUBSPACE      Alg. 2 as nmf_compress reads it (the default).
+ *  NMF_VARIANT_SWAPPED       Alg. 2's last line with the tildes swapped, the
+ *                            other dimensionally valid reading: L = Q~_R^(q),
+ *                            R = Q~_L^(q), the half-step bases (q >= 1).
+ *  NMF_VARIANT_SINGLE_CHAIN  one chain (omega_L only): L = Q_L^(q)^T and R the
+ *                            next half-step basis orth(X^T Q_L^(q)); 2q + 3
+ *                            passes of one product each.
+ *  NMF_VARIANT_POWER         randomized power iteration ("structured random
+ *                            projection"): Alg. 2's products with no
+ *                            orthonormalisation between them (columns only
+ *                            rescaled to unit norm) and one at the end.
+ *  NMF_VARIANT_GAUSSIAN      plain random projection (Sec. 3 footnote):
+ *                            L = Omega_R / sqrt(nu), R = Omega_L / sqrt(nu);
+ *                            L, R are not orthonormal; one pass over X.
+ * Same arguments, workspace and outputs as nmf_compress.
+ */
+typedef enum nmf_compress_variant {
+  NMF_VARIANT_SUBSPACE = 0,
+  NMF_VARIANT_SWAPPED = 1,
+  NMF_VARIANT_SINGLE_CHAIN = 2,
+  NMF_VARIANT_POWER = 3,
+  NMF_VARIANT_GAUSSIAN = 4
+} nmf_compress_variant_t;
+
+nmf_status_t nmf_compress_variant(nmf_stream_t stream, int n, int m, int nu, int q, nmf_prec_t prec, int variant,
+                                  const float* X, const float* omega_L, const float* omega_R, uint64_t seed,
+                                  float* L, float* R, float* XL, float* XR, void* workspace,
+                                  size_t workspace_bytes);
+
 /* ------------------------------------------------------------------------ */
 /* NeNMF solve: plain (eq. 2-3) or compressed (Alg. 1)                        */
 /* ------------------------------------------------------------------------ */

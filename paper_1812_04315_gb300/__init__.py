@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
         "nmf_gaussian_sketch": (i, [vp, i, i, u64, ctypes.c_uint32, vp]),
         "nmf_compress_workspace_size": (sz, [i, i, i, i]),
         "nmf_compress": (i, [vp, i, i, i, i, i, vp, vp, vp, u64, vp, vp, vp, vp, vp, sz]),
+        "nmf_compress_variant": (i, [vp, i, i, i, i, i, i, vp, vp, vp, u64, vp, vp, vp, vp, vp, sz]),
         "nenmf_solve_workspace_size": (sz, [ctypes.POINTER(Problem)]),
         "nenmf_solve": (i, [vp, ctypes.POINTER(Problem), vp, vp, ctypes.POINTER(Params), vp, vp, sz]),
         "nmf_rre_workspace_size": (sz, [i, i, i]),
@@ -107,7 +108,7 @@ def exported_symbols():
             "nmf_rre_workspace_size", "nmf_rre", "nmf_dual_product_workspace_size", "nmf_dual_product",
             "nmf_set_kernel_path", "nmf_kernel_launches", "nmf_rre_static",
             "nenmf_solve_batched_workspace_size", "nenmf_batch_plan_info", "nenmf_solve_batched",
-            "nenmf_backward_workspace_size", "nenmf_backward"]
+            "nenmf_backward_workspace_size", "nenmf_backward", "nmf_compress_variant"]
 
 
 # ---------------------------------------------------------------------------
@@ -177,9 +178,12 @@ def compress_workspace_size(n, m, nu, prec=PREC_BF16) -> int:
     return int(lib().nmf_compress_workspace_size(n, m, nu, prec))
 
 
+VARIANTS = {"subspace": 0, "swapped": 1, "single": 2, "power": 3, "gaussian": 4}
+
+
 def compress(X, nu: int, q: int, prec: int = PREC_BF16, omega_L=None, omega_R=None, seed: int = 0, ws=None,
-             out=None):
-    """Alg. 2 + first line of Alg. 1: returns (L nu x n, R m x nu, X_L nu x m, X_R n x nu)."""
+             out=None, variant: str = "subspace"):
+    """Alg. 2 (or a named variant) + first line of Alg. 1: returns (L nu x n, R m x nu, X_L nu x m, X_R n x nu)."""
     torch = _torch()
     n, m = X.shape
     _check_f32("X", X, (n, m))
@@ -194,8 +198,13 @@ def compress(X, nu: int, q: int, prec: int = PREC_BF16, omega_L=None, omega_R=No
     L, R, XL, XR = out
     if ws is None:
         ws = workspace(compress_workspace_size(n, m, nu, prec))
-    _ok(lib().nmf_compress(_stream(), n, m, nu, q, prec, _ptr(X), _ptr(omega_L), _ptr(omega_R), seed, _ptr(L),
-                           _ptr(R), _ptr(XL), _ptr(XR), _ptr(ws), ws.numel()), "nmf_compress")
+    if variant == "subspace":
+        _ok(lib().nmf_compress(_stream(), n, m, nu, q, prec, _ptr(X), _ptr(omega_L), _ptr(omega_R), seed, _ptr(L),
+                               _ptr(R), _ptr(XL), _ptr(XR), _ptr(ws), ws.numel()), "nmf_compress")
+    else:
+        _ok(lib().nmf_compress_variant(_stream(), n, m, nu, q, prec, VARIANTS[variant], _ptr(X), _ptr(omega_L),
+                                       _ptr(omega_R), seed, _ptr(L), _ptr(R), _ptr(XL), _ptr(XR), _ptr(ws),
+                                       ws.numel()), "nmf_compress_variant")
     return L, R, XL, XR
 
 

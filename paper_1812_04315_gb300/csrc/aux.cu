@@ -96,6 +96,11 @@ __global__ void copy_rows_kernel(const float* in, int rows, int cols, void* out,
   }
 }
 
+__global__ void scale_kernel(const float* in, float* out, long long count, float alpha) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    out[i] = alpha * in[i];
+}
+
 __global__ void timestamp_kernel(unsigned long long* t) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *t = global_ns();
 }
@@ -213,6 +218,12 @@ cudaError_t copy_rows_launch(const float* in, int rows, int cols, void* out, int
                              cudaStream_t s) {
   count_launches(1);
   copy_rows_kernel<<<grid_for((long long)rows * cols, 256), 256, 0, s>>>(in, rows, cols, out, ldo, out_bf16, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_launch(const float* in, float* out, long long count, float alpha, cudaStream_t s) {
+  count_launches(1);
+  scale_kernel<<<grid_for(count, 256), 256, 0, s>>>(in, out, count, alpha);
   return cudaGetLastError();
 }
 

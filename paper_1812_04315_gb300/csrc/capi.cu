@@ -126,48 +126,84 @@ CompressWs carve_compress(void* base, int n, int m, int nu, nmf_prec_t prec) {
   return w;
 }
 
-// One CholeskyQR2 (+ conditional third pass) of the two products of a pass.
-// Outputs: next operands (N job -> opB, T job -> opA), and on the last
-// orthonormalisation L = Q_N^T and R = Q_T.
-nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16, float* Lout, float* Rout,
-                            cudaStream_t s) {
+// Which products of a pass a step works on (N: X A, n rows; T: X^T B, m rows).
+struct Jobs {
+  bool N, T;
+};
+
+// One CholeskyQR2 (+ conditional third pass) of the present products of a
+// pass. Outputs: the next operands (N job -> opB, T job -> opA); with Lout
+// and Rout set, L = Q_N^T and R = Q_T; with XLout set, the T product itself
+// (before orthonormalisation) transposed into XLout.
+nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16, Jobs jb, float* Lout, float* Rout,
+                            float* XLout, cudaStream_t s) {
   Control* ctrl = w.ctrl;
-  int* flagN = &ctrl->flags[0];
-  int* flagT = &ctrl->flags[1];
   const int NV = w.plan.NV;
   NMF_CU(cudaMemsetAsync(ctrl->flags, 0, 2 * sizeof(int), s));
-  // reduce: Y = sum of the X pass partials, Gram 1
-  RowJob r1[2] = {};
-  r1[0].part = w.partN; r1[0].S = w.plan.S_c; r1[0].ldp = NV; r1[0].N = n; r1[0].nu = nu;
-  r1[0].Y = w.YN[0]; r1[0].gram_part = w.gramN[0]; r1[0].gram_always = 1;
-  r1[1].part = w.partT; r1[1].S = w.plan.S_r; r1[1].ldp = NV; r1[1].N = m; r1[1].nu = nu;
-  r1[1].Y = w.YT[0]; r1[1].gram_part = w.gramT[0]; r1[1].gram_always = 1;
-  NMF_CU(rows_launch(r1, 2, ctrl, s));
-  // apply 1: factor Gram 1 (shift if needed), Q1 = Y R1^-1, Gram 2
-  RowJob r2[2] = {};
-  r2[0].src = w.YN[0]; r2[0].gram_in = w.gramN[0]; r2[0].gram_parts = rows_ctas(n); r2[0].N = n; r2[0].nu = nu;
-  r2[0].Y = w.YN[1]; r2[0].gram_part = w.gramN[1]; r2[0].gram_always = 1; r2[0].shift_flag = flagN;
-  r2[1].src = w.YT[0]; r2[1].gram_in = w.gramT[0]; r2[1].gram_parts = rows_ctas(m); r2[1].N = m; r2[1].nu = nu;
-  r2[1].Y = w.YT[1]; r2[1].gram_part = w.gramT[1]; r2[1].gram_always = 1; r2[1].shift_flag = flagT;
-  NMF_CU(rows_launch(r2, 2, ctrl, s));
-  // apply 2: Q2 = Q1 R2^-1 -> outputs; Gram 3 only if some factorisation shifted
-  float* QN = w.YN[0];
-  float* QT = Rout ? Rout : w.YT[0];
-  RowJob r3[2] = {};
-  r3[0].src = w.YN[1]; r3[0].gram_in = w.gramN[1]; r3[0].gram_parts = rows_ctas(n); r3[0].N = n; r3[0].nu = nu;
-  r3[0].Y = QN; r3[0].op = w.opB; r3[0].ldop = w.ldb; r3[0].op_bf16 = bf16; r3[0].Yt = Lout;
-  r3[0].gram_part = w.gramN[0]; r3[0].gram_on_shift = 1; r3[0].shift_flag = flagN;
-  r3[1].src = w.YT[1]; r3[1].gram_in = w.gramT[1]; r3[1].gram_parts = rows_ctas(m); r3[1].N = m; r3[1].nu = nu;
-  r3[1].Y = QT; r3[1].op = w.opA; r3[1].ldop = w.lda; r3[1].op_bf16 = bf16;
-  r3[1].gram_part = w.gramT[0]; r3[1].gram_on_shift = 1; r3[1].shift_flag = flagT;
-  NMF_CU(rows_launch(r3, 2, ctrl, s));
-  // apply 3, in place, only where a shift was taken
-  RowJob r4[2] = {r3[0], r3[1]};
-  r4[0].src = QN; r4[0].gram_in = w.gramN[0]; r4[0].gram_part = nullptr; r4[0].gram_on_shift = 0;
-  r4[0].shift_flag = nullptr; r4[0].run_flag = flagN;
-  r4[1].src = QT; r4[1].gram_in = w.gramT[0]; r4[1].gram_part = nullptr; r4[1].gram_on_shift = 0;
-  r4[1].shift_flag = nullptr; r4[1].run_flag = flagT;
-  NMF_CU(rows_launch(r4, 2, ctrl, s));
+  RowJob r1[2] = {}, r2[2] = {}, r3[2] = {}, r4[2] = {};
+  int k = 0;
+  for (int t = 0; t < 2; ++t) {
+    const bool isN = t == 0;
+    if (isN ? !jb.N : !jb.T) continue;
+    const int N = isN ? n : m;
+    float* Y0 = isN ? w.YN[0] : w.YT[0];
+    float* Y1 = isN ? w.YN[1] : w.YT[1];
+    float2* g0 = isN ? w.gramN[0] : w.gramT[0];
+    float2* g1 = isN ? w.gramN[1] : w.gramT[1];
+    int* flag = &ctrl->flags[t];
+    // reduce: Y = sum of the X pass partials, Gram 1
+    RowJob& a = r1[k];
+    a.part = isN ? w.partN : w.partT; a.S = isN ? w.plan.S_c : w.plan.S_r; a.ldp = NV; a.N = N; a.nu = nu;
+    a.Y = Y0; a.gram_part = g0; a.gram_always = 1;
+    if (!isN) a.Yt = XLout;
+    // apply 1: factor Gram 1 (shift if needed), Q1 = Y R1^-1, Gram 2
+    RowJob& b = r2[k];
+    b.src = Y0; b.gram_in = g0; b.gram_parts = rows_ctas(N); b.N = N; b.nu = nu;
+    b.Y = Y1; b.gram_part = g1; b.gram_always = 1; b.shift_flag = flag;
+    // apply 2: Q2 = Q1 R2^-1 -> outputs; Gram 3 only if some factorisation shifted
+    float* Q = isN ? Y0 : (Rout ? Rout : Y0);
+    RowJob& c = r3[k];
+    c.src = Y1; c.gram_in = g1; c.gram_parts = rows_ctas(N); c.N = N; c.nu = nu;
+    c.Y = Q; c.op = isN ? w.opB : w.opA; c.ldop = isN ? w.ldb : w.lda; c.op_bf16 = bf16;
+    if (isN) c.Yt = Lout;
+    c.gram_part = g0; c.gram_on_shift = 1; c.shift_flag = flag;
+    // apply 3, in place, only where a shift was taken
+    RowJob& d = r4[k];
+    d = c;
+    d.src = Q; d.gram_in = g0; d.gram_part = nullptr; d.gram_on_shift = 0; d.shift_flag = nullptr; d.run_flag = flag;
+    ++k;
+  }
+  NMF_CU(rows_launch(r1, k, ctrl, s));
+  NMF_CU(rows_launch(r2, k, ctrl, s));
+  NMF_CU(rows_launch(r3, k, ctrl, s));
+  NMF_CU(rows_launch(r4, k, ctrl, s));
+  return NMF_OK;
+}
+
+// The power-iteration variant's step between products: every column of the
+// present products rescaled to unit norm (span unchanged, no
+// orthonormalisation), written as the next operands.
+nmf_status_t normalize_columns(const CompressWs& w, int n, int m, int nu, bool bf16, Jobs jb, cudaStream_t s) {
+  Control* ctrl = w.ctrl;
+  const int NV = w.plan.NV;
+  RowJob r1[2] = {}, r2[2] = {};
+  int k = 0;
+  for (int t = 0; t < 2; ++t) {
+    const bool isN = t == 0;
+    if (isN ? !jb.N : !jb.T) continue;
+    const int N = isN ? n : m;
+    float* Y0 = isN ? w.YN[0] : w.YT[0];
+    float2* g0 = isN ? w.gramN[0] : w.gramT[0];
+    RowJob& a = r1[k];
+    a.part = isN ? w.partN : w.partT; a.S = isN ? w.plan.S_c : w.plan.S_r; a.ldp = NV; a.N = N; a.nu = nu;
+    a.Y = Y0; a.gram_part = g0; a.gram_always = 1;
+    RowJob& b = r2[k];
+    b.src = Y0; b.gram_in = g0; b.gram_parts = rows_ctas(N); b.N = N; b.nu = nu; b.diag_only = 1;
+    b.op = isN ? w.opB : w.opA; b.ldop = isN ? w.ldb : w.lda; b.op_bf16 = bf16;
+    ++k;
+  }
+  NMF_CU(rows_launch(r1, k, ctrl, s));
+  NMF_CU(rows_launch(r2, k, ctrl, s));
   return NMF_OK;
 }
 
@@ -351,11 +387,14 @@ size_t nmf_compress_workspace_size(int n, int m, int nu, nmf_prec_t prec) {
   return carve_compress(nullptr, n, m, nu, prec).bytes;
 }
 
-nmf_status_t nmf_compress(nmf_stream_t stream, int n, int m, int nu, int q, nmf_prec_t prec, const float* X,
-                          const float* omega_L, const float* omega_R, uint64_t seed, float* L, float* R, float* XL,
-                          float* XR, void* workspace, size_t workspace_bytes) {
+nmf_status_t nmf_compress_variant(nmf_stream_t stream, int n, int m, int nu, int q, nmf_prec_t prec, int variant,
+                                  const float* X, const float* omega_L, const float* omega_R, uint64_t seed,
+                                  float* L, float* R, float* XL, float* XR, void* workspace,
+                                  size_t workspace_bytes) {
   if (n < 1 || m < 1 || nu < 1 || nu > NMF_MAX_SKETCH || nu > n || nu > m || q < 0) return NMF_ERR_INVALID_ARG;
   if (prec != NMF_PREC_FP32 && prec != NMF_PREC_BF16) return NMF_ERR_INVALID_ARG;
+  if (variant < NMF_VARIANT_SUBSPACE || variant > NMF_VARIANT_GAUSSIAN) return NMF_ERR_INVALID_ARG;
+  if (variant == NMF_VARIANT_SWAPPED && q < 1) return NMF_ERR_INVALID_ARG;
   if (!X || !L || !R || !XL || !XR) return NMF_ERR_INVALID_ARG;
   if ((omega_L == nullptr) != (omega_R == nullptr)) return NMF_ERR_INVALID_ARG;
   const CompressWs w = carve_compress(workspace, n, m, nu, prec);
@@ -369,20 +408,6 @@ nmf_status_t nmf_compress(nmf_stream_t stream, int n, int m, int nu, int q, nmf_
   NMF_CU(cudaMemsetAsync(w.opA, 0, (size_t)NV * w.lda * es, s));
   NMF_CU(cudaMemsetAsync(w.opB, 0, (size_t)NV * w.ldb * es, s));
   if (bf16) NMF_CU(to_bf16_launch(X, n, m, w.Xb, w.ldxb, w.ctrl, s));
-
-  // Omega_L (m x nu) -> opA rows (A^T), Omega_R (nu x n) -> opB rows (B^T = Omega_R).
-  const float* oL = omega_L;
-  if (!oL) {
-    NMF_CU(sketch_launch(m, nu, seed, 0u, w.omega, s));
-    oL = w.omega;
-  }
-  NMF_CU(transpose_launch(oL, m, nu, w.opA, w.lda, bf16, w.ctrl, s));
-  const float* oR = omega_R;
-  if (!oR) {
-    NMF_CU(sketch_launch(nu, n, seed, 1u, w.omega, s));
-    oR = w.omega;
-  }
-  NMF_CU(copy_rows_launch(oR, nu, n, w.opB, w.ldb, bf16, w.ctrl, s));
 
   XPassArgs xa{};
   xa.n = n;
@@ -398,23 +423,95 @@ nmf_status_t nmf_compress(nmf_stream_t stream, int n, int m, int nu, int q, nmf_
   xa.nu = nu;
   xa.doN = xa.doT = true;
   xa.ctrl = w.ctrl;
-
-  const int passes = 2 * q + 2;
-  for (int pass = 0; pass < passes; ++pass) {
-    NMF_CU(xpass_launch(w.plan, xa, prec, s));
-    if (pass == passes - 1) {
-      // Final pass: X_R = X R (N product), X_L = (X^T L^T)^T (T product).
-      RowJob r[2] = {};
-      r[0].part = w.partN; r[0].S = w.plan.S_c; r[0].ldp = NV; r[0].N = n; r[0].nu = nu; r[0].Y = XR;
-      r[1].part = w.partT; r[1].S = w.plan.S_r; r[1].ldp = NV; r[1].N = m; r[1].nu = nu; r[1].Yt = XL;
-      NMF_CU(rows_launch(r, 2, w.ctrl, s));
-    } else {
-      const bool last = pass == passes - 2;
-      nmf_status_t st = orthonormalize(w, n, m, nu, bf16, last ? L : nullptr, last ? R : nullptr, s);
-      if (st != NMF_OK) return st;
+  XPassArgs xN = xa, xT = xa;
+  xN.doT = false;
+  xT.doN = false;
+  const Jobs both{true, true}, onlyN{true, false}, onlyT{false, true};
+  // the closing pass: X_R = X R (N product) and/or X_L = (X^T L^T)^T (T product)
+  auto closing = [&](Jobs jb) -> nmf_status_t {
+    NMF_CU(xpass_launch(w.plan, jb.T ? xa : xN, prec, s));
+    RowJob r[2] = {};
+    int k = 0;
+    r[k].part = w.partN; r[k].S = w.plan.S_c; r[k].ldp = NV; r[k].N = n; r[k].nu = nu; r[k].Y = XR;
+    ++k;
+    if (jb.T) {
+      r[k].part = w.partT; r[k].S = w.plan.S_r; r[k].ldp = NV; r[k].N = m; r[k].nu = nu; r[k].Yt = XL;
+      ++k;
     }
+    NMF_CU(rows_launch(r, k, w.ctrl, s));
+    return NMF_OK;
+  };
+
+  if (variant == NMF_VARIANT_GAUSSIAN) {
+    // L = Omega_R / sqrt(nu) (nu x n), R = Omega_L / sqrt(nu) (m x nu); one pass for X_L, X_R
+    const float sc = 1.f / sqrtf((float)nu);
+    if (omega_L) {
+      NMF_CU(scale_launch(omega_L, R, (long long)m * nu, sc, s));
+      NMF_CU(scale_launch(omega_R, L, (long long)nu * n, sc, s));
+    } else {
+      NMF_CU(sketch_launch(m, nu, seed, 0u, R, s));
+      NMF_CU(scale_launch(R, R, (long long)m * nu, sc, s));
+      NMF_CU(sketch_launch(nu, n, seed, 1u, L, s));
+      NMF_CU(scale_launch(L, L, (long long)nu * n, sc, s));
+    }
+    NMF_CU(transpose_launch(R, m, nu, w.opA, w.lda, bf16, w.ctrl, s));
+    NMF_CU(copy_rows_launch(L, nu, n, w.opB, w.ldb, bf16, w.ctrl, s));
+    return closing(both);
   }
-  return NMF_OK;
+
+  // Omega_L (m x nu) -> opA rows (A^T), Omega_R (nu x n) -> opB rows (B^T = Omega_R).
+  const float* oL = omega_L;
+  if (!oL) {
+    NMF_CU(sketch_launch(m, nu, seed, 0u, w.omega, s));
+    oL = w.omega;
+  }
+  NMF_CU(transpose_launch(oL, m, nu, w.opA, w.lda, bf16, w.ctrl, s));
+  const float* oR = omega_R;
+  if (!oR) {
+    NMF_CU(sketch_launch(nu, n, seed, 1u, w.omega, s));
+    oR = w.omega;
+  }
+  NMF_CU(copy_rows_launch(oR, nu, n, w.opB, w.ldb, bf16, w.ctrl, s));
+
+  nmf_status_t st = NMF_OK;
+  if (variant == NMF_VARIANT_SINGLE_CHAIN) {
+    // one chain: Q_L^(0) = orth(X Omega_L); Q~ = orth(X^T Q_L), Q_L = orth(X Q~) q times;
+    // L = Q_L^(q)^T; X_L^T = X^T Q_L^(q) and R = orth(X^T Q_L^(q)); X_R = X R
+    NMF_CU(xpass_launch(w.plan, xN, prec, s));
+    if ((st = orthonormalize(w, n, m, nu, bf16, onlyN, q == 0 ? L : nullptr, nullptr, nullptr, s)) != NMF_OK) return st;
+    for (int k = 1; k <= q; ++k) {
+      NMF_CU(xpass_launch(w.plan, xT, prec, s));
+      if ((st = orthonormalize(w, n, m, nu, bf16, onlyT, nullptr, nullptr, nullptr, s)) != NMF_OK) return st;
+      NMF_CU(xpass_launch(w.plan, xN, prec, s));
+      if ((st = orthonormalize(w, n, m, nu, bf16, onlyN, k == q ? L : nullptr, nullptr, nullptr, s)) != NMF_OK)
+        return st;
+    }
+    NMF_CU(xpass_launch(w.plan, xT, prec, s));
+    if ((st = orthonormalize(w, n, m, nu, bf16, onlyT, nullptr, R, XL, s)) != NMF_OK) return st;
+    return closing(onlyN);
+  }
+
+  // two chains, both products of every pass: the chains trade N and T roles
+  // each pass (see the file header). Subspace iteration orthonormalises after
+  // passes 0 .. 2q (L, R after the last); the swapped reading stops one pass
+  // earlier, where the half-step bases Q~_R^(q), Q~_L^(q) sit in the N and T
+  // jobs; power iteration only rescales columns until the last pass.
+  const int steps = variant == NMF_VARIANT_SWAPPED ? 2 * q : 2 * q + 1;
+  for (int pass = 0; pass < steps; ++pass) {
+    NMF_CU(xpass_launch(w.plan, xa, prec, s));
+    const bool last = pass == steps - 1;
+    if (variant == NMF_VARIANT_POWER && !last) st = normalize_columns(w, n, m, nu, bf16, both, s);
+    else st = orthonormalize(w, n, m, nu, bf16, both, last ? L : nullptr, last ? R : nullptr, nullptr, s);
+    if (st != NMF_OK) return st;
+  }
+  return closing(both);
+}
+
+nmf_status_t nmf_compress(nmf_stream_t stream, int n, int m, int nu, int q, nmf_prec_t prec, const float* X,
+                          const float* omega_L, const float* omega_R, uint64_t seed, float* L, float* R, float* XL,
+                          float* XR, void* workspace, size_t workspace_bytes) {
+  return nmf_compress_variant(stream, n, m, nu, q, prec, NMF_VARIANT_SUBSPACE, X, omega_L, omega_R, seed, L, R, XL,
+                              XR, workspace, workspace_bytes);
 }
 
 size_t nenmf_solve_workspace_size(const nenmf_problem_t* problem) {

@@ -101,6 +101,7 @@ struct RowJob {
   int gram_on_shift;    // form gram_part when *shift_flag (as read) or this factorisation shifted
   int* shift_flag;      // apply step: raised (by CTA 0) when the factorisation needed the shift
   const int* run_flag;  // optional: skip the job unless *run_flag != 0
+  int diag_only;        // apply step: R = diag(sqrt(S_cc)) (columns rescaled to unit norm, span kept)
 };
 
 cudaError_t rows_launch(const RowJob* jobs, int njobs, Control* ctrl, cudaStream_t s);
@@ -198,6 +199,8 @@ cudaError_t transpose_launch(const float* in, int R, int C, void* out, int ldo, 
 cudaError_t copy_rows_launch(const float* in, int rows, int cols, void* out, int ldo, int out_bf16,
                              Control* ctrl, cudaStream_t s);
 cudaError_t timestamp_launch(unsigned long long* t, cudaStream_t s);
+// out[i] = alpha * in[i] (may alias)
+cudaError_t scale_launch(const float* in, float* out, long long count, float alpha, cudaStream_t s);
 cudaError_t rre_launch(int n, int m, int p, const float* X, const float* G, const float* F, double* out,
                        double* part, int parts, cudaStream_t s);
 int rre_parts(int n, int m);

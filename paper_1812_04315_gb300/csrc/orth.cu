@@ -93,7 +93,7 @@ __device__ __forceinline__ void tri_index(int e, int nu, int& a, int& b) {
 // (upper, stride kAs) in (Ihi, Ilo). Returns 0 (ok), 1 (ok, shifted) or -1
 // (failure: status set).
 __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, float* Ahi, float* Alo, float* Ihi,
-                           float* Ilo, Control* ctrl) {
+                           float* Ilo, Control* ctrl, bool diag_only) {
   __shared__ int fail;
   __shared__ float maxdiag_s, trace_s;
   __shared__ float Sdiag[NMF_MAX_SKETCH], Sdiag_lo[NMF_MAX_SKETCH];
@@ -144,6 +144,25 @@ __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, 
   if (!(maxdiag_s > 0.f)) {
     if (tid == 0) set_status(ctrl, maxdiag_s < 0.f ? NMF_ERR_NONFINITE : NMF_ERR_NOT_SPD);
     return -1;
+  }
+  if (diag_only) {
+    // R^{-1} = diag(1 / sqrt(S_cc)): every column rescaled to unit norm; a
+    // zero column stays zero
+    for (int e = tid; e < nu * kAs; e += blockDim.x) {
+      Ihi[e] = 0.f;
+      Ilo[e] = 0.f;
+    }
+    __syncthreads();
+    for (int c = tid; c < nu; c += blockDim.x) {
+      const FF d{Ahi[c * kAs + c], Alo[c * kAs + c]};
+      if (d.hi > 0.f) {
+        const FF r = ff_div(FF{1.f, 0.f}, ff_sqrt(d));
+        Ihi[c * kAs + c] = r.hi;
+        Ilo[c * kAs + c] = r.lo;
+      }
+    }
+    __syncthreads();
+    return 0;
   }
   const float floor = 1e-13f * maxdiag_s;
   // The upper triangle of (Ahi, Alo) is factorised in place; S's off-diagonal
@@ -279,7 +298,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
       Ys[r * kYsStride + c] = (s0 + s1) + (s2 + s3);
     }
   } else {
-    const int sh = factor_gram(J.gram_in, J.gram_parts, nu, Ys, Ahi, Alo, Ihi, Ilo, ctrl);
+    const int sh = factor_gram(J.gram_in, J.gram_parts, nu, Ys, Ahi, Alo, Ihi, Ilo, ctrl, J.diag_only != 0);
     if (sh < 0) return;
     if (tid == 0) shifted_s = sh;
     __syncthreads();

@@ -101,3 +101,12 @@ def test_batched_argument_errors_are_host_side(L):
     pa.record_G = None
     cfg.cluster = 3
     assert L.nenmf_solve_batched(*args(arr)) == 1
+
+
+def test_variant_argument_errors_are_host_side(L):
+    v = ctypes.c_void_p
+    # unknown variant, swapped reading with q = 0
+    assert L.nmf_compress_variant(None, 10, 10, 4, 1, 0, 7, v(256), None, None, 0, v(256), v(256), v(256), v(256),
+                                  v(256), 1 << 30) == 1
+    assert L.nmf_compress_variant(None, 10, 10, 4, 0, 0, 1, v(256), None, None, 0, v(256), v(256), v(256), v(256),
+                                  v(256), 1 << 30) == 1
