@@ -53,8 +53,11 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-rre", action="store_true", help="skip the time-to-RRE runs")
-    ap.add_argument("--workload", choices=["single", "batched"], default="single",
-                    help="single: the headline problem; batched: 256 uneven problems in one batched solve")
+    ap.add_argument("--count", type=int, default=256, help="batched workload: number of problems")
+    ap.add_argument("--workload", choices=["single", "batched", "paper"], default="single",
+                    help="single: the headline problem; batched: 256 uneven problems in one batched solve; "
+                         "paper: the paper's setting (n = m in 500, 5000, 10000; p = 15, nu = 25, Max_iter 500), "
+                         "plain NeNMF against every compression variant")
     return ap.parse_args(argv)
 
 
@@ -283,7 +286,7 @@ def run_batched(args):
     dist = dist_init(world, "nccl")
     dev = torch.device("cuda", local_rank)
     b = BATCH
-    shapes = synth.batched_shapes(b["count"], seed=b["shape_seed"])
+    shapes = synth.batched_shapes(args.count, seed=b["shape_seed"])
     prec = nmf.PREC_BF16
     Xs, outs, probs, G0s, F0s, Gs, Fs = [], [], [], [], [], [], []
     ws_c = nmf.workspace(max(nmf.compress_workspace_size(s["n"], s["m"], s["nu"], prec) for s in shapes))
@@ -358,7 +361,8 @@ def run_batched(args):
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
               "data": "synthetic (seeded low-rank nonnegative + 20 dB noise drawn on the device; random init)",
-              "config": {"workload": BATCH_NAME, "problems": len(probs), "cluster": cluster, "clusters": clusters,
+              "config": {"workload": BATCH_NAME.replace("256", str(len(probs))), "problems": len(probs),
+                         "cluster": cluster, "clusters": clusters,
                          "l2": "inputs larger than L2 (X totals ~10 GB float32)"},
               "breakdown_ms": {"compress_256": round(ms_compress, 4), "solve_batched": round(ms_solve, 4)},
               "clocks": clocks, "gpu_launches": launches,
@@ -577,6 +581,77 @@ def time_to_rre(nmf, Xg, G0g, F0g, dev):
                           "with RRE <= tau; device time"}
 
 
+PAPER = dict(sizes=(500, 5000, 10000), draws=3, p=15, nu=25, q=4, snr_db=30.0, max_outer=60, max_inner=500,
+             tol=1e-6, variants=("subspace", "power", "swapped", "single", "gaussian"))
+
+
+def run_paper(args):
+    """Sec. 4's setting on synthetic data: plain NeNMF and compressed NeNMF with every compression
+    variant, RRE against device time; tau = (1 + 1e-2) * plain NeNMF's final RRE."""
+    import torch
+    import synth
+    import paper_1812_04315_gb300 as nmf
+
+    dev = torch.device("cuda", 0)
+    w = PAPER
+    p, nu, q, T, K, tol = w["p"], w["nu"], w["q"], w["max_outer"], w["max_inner"], w["tol"]
+    out = {}
+    for n in w["sizes"]:
+        m = n
+        per = {}
+        for d in range(w["draws"]):
+            X, _, _ = synth.lowrank_data(n, m, p, seed=100 * n + d, snr_db=w["snr_db"], dtype=np.float32)
+            G0, F0 = synth.initial_factors(n, m, p, seed=100 * n + d + 50)
+            Xg = torch.from_numpy(X).to(dev)
+            G0g, F0g = torch.from_numpy(G0.astype(np.float32)).to(dev), torch.from_numpy(F0.astype(np.float32)).to(dev)
+            rec = nmf.SolveRecord(G=torch.empty((T, n, p), device=dev), F=torch.empty((T, p, m), device=dev),
+                                  times=torch.zeros(T + 1, dtype=torch.int64, device=dev))
+            stream = torch.cuda.current_stream()
+
+            def curve(prob, t0=0.0):
+                G, F = G0g.clone(), F0g.clone()
+                nmf.solve(prob, G, F, T, K, tol=tol, record=rec)
+                torch.cuda.synchronize()
+                ts = rec.times.cpu().numpy().astype(np.float64)
+                terms = [nmf.rre_terms(Xg, rec.G[t], rec.F[t]) for t in range(T)]
+                torch.cuda.synchronize()
+                r = np.array([float((x[0] / x[1]).sqrt()) for x in (t.cpu() for t in terms)])
+                return t0 + (ts[1:] - ts[0]) / 1e9, r
+
+            runs = {"plain": curve(nmf.plain_problem(Xg, p, nmf.PREC_BF16))}
+            for v in w["variants"]:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                nmf.compress(Xg, nu, q, prec=nmf.PREC_BF16, seed=d, variant=v)   # warm
+                a.record(stream)
+                L, R, XL, XR = nmf.compress(Xg, nu, q, prec=nmf.PREC_BF16, seed=d, variant=v)
+                b.record(stream)
+                torch.cuda.synchronize()
+                runs[v] = curve(nmf.compressed_problem(L, R, XL, XR, p), a.elapsed_time(b) / 1e3)
+            tau = (1 + 1e-2) * runs["plain"][1][-1]
+            for name, (t, r) in runs.items():
+                idx = np.nonzero(r <= tau)[0]
+                e = per.setdefault(name, {"seconds_to_tau": [], "final_rre": [], "seconds_total": []})
+                e["seconds_to_tau"].append(float(t[idx[0]]) if idx.size else None)
+                e["final_rre"].append(float(r[-1]))
+                e["seconds_total"].append(float(t[-1]))
+            del Xg
+        summ = {}
+        for name, e in per.items():
+            reached = [x for x in e["seconds_to_tau"] if x is not None]
+            summ[name] = {"median_seconds_to_tau": statistics.median(reached) if reached else None,
+                          "reached": f"{len(reached)}/{len(e['seconds_to_tau'])}",
+                          "median_final_rre": statistics.median(e["final_rre"]),
+                          "median_seconds_total": statistics.median(e["seconds_total"])}
+        out[str(n)] = summ
+    print(json.dumps({"metric": "paper setting: device seconds to RRE tau, plain vs compressed variants",
+                      "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "bf16",
+                      "data": "synthetic (seeded low-rank nonnegative + 30 dB noise; random init)",
+                      "config": {"workload": "n = m in (500, 5000, 10000), p = 15, nu = 25, q = 4, 30 dB, "
+                                             f"Max_iter 500, tol 1e-6, {T} outer, {w['draws']} draws per size",
+                                 "tau": "(1 + 1e-2) * final RRE of plain NeNMF on the same draw"},
+                      "results": out}), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # the FP64 CPU oracle: cpu_baseline leg and the reference arm
 # ---------------------------------------------------------------------------
@@ -632,6 +707,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.workload == "batched":
         run_batched(args)
+    elif args.workload == "paper":
+        run_paper(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
