@@ -198,6 +198,11 @@ size_t nenmf_solve_workspace_size(const nenmf_problem_t* problem);
  *  problem  host pointer; its matrix pointers are device memory.
  *  params   host pointer.
  *  stats    device pointer to one nenmf_stats_t (may be NULL).
+ * The stop test of the per-update kernels needs all their CTAs resident at
+ * once; a compressed problem with more vectors than that (about 150 x 128 at
+ * p = 32) runs on the batched kernel instead (one problem, one cluster; no
+ * snapshots there: NMF_ERR_UNSUPPORTED if record_* is set), plain mode
+ * returns NMF_ERR_UNSUPPORTED. The workspace query covers both.
  */
 nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, float* G, float* F,
                          const nenmf_params_t* params, nenmf_stats_t* stats, void* workspace,

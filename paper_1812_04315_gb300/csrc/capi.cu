@@ -514,9 +514,41 @@ nmf_status_t nmf_compress(nmf_stream_t stream, int n, int m, int nu, int q, nmf_
                               XR, workspace, workspace_bytes);
 }
 
+// The stop test needs every CTA of a solve launch resident at once. A
+// compressed problem with more vectors than that runs on the batched kernel
+// instead (one problem, one cluster of CTAs: its stop test is block-wise and
+// needs no co-residency).
+bool too_many_ctas(const nenmf_problem_t& pr) {
+  const bool plain = pr.mode == NENMF_PLAIN;
+  const int nu = plain ? 0 : pr.nu;
+  const int epiG = plain ? EPI_GRAM : EPI_W_COLS;
+  const int epiF = plain ? EPI_GRAM : EPI_W_ROWS;
+  const int P = partial_stride(plain ? pr.p * pr.p : pr.p * nu);
+  const int ctasG = solve_ctas(pr.n), ctasF = solve_ctas(pr.m);
+  const int gG = partial_group_size(ctasG, P), gF = partial_group_size(ctasF, P);
+  const int inG = gF > 1 ? group_count(ctasF, gF) : ctasF;
+  const int inF = gG > 1 ? group_count(ctasG, gG) : ctasG;
+  return ctasG > solve_max_coresident(pr.p, nu, epiG, inG) || ctasF > solve_max_coresident(pr.p, nu, epiF, inF);
+}
+
+constexpr int kLargeCluster = 8;
+
+size_t large_workspace(const nenmf_problem_t& pr) {
+  nenmf_params_t worst{};
+  worst.max_outer = 1;
+  worst.max_inner = kMaxInnerIters;
+  worst.min_inner = 1;
+  worst.tol = 1.0;
+  worst.tol_mode = NENMF_TOL_REL;
+  const nenmf_batch_config_t cfg{kLargeCluster};
+  return nenmf_solve_batched_workspace_size(1, &pr, &worst, &cfg);
+}
+
 size_t nenmf_solve_workspace_size(const nenmf_problem_t* problem) {
   if (!problem_ok(problem)) return 0;
-  return carve_solve(nullptr, *problem).bytes;
+  size_t b = carve_solve(nullptr, *problem).bytes;
+  if (problem->mode == NENMF_COMPRESSED && too_many_ctas(*problem)) b = std::max(b, large_workspace(*problem));
+  return b;
 }
 
 nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, float* G, float* F,
@@ -537,8 +569,13 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
   const int groupsInG = w.groupF > 1 ? group_count(w.ctasF, w.groupF) : w.ctasF;  // read by the G update
   const int groupsInF = w.groupG > 1 ? group_count(w.ctasG, w.groupG) : w.ctasG;  // read by the F update
   if (test && (w.ctasG > solve_max_coresident(p, nu, epiG, groupsInG) ||
-               w.ctasF > solve_max_coresident(p, nu, epiF, groupsInF)))
-    return NMF_ERR_UNSUPPORTED;
+               w.ctasF > solve_max_coresident(p, nu, epiF, groupsInF))) {
+    // more vectors than one co-resident grid: compressed problems go to the
+    // batched kernel (snapshots are single-kernel only)
+    if (plain || pa.record_G || pa.record_F || pa.record_time_ns) return NMF_ERR_UNSUPPORTED;
+    const nenmf_batch_config_t cfg{kLargeCluster};
+    return nenmf_solve_batched(stream, 1, &pr, &G, &F, &pa, &cfg, stats, workspace, workspace_bytes);
+  }
   cudaStream_t s = (cudaStream_t)stream;
   Control* ctrl = w.ctrl;
   const nmf_prec_t prec = (nmf_prec_t)pr.prec;

@@ -71,3 +71,33 @@ def test_full_size_workload(nmf, prec, tol_rre):
     Go, Fo, info = nenmf.nenmf_compressed(L, R, XL, XR, G0, F0, T, inner, tol=tol, record=True)
     r_ora = np.array([metrics.rre(Xd, *info["history"][t]) for t in keep])
     assert np.max(np.abs(r_gpu - r_ora)) <= tol_rre, (r_gpu, r_ora)
+
+
+def test_largest_configuration(nmf):
+    # n = 5e4, m = 2e4 (X 4 GB float32), p = 32, nu = 42, q = 4, 40 dB, 10%
+    # of G0's entries zero, bfloat16 compression. With the stop test on, the
+    # solve has more vectors than one co-resident grid holds and runs on the
+    # batched kernel; properties at full size, and the single-problem kernel
+    # (stop test off, which needs no co-residency) against the batched kernel
+    # on the same compressed inputs.
+    import torch
+    n, m, p, nu, q = 50000, 20000, 32, 42, 4
+    X, _, _ = synth.lowrank_data_device(n, m, p, seed=5, snr_db=40.0, zero_frac=0.1)
+    L, R, XL, XR = nmf.compress(X, nu, q, prec=nmf.PREC_BF16, seed=6)
+    assert float((L @ L.T - torch.eye(nu, device="cuda")).abs().max()) < 2e-5
+    assert float((R.T @ R - torch.eye(nu, device="cuda")).abs().max()) < 2e-5
+    G0, F0 = (_t(a) for a in synth.initial_factors(n, m, p, seed=7))
+    prob = nmf.compressed_problem(L, R, XL, XR, p)
+    G, F = G0.clone(), F0.clone()
+    st = nmf.read_stats(nmf.solve(prob, G, F, 60, 10, tol=1e-6))
+    torch.cuda.synchronize()
+    assert st.status == 0 and st.outer_done == 60
+    assert bool(torch.isfinite(G).all()) and bool((G >= 0).all()) and bool((F >= 0).all())
+    r0, r1 = nmf.rre(X, G0, F0), nmf.rre(X, G, F)
+    assert r1 < 0.05 and r1 < r0 / 10, (r0, r1)   # 40 dB: the noise floor is about 0.01
+    # two kernels, one method: stop test off, 5 outer iterations
+    G1, F1 = G0.clone(), F0.clone()
+    nmf.solve(prob, G1, F1, 5, 10)
+    G2, F2 = G0.clone(), F0.clone()
+    nmf.solve_batched([prob], [G2], [F2], 5, 10, cluster=8)
+    assert abs(nmf.rre(X, G1, F1) - nmf.rre(X, G2, F2)) <= 1e-5
