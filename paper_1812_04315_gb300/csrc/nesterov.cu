@@ -93,13 +93,18 @@ constexpr int kThreadsAll = T + 32;     // plus the collector warp
 
 __device__ __forceinline__ uint32_t stop_tag(int epoch, int j) { return ((uint32_t)epoch << 16) | (uint32_t)(j + 1); }
 
+// Shared words: (test + 1) << 32 | payload, one 64-bit store each, so a
+// reader that sees the tag sees the payload with it (no fence); zeroed at
+// kernel start, so nothing a previous launch left in this shared memory
+// matches a tag.
 struct StopShared {
-  float part[kStopSlots][kWarps];
-  int part_tag[kStopSlots][kWarps];
-  int dec_tag[kStopSlots];
-  int dec_val[kStopSlots];
-  double dec_tot[kStopSlots];
+  unsigned long long part[kStopSlots][kWarps];  // payload: float bits of the warp's partial
+  unsigned long long dec[kStopSlots];           // payload: 1 = stop, 0 = go on
+  double dec_tot[kStopSlots];                   // the total, written before dec (collector fences)
 };
+__device__ __forceinline__ unsigned long long stop_word(int j, uint32_t payload) {
+  return ((unsigned long long)(uint32_t)(j + 1) << 32) | payload;
+}
 
 // Collector warp: processes tests 0 .. ntests-1 in order until one passes.
 // Returns false on timeout or abort.
@@ -110,36 +115,35 @@ __device__ bool collector_loop(StopShared& S, unsigned long long* slots, int nte
   const unsigned long long t0 = global_ns();
   for (int j = 0; j < ntests; ++j) {
     const int sl = j % kStopSlots;
-    // 1. the CTA's partial
+    // 1. the CTA's partial: lane w waits for warp w's word of test j
     int ok = 1;
+    float pv = 0.f;
     if (lane < kWarps) {
-      while (*((volatile int*)&S.part_tag[sl][lane]) != j + 1) {
+      unsigned long long w = *((volatile unsigned long long*)&S.part[sl][lane]);
+      while ((uint32_t)(w >> 32) != (uint32_t)(j + 1)) {
         if (*((volatile int*)&c->abort) || global_ns() - t0 > kWaitNs) { ok = 0; break; }
+        w = *((volatile unsigned long long*)&S.part[sl][lane]);
       }
+      pv = __uint_as_float((uint32_t)w);
     }
     if (!__all_sync(0xffffffffu, ok)) return false;
-    __threadfence_block();
+    float own = 0.f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) own += __shfl_sync(0xffffffffu, pv, w);  // same order in every lane
     if (lane == 0) {
-      float s = 0.f;
-      for (int w = 0; w < kWarps; ++w) s += *((volatile float*)&S.part[sl][w]);
       const unsigned long long word =
-          ((unsigned long long)stop_tag(epoch, j) << 32) | (unsigned long long)__float_as_uint(s);
+          ((unsigned long long)stop_tag(epoch, j) << 32) | (unsigned long long)__float_as_uint(own);
       cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(slots[(size_t)j * ctas + blockIdx.x]);
       r.store(word, cuda::memory_order_relaxed);
     }
     // Partials are nonnegative and every sum below is monotone, so the total
     // is at least this CTA's partial: when that already exceeds eps^2 the
     // test fails in every CTA, and the decision needs no other CTA's word.
-    float own = 0.f;
-    if (lane == 0)
-      for (int w = 0; w < kWarps; ++w) own += *((volatile float*)&S.part[sl][w]);
-    own = __shfl_sync(0xffffffffu, own, 0);
     if ((double)own > eps2) {
       if (lane == 0) {
-        S.dec_val[sl] = 0;
         S.dec_tot[sl] = (double)own;
         __threadfence_block();
-        *((volatile int*)&S.dec_tag[sl]) = j + 1;
+        *((volatile unsigned long long*)&S.dec[sl]) = stop_word(j, 0u);
       }
       continue;
     }
@@ -168,10 +172,9 @@ __device__ bool collector_loop(StopShared& S, unsigned long long* slots, int nte
     const double total = (double)acc.hi + (double)acc.lo;
     const int stop = total <= eps2;
     if (lane == 0) {
-      S.dec_val[sl] = stop;
       S.dec_tot[sl] = total;
       __threadfence_block();
-      *((volatile int*)&S.dec_tag[sl]) = j + 1;
+      *((volatile unsigned long long*)&S.dec[sl]) = stop_word(j, (uint32_t)stop);
     }
     if (stop) return true;
   }
@@ -182,12 +185,15 @@ __device__ bool collector_loop(StopShared& S, unsigned long long* slots, int nte
 // go on, -1 = timeout or abort).
 __device__ __forceinline__ int wait_decision(StopShared& S, int j, Control* c) {
   const int sl = j % kStopSlots;
-  const unsigned long long t0 = global_ns();
-  while (*((volatile int*)&S.dec_tag[sl]) != j + 1) {
-    if (*((volatile int*)&c->abort) || global_ns() - t0 > kWaitNs) return -1;
+  unsigned long long w = *((volatile unsigned long long*)&S.dec[sl]);
+  if ((uint32_t)(w >> 32) != (uint32_t)(j + 1)) {
+    const unsigned long long t0 = global_ns();
+    do {
+      if (*((volatile int*)&c->abort) || global_ns() - t0 > kWaitNs) return -1;
+      w = *((volatile unsigned long long*)&S.dec[sl]);
+    } while ((uint32_t)(w >> 32) != (uint32_t)(j + 1));
   }
-  __threadfence_block();
-  return *((volatile int*)&S.dec_val[sl]);
+  return (int)(w & 1ull);
 }
 
 // Bulk copy global -> shared (async proxy), completion counted on an mbarrier.
@@ -247,6 +253,7 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
   __shared__ int flag_s;
   __shared__ StopShared stop_s;
   __shared__ double lam_s;
+  __shared__ __align__(16) float lam_dg[2 * PM];
   extern __shared__ __align__(16) float dyn[];
   const bool epiW = a.epi == EPI_W_ROWS || a.epi == EPI_W_COLS;
   const bool stageD = kp.mode != MODE_EPI_ONLY && !gram;
@@ -256,6 +263,10 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
   float* scratch = Ds + (stageD ? vecF : 0);         // partial sums, pending iterates, epilogue
 
   // ---- independent of the previous kernel ----
+  for (int i = tid; i < kStopSlots * (kWarps + 1); i += NT) {
+    if (i < kStopSlots * kWarps) stop_s.part[i / kWarps][i % kWarps] = 0ull;
+    else stop_s.dec[i - kStopSlots * kWarps] = 0ull;
+  }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&pbar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -376,13 +387,6 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
       }
     }
     __syncthreads();
-    // L_c by the collector warp while the compute warps form B.
-    if (kp.mode == MODE_SOLVE && !colthr) {
-      const int ln = tid & 31;
-      float* Ms = Red;  // the slice sums are consumed: 2 PM lam_stride<PM>() scratch
-      const double lam = lambda_max_warp<PM>(Hs, Ms, p);
-      if (ln == 0) lam_s = lam;
-    }
     if (active) {
       if (gram) {
         // B(:, col) = sum over the X pass partials; a whole row of partials
@@ -401,6 +405,8 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
         }
       }
     }
+    // L_c by the whole block (the slice sums are consumed: eigenvalue scratch)
+    if (kp.mode == MODE_SOLVE) lambda_max_cta<PM>(Hs, Red, lam_dg, &lam_s, p);
     __syncthreads();
     if (kp.mode == MODE_SOLVE) {
       Lc_d = lam_s;
@@ -483,11 +489,8 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
         if (test && k + 1 >= a.min_inner) {
           const float ws = warp_sum(active ? pg_sq<PM>(f, gf) : 0.f);
           const int sl = tests % kStopSlots;
-          if ((tid & 31) == 0) {
-            stop_s.part[sl][tid >> 5] = ws;
-            __threadfence_block();
-            *((volatile int*)&stop_s.part_tag[sl][tid >> 5]) = tests + 1;
-          }
+          if ((tid & 31) == 0)
+            *((volatile unsigned long long*)&stop_s.part[sl][tid >> 5]) = stop_word(tests, __float_as_uint(ws));
           float* slot = keep + (size_t)(tests % kKeep) * PM * T;
 #pragma unroll
           for (int c = 0; c < PM; ++c) slot[c * T + tid] = f[c];

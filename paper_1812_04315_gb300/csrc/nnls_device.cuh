@@ -198,4 +198,141 @@ __device__ double lambda_max_warp(const float* Hs, float* Ms, int p, float* v = 
   return (double)q0 + (double)(r / den.hi);
 }
 
+// lambda_max of H like lambda_max_warp, by every thread of the block: the
+// upper-triangle entries of each squaring are shared over all threads, with
+// a barrier per squaring; the trace of the new iterate is summed by every
+// thread from a double-buffered diagonal in one fixed order, so all threads
+// take the same branch and the result is deterministic. Ms: 2 PM
+// lam_stride<PM>() floats, dg: 2 PM floats, lam_out: one double (shared).
+// Returns the value in every thread.
+template <int PM>
+__device__ double lambda_max_cta(const float* Hs, float* Ms, float* dg, double* lam_out, int p) {
+  constexpr int LS = lam_stride<PM>();
+  constexpr int E = PM * (PM + 1) / 2;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  float tr = 0.f;
+  for (int c = 0; c < p; ++c) tr += Hs[c * PM + c];
+  if (!(tr > 0.f) || !isfinite(tr)) {
+    // every thread sees the same trace: a uniform exit
+    const double r = isfinite(tr) ? 0.0 : (double)tr;
+    if (tid == 0) *lam_out = r;
+    __syncthreads();
+    return r;
+  }
+  float* A = Ms;
+  float* B = Ms + PM * LS;
+  for (int i = tid; i < PM * PM; i += NT) A[(i / PM) * LS + i % PM] = Hs[i];
+  __syncthreads();
+  // this thread's upper-triangle entries (i << 8 | j), found once
+  constexpr int kPairs = (E + 127) / 128;  // blocks of at least 128 threads
+  int pr[kPairs];
+#pragma unroll
+  for (int q = 0; q < kPairs; ++q) {
+    const int e0 = tid + q * NT;
+    int i = 0, e = e0;
+    while (i < PM && e >= PM - i) {
+      e -= PM - i;
+      ++i;
+    }
+    pr[q] = e0 < E ? (i << 8) | (i + e) : -1;
+  }
+  float t = tr;
+  int par = 0;
+  for (int s = 0; s < kMaxSquarings; ++s) {
+    const float sc = __fdividef(1.f, t);
+    const float sc2 = sc * sc;
+#pragma unroll
+    for (int q = 0; q < kPairs; ++q) {
+      if (pr[q] < 0) continue;
+      const int i = pr[q] >> 8, j = pr[q] & 255;
+      const float4* ri = reinterpret_cast<const float4*>(A + i * LS);
+      const float4* rj = reinterpret_cast<const float4*>(A + j * LS);
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int d4 = 0; d4 < PM / 4; ++d4) {
+        const float4 x = ri[d4], z = rj[d4];
+        s0 = fmaf(x.x, z.x, s0);
+        s1 = fmaf(x.y, z.y, s1);
+        s0 = fmaf(x.z, z.z, s0);
+        s1 = fmaf(x.w, z.w, s1);
+      }
+      const float v = (s0 + s1) * sc2;
+      B[i * LS + j] = v;
+      B[j * LS + i] = v;
+      if (i == j) dg[par * PM + i] = v;
+    }
+    __syncthreads();
+    // the new trace, same order in every thread: float4 lanes, then a short tree
+    float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c4 = 0; c4 < PM / 4; ++c4) {
+      const float4 v = reinterpret_cast<const float4*>(dg + par * PM)[c4];
+      tq.x += v.x;
+      tq.y += v.y;
+      tq.z += v.z;
+      tq.w += v.w;
+    }
+    const float t2 = (tq.x + tq.y) + (tq.z + tq.w);
+    float* tmp = A;
+    A = B;
+    B = tmp;
+    t = t2;
+    par ^= 1;
+    if (!(t2 > 0.f) || 1.f - t2 < 1e-5f) break;
+  }
+  if (tid < 32) {
+    // dominant column and its float-float Rayleigh quotient (one warp)
+    const int lane = tid;
+    float best = lane < p ? A[lane * LS + lane] : -1.f;
+    int jb = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
+      if (ob > best || (ob == best && oj < jb)) {
+        best = ob;
+        jb = oj;
+      }
+    }
+    const float* vrow = A + jb * LS;
+    const float vc = lane < p ? vrow[lane] : 0.f;
+    DF hv{0.f, 0.f};
+    if (lane < p) {
+#pragma unroll
+      for (int d = 0; d < PM; ++d) df_add_product(hv, Hs[lane * PM + d], vrow[d]);
+    }
+    DF num{0.f, 0.f}, den{0.f, 0.f};
+    df_add_product(num, vc, hv.hi);
+    num.lo = fmaf(vc, hv.lo, num.lo);
+    df_add_product(den, vc, vc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float nh = __shfl_xor_sync(0xffffffffu, num.hi, o), nl = __shfl_xor_sync(0xffffffffu, num.lo, o);
+      const float dh = __shfl_xor_sync(0xffffffffu, den.hi, o), dl = __shfl_xor_sync(0xffffffffu, den.lo, o);
+      DF a = (lane & o) ? DF{nh, nl} : num, b = (lane & o) ? num : DF{nh, nl};
+      df_add(a, b.hi, b.lo);
+      num = a;
+      a = (lane & o) ? DF{dh, dl} : den;
+      b = (lane & o) ? den : DF{dh, dl};
+      df_add(a, b.hi, b.lo);
+      den = a;
+    }
+    df_norm(num);
+    df_norm(den);
+    if (lane == 0) {
+      double lam = 0.0;
+      if (den.hi > 0.f) {
+        const float q0 = num.hi / den.hi;
+        const float ph = q0 * den.hi;
+        const float pe = fmaf(q0, den.hi, -ph);
+        const float r = ((num.hi - ph) - pe) + (num.lo - q0 * den.lo);
+        lam = (double)q0 + (double)(r / den.hi);
+      }
+      *lam_out = lam;
+    }
+  }
+  __syncthreads();
+  return *lam_out;
+}
+
 }  // namespace nmf
