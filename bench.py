@@ -265,7 +265,7 @@ def xpass_bytes(n, m, nu, elem=2):
 
 BATCH = dict(count=256, shape_seed=0, q=2, snr_db=20.0, max_outer=50, max_inner=10, tol=1e-6)
 BATCH_NAME = ("256 compressed NeNMF problems, n~U[1000,8000], m~U[500,4000], p~U{4..16}, nu=p+10, q=2, 20 dB, "
-              "50 outer x <=10 inner, bf16 compression GEMMs, one batched solve")
+              "50 outer x <=10 inner, bf16 compression GEMMs (nmf_compress_batched), one batched solve")
 
 
 def batched_solve_bytes(shapes, T):
@@ -289,7 +289,6 @@ def run_batched(args):
     shapes = synth.batched_shapes(args.count, seed=b["shape_seed"])
     prec = nmf.PREC_BF16
     Xs, outs, probs, G0s, F0s, Gs, Fs = [], [], [], [], [], [], []
-    ws_c = nmf.workspace(max(nmf.compress_workspace_size(s["n"], s["m"], s["nu"], prec) for s in shapes))
     for i, sh in enumerate(shapes):
         X, _, _ = synth.lowrank_data_device(sh["n"], sh["m"], sh["p"], seed=1000 * (rank + 1) + i, snr_db=b["snr_db"],
                                             device=str(dev))
@@ -304,6 +303,10 @@ def run_batched(args):
         Gs.append(G0s[-1].clone())
         Fs.append(F0s[-1].clone())
     T, K_in, tol = b["max_outer"], b["max_inner"], b["tol"]
+    nus = [s["nu"] for s in shapes]
+    seeds = [5000 + i for i in range(len(shapes))]
+    ws_c = nmf.workspace(nmf.compress_batched_workspace_size([(s["n"], s["m"], s["nu"]) for s in shapes], b["q"],
+                                                             prec))
     cluster, clusters = nmf.batch_plan(probs, T, K_in, tol=tol)
     ws_s = nmf.workspace(nmf.batch_workspace_size(probs, T, K_in, tol=tol))
     stats = torch.zeros(len(probs) * 256, dtype=torch.uint8, device=dev)
@@ -312,8 +315,7 @@ def run_batched(args):
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        for i, sh in enumerate(shapes):
-            nmf.compress(Xs[i], sh["nu"], b["q"], prec=prec, seed=5000 + i, ws=ws_c, out=outs[i])
+        nmf.compress_batched(Xs, nus, b["q"], prec=prec, seeds=seeds, outs=outs, ws=ws_c)
         if ev is not None:
             ev[1].record(stream)
         torch._foreach_copy_(Gs, G0s)
@@ -346,7 +348,23 @@ def run_batched(args):
     clocks = sampler.stop()
     ms_compress = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     ms_solve = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
-    ms_step = max_over_ranks(dist, statistics.mean(e[0].elapsed_time(e[2]) for e in evs), dev)
+    ms_eager = statistics.mean(e[0].elapsed_time(e[2]) for e in evs)
+    # The step enqueues ~8000 small kernels, faster on the device than the host
+    # can launch them one by one: the value is taken from the same step captured
+    # once as a CUDA graph and replayed (every call in it is capturable).
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    graph.replay()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dist, local_rank)
+    g0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms_step = max_over_ranks(dist, g0.elapsed_time(g1) / args.steps, dev)
     units = len(probs) * T
     peaks = {}
     try:
@@ -364,7 +382,8 @@ def run_batched(args):
               "config": {"workload": BATCH_NAME.replace("256", str(len(probs))), "problems": len(probs),
                          "cluster": cluster, "clusters": clusters,
                          "l2": "inputs larger than L2 (X totals ~10 GB float32)"},
-              "breakdown_ms": {"compress_256": round(ms_compress, 4), "solve_batched": round(ms_solve, 4)},
+              "breakdown_ms": {"compress_batched_eager": round(ms_compress, 4), "solve_batched_eager": round(ms_solve, 4),
+                               "step_eager": round(ms_eager, 4), "step_graph": round(ms_step, 4)},
               "clocks": clocks, "gpu_launches": launches,
               "e2e": None,
               "roofline": {"kernel": "batched_kernel (all problems, all outer iterations)", "bound": "hbm",

@@ -143,6 +143,30 @@ nmf_status_t nmf_compress_variant(nmf_stream_t stream, int n, int m, int nu, int
                                   float* L, float* R, float* XL, float* XR, void* workspace,
                                   size_t workspace_bytes);
 
+/*
+ * Many independent compressions (Alg. 2 and X_L, X_R for each): the items run
+ * on up to 8 library-owned streams forked from `stream` (an event fork and
+ * join, so the call is stream-ordered and capturable); each item draws its
+ * sketches from its own seed. Results per item equal nmf_compress_variant's.
+ * The library creates its streams and events once per device and keeps
+ * them; concurrent enqueues on one device are serialised by a mutex.
+ * Workspace: min(count, 8) slots of the largest item's compression workspace.
+ */
+typedef struct nmf_compress_item {
+  int n, m, nu, q;
+  const float* X;   /* n x m, device */
+  uint64_t seed;    /* sketch seed (streams 0 and 1 of nmf_gaussian_sketch) */
+  float* L;         /* out: nu x n */
+  float* R;         /* out: m x nu */
+  float* XL;        /* out: nu x m */
+  float* XR;        /* out: n x nu */
+} nmf_compress_item_t;
+
+size_t nmf_compress_batched_workspace_size(int count, const nmf_compress_item_t* items, nmf_prec_t prec);
+
+nmf_status_t nmf_compress_batched(nmf_stream_t stream, int count, const nmf_compress_item_t* items, nmf_prec_t prec,
+                                  int variant, void* workspace, size_t workspace_bytes);
+
 /* ------------------------------------------------------------------------ */
 /* NeNMF solve: plain (eq. 2-3) or compressed (Alg. 1)                        */
 /* ------------------------------------------------------------------------ */

@@ -46,6 +46,12 @@ class Params(ctypes.Structure):
                 ("record_F", ctypes.c_void_p), ("record_time_ns", ctypes.c_void_p), ("restart", ctypes.c_int)]
 
 
+class CompressItem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("nu", ctypes.c_int), ("q", ctypes.c_int),
+                ("X", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("L", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                ("XL", ctypes.c_void_p), ("XR", ctypes.c_void_p)]
+
+
 class BatchConfig(ctypes.Structure):
     _fields_ = [("cluster", ctypes.c_int)]
 
@@ -76,6 +82,8 @@ def lib() -> ctypes.CDLL:
         "nmf_compress_workspace_size": (sz, [i, i, i, i]),
         "nmf_compress": (i, [vp, i, i, i, i, i, vp, vp, vp, u64, vp, vp, vp, vp, vp, sz]),
         "nmf_compress_variant": (i, [vp, i, i, i, i, i, i, vp, vp, vp, u64, vp, vp, vp, vp, vp, sz]),
+        "nmf_compress_batched_workspace_size": (sz, [i, vp, i]),
+        "nmf_compress_batched": (i, [vp, i, vp, i, i, vp, sz]),
         "nenmf_solve_workspace_size": (sz, [ctypes.POINTER(Problem)]),
         "nenmf_solve": (i, [vp, ctypes.POINTER(Problem), vp, vp, ctypes.POINTER(Params), vp, vp, sz]),
         "nmf_rre_workspace_size": (sz, [i, i, i]),
@@ -108,7 +116,8 @@ def exported_symbols():
             "nmf_rre_workspace_size", "nmf_rre", "nmf_dual_product_workspace_size", "nmf_dual_product",
             "nmf_set_kernel_path", "nmf_kernel_launches", "nmf_rre_static",
             "nenmf_solve_batched_workspace_size", "nenmf_batch_plan_info", "nenmf_solve_batched",
-            "nenmf_backward_workspace_size", "nenmf_backward", "nmf_compress_variant"]
+            "nenmf_backward_workspace_size", "nenmf_backward", "nmf_compress_variant",
+            "nmf_compress_batched_workspace_size", "nmf_compress_batched"]
 
 
 # ---------------------------------------------------------------------------
@@ -206,6 +215,43 @@ def compress(X, nu: int, q: int, prec: int = PREC_BF16, omega_L=None, omega_R=No
                                        _ptr(omega_R), seed, _ptr(L), _ptr(R), _ptr(XL), _ptr(XR), _ptr(ws),
                                        ws.numel()), "nmf_compress_variant")
     return L, R, XL, XR
+
+
+def compress_batched_workspace_size(shapes, q: int, prec: int = PREC_BF16) -> int:
+    """Workspace bytes of nmf_compress_batched for [(n, m, nu), ...]."""
+    items = (CompressItem * max(1, len(shapes)))()
+    for i, (n, m, nu) in enumerate(shapes):
+        items[i].n, items[i].m, items[i].nu, items[i].q = n, m, nu, q
+    return int(lib().nmf_compress_batched_workspace_size(len(shapes), ctypes.cast(items, ctypes.c_void_p), prec))
+
+
+def compress_batched(Xs, nus, q: int, prec: int = PREC_BF16, seeds=None, outs=None, variant: str = "subspace",
+                     ws=None):
+    """nmf_compress_batched over the matrices Xs (one nu per matrix); returns [(L, R, X_L, X_R), ...]."""
+    torch = _torch()
+    count = len(Xs)
+    seeds = list(range(count)) if seeds is None else list(seeds)
+    if outs is None:
+        outs = []
+        for X, nu in zip(Xs, nus):
+            n, m = X.shape
+            outs.append((torch.empty((nu, n), dtype=torch.float32, device=X.device),
+                         torch.empty((m, nu), dtype=torch.float32, device=X.device),
+                         torch.empty((nu, m), dtype=torch.float32, device=X.device),
+                         torch.empty((n, nu), dtype=torch.float32, device=X.device)))
+    items = (CompressItem * max(1, count))()
+    for i, (X, nu, sd, o) in enumerate(zip(Xs, nus, seeds, outs)):
+        n, m = X.shape
+        _check_f32("X", X, (n, m))
+        items[i].n, items[i].m, items[i].nu, items[i].q = n, m, nu, q
+        items[i].X, items[i].seed = X.data_ptr(), sd
+        items[i].L, items[i].R, items[i].XL, items[i].XR = (t.data_ptr() for t in o)
+    if ws is None:
+        ws = workspace(compress_batched_workspace_size([(X.shape[0], X.shape[1], nu) for X, nu in zip(Xs, nus)], q,
+                                                       prec))
+    _ok(lib().nmf_compress_batched(_stream(), count, ctypes.cast(items, ctypes.c_void_p), prec, VARIANTS[variant],
+                                   _ptr(ws), ws.numel()), "nmf_compress_batched")
+    return outs
 
 
 def _problem(mode, n, m, p, nu=0, prec=PREC_FP32, X=None, L=None, R=None, XL=None, XR=None):

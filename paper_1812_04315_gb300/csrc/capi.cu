@@ -507,6 +507,100 @@ nmf_status_t nmf_compress_variant(nmf_stream_t stream, int n, int m, int nu, int
   return closing(both);
 }
 
+namespace {
+
+// Lanes of a batched compression: library-owned streams of one device,
+// created on first use and kept for the process; calls that enqueue on
+// them are serialised by a mutex (the enqueue only, not the GPU work).
+constexpr int kLanes = 8;
+struct LaneSet {
+  int dev = -1;
+  cudaStream_t s[kLanes] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kLanes] = {};
+};
+std::mutex g_lane_mu;
+std::vector<LaneSet> g_lanes;
+
+cudaError_t lanes_for_device(LaneSet** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  for (auto& l : g_lanes)
+    if (l.dev == dev) {
+      *out = &l;
+      return cudaSuccess;
+    }
+  LaneSet l;
+  l.dev = dev;
+  for (int i = 0; i < kLanes; ++i) {
+    if ((e = cudaStreamCreateWithFlags(&l.s[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&l.join[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+  }
+  if ((e = cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+  g_lanes.push_back(l);
+  *out = &g_lanes.back();
+  return cudaSuccess;
+}
+
+size_t batch_slot_bytes(int count, const nmf_compress_item_t* items, nmf_prec_t prec) {
+  size_t slot = 0;
+  for (int i = 0; i < count; ++i) {
+    const size_t b = nmf_compress_workspace_size(items[i].n, items[i].m, items[i].nu, prec);
+    if (b == 0) return 0;
+    slot = std::max(slot, round_up_sz(b, 256));
+  }
+  return slot;
+}
+
+}  // namespace
+
+size_t nmf_compress_batched_workspace_size(int count, const nmf_compress_item_t* items, nmf_prec_t prec) {
+  if (count < 1 || !items) return 0;
+  const size_t slot = batch_slot_bytes(count, items, prec);
+  return slot * (size_t)std::min(count, kLanes);
+}
+
+nmf_status_t nmf_compress_batched(nmf_stream_t stream, int count, const nmf_compress_item_t* items, nmf_prec_t prec,
+                                  int variant, void* workspace, size_t workspace_bytes) {
+  if (count < 0 || (count > 0 && !items)) return NMF_ERR_INVALID_ARG;
+  if (count == 0) return NMF_OK;
+  for (int i = 0; i < count; ++i) {
+    const nmf_compress_item_t& it = items[i];
+    if (it.n < 1 || it.m < 1 || it.nu < 1 || it.nu > NMF_MAX_SKETCH || it.nu > it.n || it.nu > it.m || it.q < 0)
+      return NMF_ERR_INVALID_ARG;
+    if (!it.X || !it.L || !it.R || !it.XL || !it.XR) return NMF_ERR_INVALID_ARG;
+    if (variant == NMF_VARIANT_SWAPPED && it.q < 1) return NMF_ERR_INVALID_ARG;
+  }
+  if (prec != NMF_PREC_FP32 && prec != NMF_PREC_BF16) return NMF_ERR_INVALID_ARG;
+  if (variant < NMF_VARIANT_SUBSPACE || variant > NMF_VARIANT_GAUSSIAN) return NMF_ERR_INVALID_ARG;
+  const size_t slot = batch_slot_bytes(count, items, prec);
+  const int lanes = std::min(count, kLanes);
+  if (!ws_ok(workspace, workspace_bytes, slot * lanes)) return NMF_ERR_WORKSPACE;
+  std::lock_guard<std::mutex> g(g_lane_mu);
+  LaneSet* L = nullptr;
+  NMF_CU(lanes_for_device(&L));
+  cudaStream_t s = (cudaStream_t)stream;
+  // fork: every lane starts after what the caller's stream holds
+  NMF_CU(cudaEventRecord(L->fork, s));
+  for (int k = 0; k < lanes; ++k) NMF_CU(cudaStreamWaitEvent(L->s[k], L->fork, 0));
+  for (int i = 0; i < count; ++i) {
+    const int k = i % lanes;
+    const nmf_compress_item_t& it = items[i];
+    char* ws = static_cast<char*>(workspace) + (size_t)k * slot;
+    const nmf_status_t st =
+        nmf_compress_variant((nmf_stream_t)L->s[k], it.n, it.m, it.nu, it.q, prec, variant, it.X, nullptr, nullptr,
+                             it.seed, it.L, it.R, it.XL, it.XR, ws, slot);
+    if (st != NMF_OK) return st;
+  }
+  // join: the caller's stream continues after every lane
+  for (int k = 0; k < lanes; ++k) {
+    NMF_CU(cudaEventRecord(L->join[k], L->s[k]));
+    NMF_CU(cudaStreamWaitEvent(s, L->join[k], 0));
+  }
+  return NMF_OK;
+}
+
 nmf_status_t nmf_compress(nmf_stream_t stream, int n, int m, int nu, int q, nmf_prec_t prec, const float* X,
                           const float* omega_L, const float* omega_R, uint64_t seed, float* L, float* R, float* XL,
                           float* XR, void* workspace, size_t workspace_bytes) {

@@ -135,3 +135,21 @@ def test_library_sketch_variants_match_default_draw(nmf):
     g2 = nmf.compress(_t(X), nu, 0, prec=0, seed=5, variant="gaussian")
     for x, y in zip(g1, g2):
         assert bool(torch.equal(x, y))
+
+
+@pytest.mark.parametrize("variant", ["subspace", "power"])
+def test_compress_batched_equals_one_by_one(nmf, variant):
+    # nmf_compress_batched runs each item's compression on its own lane: every
+    # item equals nmf_compress_variant with the same seed, bit for bit
+    import torch
+    shapes = [(300, 200, 8), (128, 400, 5), (257, 129, 12), (90, 90, 4), (500, 333, 20), (64, 70, 3),
+              (211, 150, 9), (180, 260, 7), (99, 101, 6), (77, 300, 10)]
+    Xs = [_t(synth.lowrank_data(n, m, 4, seed=i, snr_db=20.0, dtype=np.float32)[0]) for i, (n, m, _) in
+          enumerate(shapes)]
+    nus = [nu for _, _, nu in shapes]
+    outs = nmf.compress_batched(Xs, nus, 2, prec=1, seeds=list(range(40, 50)), variant=variant)
+    torch.cuda.synchronize()
+    for i, (X, nu) in enumerate(zip(Xs, nus)):
+        ref = nmf.compress(X, nu, 2, prec=1, seed=40 + i, variant=variant)
+        for a, b in zip(outs[i], ref):
+            assert bool(torch.equal(a, b)), i
