@@ -230,7 +230,10 @@ __device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, Control* c) {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
 
-template <int PM>
+// TEST, RESTART: the launch runs the stop test, the adaptive restart
+// (template parameters, so launches without them carry none of their code in
+// the inner loop, which then stays small enough for the instruction cache).
+template <int PM, bool TEST, bool RESTART>
 __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
   const SolveArgs& a = kp.a;
   Control* ctrl = a.ctrl;
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
     float obj_prev = 0.f;  // restart: this vector's previous objective
     float* keep = scratch;  // [kKeep][PM][T]: iterates whose stop test is pending (per thread)
     const float inv_Lc = 1.f / Lc;
-    const bool test = a.stop_test;
+    constexpr bool test = TEST;
     const double eps2 = ctrl->eps2;
     int tests = 0, stop_j = -1;
     bool aborted = false;
@@ -462,7 +465,7 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
         if (k + 1 < a.max_inner) beta_next = __ldg(kp.beta + k + 1);  // in flight during the product
         float gf[PM];
         hmatvec<PM>(Hs, f, b, gf);
-        if (a.restart) {
+        if (RESTART) {
           // adaptive restart: this vector's objective 1/2 f^T H f - b^T f = 1/2 f^T (gf - b);
           // when it rises the vector drops its momentum (beta_0 = 0 now, beta_1 next)
           // a rise counts beyond kRestartTol of the terms' scale (float32 rounding stays below it)
@@ -656,7 +659,10 @@ cudaError_t launch_pm(const KParams& kp, cudaStream_t s) {
   const SolveArgs& a = kp.a;
   const int ctas = solve_ctas(a.N);
   const size_t smem = dyn_smem<PM>(a, kp.mode);
-  cudaError_t e = allow_dynamic_smem((const void*)solve_kernel<PM>, (int)smem);
+  const bool t = kp.a.stop_test, r = kp.a.restart != 0;
+  const void* fn = t ? (r ? (const void*)solve_kernel<PM, true, true> : (const void*)solve_kernel<PM, true, false>)
+                     : (r ? (const void*)solve_kernel<PM, false, true> : (const void*)solve_kernel<PM, false, false>);
+  cudaError_t e = allow_dynamic_smem(fn, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(ctas);
@@ -671,7 +677,10 @@ cudaError_t launch_pm(const KParams& kp, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   count_launches(1);
-  return cudaLaunchKernelEx(&cfg, solve_kernel<PM>, kp);
+  if (t) return r ? cudaLaunchKernelEx(&cfg, solve_kernel<PM, true, true>, kp)
+               : cudaLaunchKernelEx(&cfg, solve_kernel<PM, true, false>, kp);
+  return r ? cudaLaunchKernelEx(&cfg, solve_kernel<PM, false, true>, kp)
+           : cudaLaunchKernelEx(&cfg, solve_kernel<PM, false, false>, kp);
 }
 
 __global__ void beta_kernel(float* beta, int K) {
@@ -724,9 +733,11 @@ int pad_rank(int p) { return p <= 4 ? 4 : p <= 8 ? 8 : p <= 12 ? 12 : p <= 16 ? 
 template <int PM>
 int occupancy_pm(size_t smem) {
   int per = 0;
-  if (allow_dynamic_smem((const void*)solve_kernel<PM>, (int)smem) != cudaSuccess)
+  if (allow_dynamic_smem((const void*)solve_kernel<PM, true, true>, (int)smem) != cudaSuccess)
     return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<PM>, kThreadsAll, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<PM, true, true>, kThreadsAll, smem) !=
+      cudaSuccess)
+    return 0;
   return per;
 }
 
