@@ -94,9 +94,10 @@ __device__ __forceinline__ void tri_index(int e, int nu, int& a, int& b) {
 // (failure: status set).
 __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, float* Ahi, float* Alo, float* Ihi,
                            float* Ilo, Control* ctrl, bool diag_only) {
-  __shared__ int fail;
   __shared__ float maxdiag_s, trace_s;
   __shared__ float Sdiag[NMF_MAX_SKETCH], Sdiag_lo[NMF_MAX_SKETCH];
+  __shared__ float Dinv_hi[NMF_MAX_SKETCH], Dinv_lo[NMF_MAX_SKETCH];
+  __shared__ float Rs_hi[NMF_MAX_SKETCH], Rs_lo[NMF_MAX_SKETCH];
   const int tid = threadIdx.x;
   const int E = nu * (nu + 1) / 2;
   const int E2 = gram_stride(nu);
@@ -112,7 +113,20 @@ __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, 
     const int np = min(chunk, parts - p0);
     const float4* src = reinterpret_cast<const float4*>(gram + (size_t)p0 * E2);  // even offset: 16-byte aligned
     const int n4 = np * E2 / 2;
-    for (int i = tid; i < n4; i += blockDim.x) reinterpret_cast<float4*>(st)[i] = __ldcg(src + i);
+    // eight loads in flight per thread before any store
+    for (int i0 = tid; i0 < n4; i0 += 8 * (int)blockDim.x) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * (int)blockDim.x;
+        if (i < n4) v[u] = __ldcg(src + i);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * (int)blockDim.x;
+        if (i < n4) reinterpret_cast<float4*>(st)[i] = v[u];
+      }
+    }
     __syncthreads();
     for (int e = tid; e < E; e += blockDim.x) {
       int a, b;
@@ -182,9 +196,15 @@ __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, 
   }
   __syncthreads();
   int shifted = 0;
+  bool fail = false;
+  // this thread's first entry of the upper triangle (the common case nu <= 22
+  // has at most one per thread)
+  int pa = 0, pb = 0;
+  if (tid < E) tri_index(tid, nu, pa, pb);
   for (int attempt = 0; attempt < 2; ++attempt) {
     if (attempt == 1) {
       // restore S from the lower triangle and shift the diagonal
+      __syncthreads();
       const FF sh{1e-10f * trace_s, 0.f};
       for (int e = tid; e < E; e += blockDim.x) {
         int a, b;
@@ -195,65 +215,82 @@ __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, 
       }
       shifted = 1;
     }
-    if (tid == 0) fail = 0;
     __syncthreads();
+    // S = U^T D U (LDL^T, right-looking): step j takes the pivot d_j and
+    // subtracts (S_ji / d_j) S_jk from every trailing entry j < i <= k. All
+    // threads read the same pivot and take the same decision, so a step needs
+    // one barrier. Row j is read, never written, during step j.
+    fail = false;
     for (int j = 0; j < nu; ++j) {
+      const FF d{Ahi[j * kAs + j], Alo[j * kAs + j]};
+      if (!(d.hi > floor) || !isfinite(d.hi)) {
+        fail = true;
+        break;
+      }
+      const FF inv = ff_div(FF{1.f, 0.f}, d);
       if (tid == 0) {
-        const FF d{Ahi[j * kAs + j], Alo[j * kAs + j]};
-        if (!(d.hi > floor) || !isfinite(d.hi)) {
-          fail = 1;
-        } else {
-          const FF r = ff_sqrt(d);
-          Ahi[j * kAs + j] = r.hi;
-          Alo[j * kAs + j] = r.lo;
-        }
+        Dinv_hi[j] = inv.hi;
+        Dinv_lo[j] = inv.lo;
       }
-      __syncthreads();
-      if (fail) break;
-      const FF rjj{Ahi[j * kAs + j], Alo[j * kAs + j]};
-      for (int i = j + 1 + tid; i < nu; i += blockDim.x) {
-        const FF v = ff_div(FF{Ahi[j * kAs + i], Alo[j * kAs + i]}, rjj);
-        Ahi[j * kAs + i] = v.hi;
-        Alo[j * kAs + i] = v.lo;
-      }
-      __syncthreads();
-      const int w = nu - j - 1;
-      for (int t = tid; t < w * w; t += blockDim.x) {
-        const int i = j + 1 + t / w, k = j + 1 + t % w;
-        if (k >= i) {
-          const FF prod = ff_mul(FF{Ahi[j * kAs + i], Alo[j * kAs + i]}, FF{Ahi[j * kAs + k], Alo[j * kAs + k]});
-          const FF v = ff_add(FF{Ahi[i * kAs + k], Alo[i * kAs + k]}, ff_neg(prod));
-          Ahi[i * kAs + k] = v.hi;
-          Alo[i * kAs + k] = v.lo;
-        }
+      for (int e = tid; e < E; e += blockDim.x) {
+        int i = pa, k = pb;
+        if (e != tid) tri_index(e, nu, i, k);
+        if (i <= j) continue;
+        const FF l = ff_mul(FF{Ahi[j * kAs + i], Alo[j * kAs + i]}, inv);
+        const FF v = ff_add(FF{Ahi[i * kAs + k], Alo[i * kAs + k]},
+                            ff_neg(ff_mul(l, FF{Ahi[j * kAs + k], Alo[j * kAs + k]})));
+        Ahi[i * kAs + k] = v.hi;
+        Alo[i * kAs + k] = v.lo;
       }
       __syncthreads();
     }
     if (!fail) break;
-    __syncthreads();
   }
   if (fail) {
     if (tid == 0) set_status(ctrl, NMF_ERR_NOT_SPD);
     return -1;
   }
-  // R^{-1} column by column (thread c owns column c): back substitution
-  // x_c = 1 / R_cc, x_i = -(sum_{k=i+1..c} R_ik x_k) / R_ii, in float-float.
+  // R = D^{1/2} U, so R^{-1} = U^{-1} D^{-1/2}. U_jk = S'_jk / d_j (strict
+  // upper part), and X = U^{-1} starts as the identity.
+  for (int e = tid; e < E; e += blockDim.x) {
+    int i = pa, k = pb;
+    if (e != tid) tri_index(e, nu, i, k);
+    if (i < k) {
+      const FF u = ff_mul(FF{Ahi[i * kAs + k], Alo[i * kAs + k]}, FF{Dinv_hi[i], Dinv_lo[i]});
+      Ahi[i * kAs + k] = u.hi;
+      Alo[i * kAs + k] = u.lo;
+    }
+  }
   for (int c = tid; c < nu; c += blockDim.x) {
-    for (int i = c + 1; i < nu; ++i) {
-      Ihi[i * kAs + c] = 0.f;
-      Ilo[i * kAs + c] = 0.f;
+    const FF r = ff_div(FF{1.f, 0.f}, ff_sqrt(FF{Ahi[c * kAs + c], Alo[c * kAs + c]}));
+    Rs_hi[c] = r.hi;
+    Rs_lo[c] = r.lo;
+  }
+  for (int e = tid; e < nu * kAs; e += blockDim.x) {
+    Ihi[e] = (e / kAs == e % kAs) ? 1.f : 0.f;
+    Ilo[e] = 0.f;
+  }
+  __syncthreads();
+  // U X = I with a unit diagonal, column-oriented: once row k of X is final
+  // (k from the last row to the second), X_ic -= U_ik X_kc for every i < k <= c.
+  for (int k = nu - 1; k >= 1; --k) {
+    const int w = nu - k;
+    for (int t = tid; t < k * w; t += blockDim.x) {
+      const int i = t / w, c = k + t % w;
+      const FF v = ff_add(FF{Ihi[i * kAs + c], Ilo[i * kAs + c]},
+                          ff_neg(ff_mul(FF{Ahi[i * kAs + k], Alo[i * kAs + k]}, FF{Ihi[k * kAs + c], Ilo[k * kAs + c]})));
+      Ihi[i * kAs + c] = v.hi;
+      Ilo[i * kAs + c] = v.lo;
     }
-    const FF xc = ff_div(FF{1.f, 0.f}, FF{Ahi[c * kAs + c], Alo[c * kAs + c]});
-    Ihi[c * kAs + c] = xc.hi;
-    Ilo[c * kAs + c] = xc.lo;
-    for (int i = c - 1; i >= 0; --i) {
-      FF s{0.f, 0.f};
-      for (int k = i + 1; k <= c; ++k)
-        s = ff_add(s, ff_mul(FF{Ahi[i * kAs + k], Alo[i * kAs + k]}, FF{Ihi[k * kAs + c], Ilo[k * kAs + c]}));
-      const FF x = ff_neg(ff_div(s, FF{Ahi[i * kAs + i], Alo[i * kAs + i]}));
-      Ihi[i * kAs + c] = x.hi;
-      Ilo[i * kAs + c] = x.lo;
-    }
+    __syncthreads();
+  }
+  // column c of R^{-1} = column c of U^{-1} times d_c^{-1/2}
+  for (int e = tid; e < E; e += blockDim.x) {
+    int i = pa, c = pb;
+    if (e != tid) tri_index(e, nu, i, c);
+    const FF v = ff_mul(FF{Ihi[i * kAs + c], Ilo[i * kAs + c]}, FF{Rs_hi[c], Rs_lo[c]});
+    Ihi[i * kAs + c] = v.hi;
+    Ilo[i * kAs + c] = v.lo;
   }
   __syncthreads();
   return shifted;
@@ -281,21 +318,45 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
 
   bool extra_gram = false;
   if (J.part) {
-    // Y = sum over the S partials, 4 independent accumulators, fixed order.
-    for (int i = tid; i < rows * nu; i += kRowThreads) {
-      const int r = i / nu, c = i % nu;
-      const float* p = J.part + (size_t)(r0 + r) * J.ldp + c;
-      const size_t stride = (size_t)J.N * J.ldp;
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      int k = 0;
-      for (; k + 4 <= J.S; k += 4) {
-        s0 += __ldcg(p + (k + 0) * stride);
-        s1 += __ldcg(p + (k + 1) * stride);
-        s2 += __ldcg(p + (k + 2) * stride);
-        s3 += __ldcg(p + (k + 3) * stride);
+    // Y = sum over the S partials: four accumulators (partial k feeds
+    // accumulator k mod 4, in increasing k), float4 over four columns, up to
+    // 16 partials' loads in flight per thread. Rows of a partial are ldp
+    // floats, ldp a multiple of 16, so the float4 loads are aligned.
+    const int nu4 = (nu + 3) >> 2;
+    const size_t stride4 = (size_t)J.N * J.ldp / 4;
+    const int S4 = J.S & ~3;
+    for (int i = tid; i < rows * nu4; i += kRowThreads) {
+      const int r = i / nu4, c4 = i % nu4;
+      const float4* pp = reinterpret_cast<const float4*>(J.part + (size_t)(r0 + r) * J.ldp) + c4;
+      float4 acc[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k0 = 0; k0 < S4; k0 += 16) {
+        float4 v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (k0 + u < S4) v[u] = __ldcg(pp + (k0 + u) * stride4);
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (k0 + u < S4) {
+            acc[u & 3].x += v[u].x;
+            acc[u & 3].y += v[u].y;
+            acc[u & 3].z += v[u].z;
+            acc[u & 3].w += v[u].w;
+          }
       }
-      for (; k < J.S; ++k) s0 += __ldcg(p + k * stride);
-      Ys[r * kYsStride + c] = (s0 + s1) + (s2 + s3);
+      for (int k = S4; k < J.S; ++k) {
+        const float4 v = __ldcg(pp + k * stride4);
+        acc[0].x += v.x;
+        acc[0].y += v.y;
+        acc[0].z += v.z;
+        acc[0].w += v.w;
+      }
+      const float o[4] = {(acc[0].x + acc[1].x) + (acc[2].x + acc[3].x), (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y),
+                          (acc[0].z + acc[1].z) + (acc[2].z + acc[3].z), (acc[0].w + acc[1].w) + (acc[2].w + acc[3].w)};
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (4 * c4 + t < nu) Ys[r * kYsStride + 4 * c4 + t] = o[t];
     }
   } else {
     const int sh = factor_gram(J.gram_in, J.gram_parts, nu, Ys, Ahi, Alo, Ihi, Ilo, ctrl, J.diag_only != 0);
@@ -315,20 +376,28 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
       Ys[r * kYsStride + c] = J.src[(size_t)(r0 + r) * nu + c];
     }
     __syncthreads();
-    // q = y R^{-1}: q_c = sum_{k<=c} y_k (R^{-1})_kc with exact float32 x
-    // float-float products and float-float sums, one rounding at the end;
-    // columns from the last to the first, so the row is overwritten in place.
+    // q = y R^{-1}: q_c = sum_{k<=c} y_k (R^{-1})_kc, a compensated dot
+    // product (Dot2 of Ogita, Rump and Oishi, 2005, with the float-float
+    // R^{-1}): each product's exact error, the running sum's exact rounding
+    // error (TwoSum) and the low part of R^{-1} are gathered in a float
+    // correction added once at the end, so q_c is as accurate as if summed in
+    // twice the precision, then rounded. Columns from the last to the first,
+    // so the row is overwritten in place.
     if (tid < rows) {
       float* y = Ys + tid * kYsStride;
       for (int c = nu - 1; c >= 0; --c) {
-        FF acc{0.f, 0.f};
+        float sum = 0.f, corr = 0.f;
         for (int k = 0; k <= c; ++k) {
           const float yk = y[k];
-          const float ph = yk * Ihi[k * kAs + c];
-          const float pe = fmaf(yk, Ilo[k * kAs + c], fmaf(yk, Ihi[k * kAs + c], -ph));
-          acc = ff_add(acc, ff_quick(ph, pe));
+          const float ih = Ihi[k * kAs + c];
+          const float ph = yk * ih;
+          const float pe = fmaf(yk, Ilo[k * kAs + c], fmaf(yk, ih, -ph));
+          const float t = sum + ph;
+          const float bp = t - sum;
+          corr += ((sum - (t - bp)) + (ph - bp)) + pe;
+          sum = t;
         }
-        y[c] = acc.hi + acc.lo;
+        y[c] = sum + corr;
       }
     }
   }
@@ -367,10 +436,21 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
       }
       int a, b;
       tri_index(e, nu, a, b);
-      DF s{0.f, 0.f};
-      for (int r = 0; r < rows; ++r) df_add_product(s, Ys[r * kYsStride + a], Ys[r * kYsStride + b]);
-      df_norm(s);
-      J.gram_part[(size_t)cta * E2 + e] = make_float2(s.hi, s.lo);
+      // four accumulators over interleaved rows (shorter dependent chains)
+      DF s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f}, s3{0.f, 0.f};
+      int r = 0;
+      for (; r + 4 <= rows; r += 4) {
+        df_add_product(s0, Ys[(r + 0) * kYsStride + a], Ys[(r + 0) * kYsStride + b]);
+        df_add_product(s1, Ys[(r + 1) * kYsStride + a], Ys[(r + 1) * kYsStride + b]);
+        df_add_product(s2, Ys[(r + 2) * kYsStride + a], Ys[(r + 2) * kYsStride + b]);
+        df_add_product(s3, Ys[(r + 3) * kYsStride + a], Ys[(r + 3) * kYsStride + b]);
+      }
+      for (; r < rows; ++r) df_add_product(s0, Ys[r * kYsStride + a], Ys[r * kYsStride + b]);
+      df_add(s0, s1.hi, s1.lo);
+      df_add(s2, s3.hi, s3.lo);
+      df_add(s0, s2.hi, s2.lo);
+      df_norm(s0);
+      J.gram_part[(size_t)cta * E2 + e] = make_float2(s0.hi, s0.lo);
     }
   }
 }
