@@ -68,6 +68,16 @@ cudaError_t xpass_launch(const XPassPlan& plan, const XPassArgs& a, nmf_prec_t p
   return xpass_simt_launch(plan, a, prec == NMF_PREC_BF16, s);
 }
 
+size_t xb_elems(const XPassPlan& plan, int n, int ldxb) {
+  return plan.tiled ? (size_t)plan.tiles_r * plan.tiles_c * plan.tile_r * plan.tile_c : (size_t)n * ldxb;
+}
+
+cudaError_t xb_convert(const XPassPlan& plan, const float* X, int n, int m, __nv_bfloat16* Xb, int ldxb,
+                       Control* ctrl, cudaStream_t s) {
+  if (plan.tiled) return xpass_tc_convert(plan, X, n, m, Xb, ctrl, s);
+  return to_bf16_launch(X, n, m, Xb, ldxb, ctrl, s);
+}
+
 }  // namespace nmf
 
 namespace {
@@ -103,7 +113,7 @@ CompressWs carve_compress(void* base, int n, int m, int nu, nmf_prec_t prec) {
   w.ctrl = cv.take<Control>(1);
   if (prec == NMF_PREC_BF16) {
     w.ldxb = round_up(m, 64);
-    w.Xb = cv.take<__nv_bfloat16>((size_t)n * w.ldxb);
+    w.Xb = cv.take<__nv_bfloat16>(xb_elems(w.plan, n, w.ldxb));
   }
   w.lda = round_up(m, 128);
   w.ldb = round_up(n, 128);
@@ -278,7 +288,7 @@ SolveWs carve_solve(void* base, const nenmf_problem_t& pr) {
     const size_t es = prec == NMF_PREC_BF16 ? 2 : 4;
     if (prec == NMF_PREC_BF16) {
       w.ldxb = round_up(m, 64);
-      w.Xb = cv.take<__nv_bfloat16>((size_t)n * w.ldxb);
+      w.Xb = cv.take<__nv_bfloat16>(xb_elems(w.plan, n, w.ldxb));
     }
     w.ldF = round_up(m, 128);
     w.ldG = round_up(n, 128);
@@ -329,7 +339,7 @@ DualWs carve_dual(void* base, int n, int m, int k, nmf_prec_t prec) {
   w.ctrl = cv.take<Control>(1);
   if (prec == NMF_PREC_BF16) {
     w.ldxb = round_up(m, 64);
-    w.Xb = cv.take<__nv_bfloat16>((size_t)n * w.ldxb);
+    w.Xb = cv.take<__nv_bfloat16>(xb_elems(w.plan, n, w.ldxb));
   }
   w.lda = round_up(m, 128);
   w.ldb = round_up(n, 128);
@@ -407,7 +417,7 @@ nmf_status_t nmf_compress_variant(nmf_stream_t stream, int n, int m, int nu, int
   NMF_CU(cudaMemsetAsync(w.ctrl, 0, sizeof(Control), s));
   NMF_CU(cudaMemsetAsync(w.opA, 0, (size_t)NV * w.lda * es, s));
   NMF_CU(cudaMemsetAsync(w.opB, 0, (size_t)NV * w.ldb * es, s));
-  if (bf16) NMF_CU(to_bf16_launch(X, n, m, w.Xb, w.ldxb, w.ctrl, s));
+  if (bf16) NMF_CU(xb_convert(w.plan, X, n, m, w.Xb, w.ldxb, w.ctrl, s));
 
   XPassArgs xa{};
   xa.n = n;
@@ -697,7 +707,7 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
     const size_t es = bf16 ? 2 : 4;
     NMF_CU(cudaMemsetAsync(w.opF, 0, (size_t)w.plan.NV * w.ldF * es, s));
     NMF_CU(cudaMemsetAsync(w.opG, 0, (size_t)w.plan.NV * w.ldG * es, s));
-    if (bf16) NMF_CU(to_bf16_launch(pr.X, n, m, w.Xb, w.ldxb, ctrl, s));
+    if (bf16) NMF_CU(xb_convert(w.plan, pr.X, n, m, w.Xb, w.ldxb, ctrl, s));
     xa.n = n;
     xa.m = m;
     xa.X = bf16 ? (const void*)w.Xb : (const void*)pr.X;
@@ -819,7 +829,7 @@ nmf_status_t nmf_dual_product(nmf_stream_t stream, int n, int m, int k, nmf_prec
   NMF_CU(cudaMemsetAsync(w.ctrl, 0, sizeof(Control), s));
   NMF_CU(cudaMemsetAsync(w.opA, 0, (size_t)w.plan.NV * w.lda * es, s));
   NMF_CU(cudaMemsetAsync(w.opB, 0, (size_t)w.plan.NV * w.ldb * es, s));
-  if (bf16) NMF_CU(to_bf16_launch(X, n, m, w.Xb, w.ldxb, w.ctrl, s));
+  if (bf16) NMF_CU(xb_convert(w.plan, X, n, m, w.Xb, w.ldxb, w.ctrl, s));
   if (A) NMF_CU(transpose_launch(A, m, k, w.opA, w.lda, bf16, w.ctrl, s));
   if (B) NMF_CU(transpose_launch(B, n, k, w.opB, w.ldb, bf16, w.ctrl, s));
   XPassArgs xa{};

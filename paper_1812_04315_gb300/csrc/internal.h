@@ -47,6 +47,7 @@ struct XPassPlan {
   int S_r, S_c;         // region grid: S_r row groups x S_c column groups
   int NV;               // padded operand / partial width
   int ctas;
+  int tiled;            // bfloat16 X held tile by tile (the tensor-core path's layout)
 };
 
 struct XPassArgs {
@@ -67,6 +68,13 @@ struct XPassArgs {
 // Plans (tile sizes, region grid) for a pass at the given width.
 XPassPlan xpass_plan(int n, int m, int nu, nmf_prec_t prec, int num_sms);
 cudaError_t xpass_launch(const XPassPlan& plan, const XPassArgs& a, nmf_prec_t prec, cudaStream_t s);
+// bfloat16 copy of a float32 X in the layout the plan's kernel reads:
+// row-major with ldxb columns, or (plan.tiled) tile by tile.
+size_t xb_elems(const XPassPlan& plan, int n, int ldxb);
+cudaError_t xb_convert(const XPassPlan& plan, const float* X, int n, int m, __nv_bfloat16* Xb, int ldxb,
+                       Control* ctrl, cudaStream_t s);
+cudaError_t xpass_tc_convert(const XPassPlan& plan, const float* X, int n, int m, void* Xt, Control* ctrl,
+                             cudaStream_t s);
 // Float32 CUDA-core path for bfloat16 X (same rounding of inputs as the
 // tensor-core path, different summation order); used as an independent check.
 cudaError_t xpass_simt_launch(const XPassPlan& plan, const XPassArgs& a, bool bf16, cudaStream_t s);

@@ -4,9 +4,11 @@
 // NeNMF's X F^T, X^T G).
 //
 // Tiles. X is cut into 128 x 128 tiles; a CTA owns a rectangle of tiles
-// (row tiles rt0..rt1, column tiles ct0..ct1) and walks it row by row. One
-// X tile lands in shared memory once (TMA, 128-byte swizzle, two 128 x 64
-// boxes) and feeds two MMAs:
+// (row tiles rt0..rt1, column tiles ct0..ct1) and walks it row by row. The
+// bfloat16 copy of X is stored tile by tile, each tile already in the byte
+// order the MMAs read from shared memory (two 128 x 64 boxes, 128-byte
+// swizzle), so a tile is one contiguous 32 KB bulk copy. One X tile lands in
+// shared memory once and feeds two MMAs:
 //   N product: D_N[128 rows x NV] += X_tile (K-major, K = tile columns) * A^T tile
 //   T product: D_T[ct][128 cols x NV] += X_tile^T (MN-major view of the same
 //              bytes, K = tile rows) * B^T tile
@@ -14,6 +16,8 @@
 // by the epilogue warps as one partial of the CTA's column group; every D_T[ct]
 // accumulates over the CTA's row tiles in TMEM and is drained at the end as
 // one partial of its row group. Partials are summed in a fixed order later.
+// The epilogue stages each warp's 32 rows in shared memory so that its global
+// stores cover whole 128-byte lines.
 //
 // Warps: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2..5 = epilogue
 // (TMEM lane quarter = warp % 4). Every mbarrier wait is bounded; on expiry
@@ -22,6 +26,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "internal.h"
@@ -38,8 +43,11 @@ constexpr size_t kSmemBudget = 220 * 1024;
 constexpr int kXStageBytes = kTM * kTK * 2;  // 32 KB
 constexpr uint32_t kMaxTmemCols = 512;
 constexpr long long kWaitLimit = 1ll << 31;  // clock cycles (~1 s)
+constexpr int kStg = 36;                     // floats per staged row (16-byte rows, 4 banks apart)
+constexpr int kStageArea = 4 * 32 * kStg * 4;  // epilogue staging: 4 warps x 32 rows
 
 struct TcParams {
+  const uint8_t* Xt;  // bfloat16 tiles, tile (rt, ct) at byte (rt * tiles_c + ct) * kXStageBytes
   int n, m, stages;
   int tiles_r, tiles_c, S_r, S_c;
   int doN, doT;
@@ -89,6 +97,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     }
   }
   return true;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   asm volatile(
@@ -140,10 +154,34 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N, int a_mn_major) 
          ((uint32_t)(M >> 4) << 24);
 }
 
+// Stores a warp's block of 32 rows x NV floats (row r in lane r's v[]) to dst
+// (row stride NV), rows from `valid` on skipped: through shared memory, in
+// rounds of W columns, so that each store instruction covers whole lines.
+template <int NV>
+__device__ __forceinline__ void store_block(const float* v, float* stg, float* dst, int valid, int lane) {
+  constexpr int W = NV % 32 == 0 ? 32 : 16;
+  constexpr int W4 = W / 4;
+#pragma unroll
+  for (int c0 = 0; c0 < NV; c0 += W) {
+#pragma unroll
+    for (int c = 0; c < W; c += 4)
+      *reinterpret_cast<float4*>(stg + lane * kStg + c) =
+          make_float4(v[c0 + c], v[c0 + c + 1], v[c0 + c + 2], v[c0 + c + 3]);
+    __syncwarp();
+#pragma unroll
+    for (int g = lane; g < 32 * W4; g += 32) {
+      const int r = g / W4, c4 = g % W4;
+      if (r < valid)
+        *reinterpret_cast<float4*>(dst + (size_t)r * NV + c0 + 4 * c4) =
+            *reinterpret_cast<const float4*>(stg + r * kStg + 4 * c4);
+    }
+    __syncwarp();
+  }
+}
+
 template <int NV>
 __global__ void __launch_bounds__(kThreads, 1)
-    xpass_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapA,
-                    const __grid_constant__ CUtensorMap mapB, TcParams P) {
+    xpass_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcParams P) {
   if (call_failed(P.ctrl)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -196,8 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
           uint8_t* st = smem + (size_t)s * stageBytes;
           mbar_arrive_expect_tx(&full[s], bytes);
-          tma_load_2d(st, &mapX, &full[s], ct * kTK, rt * kTM);
-          tma_load_2d(st + kXStageBytes / 2, &mapX, &full[s], ct * kTK + kBoxK, rt * kTM);
+          bulk_load(st, P.Xt + ((size_t)rt * P.tiles_c + ct) * kXStageBytes, (uint32_t)kXStageBytes, &full[s]);
           if (P.doN) {
             tma_load_2d(st + kXStageBytes, &mapA, &full[s], ct * kTK, 0);
             tma_load_2d(st + kXStageBytes + opBox, &mapA, &full[s], ct * kTK + kBoxK, 0);
@@ -268,6 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue (warps 2..5) ----------------
     const int q = warp & 3;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    float* stg = reinterpret_cast<float*>(smem + (size_t)kStages * stageBytes) + (warp - 2) * 32 * kStg;
     float v[NV];
     if (P.doN) {
       for (int ri = 0; ri < nrt; ++ri) {
@@ -280,12 +318,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
-        const int row = (rt0 + ri) * kTM + q * 32 + lane;
-        if (row < P.n) {
-          float4* dst = reinterpret_cast<float4*>(P.partN + ((size_t)cg * P.n + row) * NV);
-#pragma unroll
-          for (int c = 0; c < NV; c += 4) dst[c / 4] = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
-        }
+        const int row0 = (rt0 + ri) * kTM + q * 32;
+        store_block<NV>(v, stg, P.partN + ((size_t)cg * P.n + row0) * NV, P.n - row0, lane);
       }
     }
     if (P.doT && mbar_wait(&tdone, 0u, abort_flag)) {
@@ -294,12 +328,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int c = 0; c < NV; c += 8) tmem_ld8(tmem + lane_off + (uint32_t)((2 + ci) * NV + c), v + c);
         tmem_ld_wait();
-        const int col = (ct0 + ci) * kTK + q * 32 + lane;
-        if (col < P.m) {
-          float4* dst = reinterpret_cast<float4*>(P.partT + ((size_t)rg * P.m + col) * NV);
-#pragma unroll
-          for (int c = 0; c < NV; c += 4) dst[c / 4] = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
-        }
+        const int col0 = (ct0 + ci) * kTK + q * 32;
+        store_block<NV>(v, stg, P.partT + ((size_t)rg * P.m + col0) * NV, P.m - col0, lane);
       }
     } else if (!P.doT) {
       mbar_wait(&tdone, 0u, abort_flag);
@@ -354,19 +384,59 @@ int max_col_tiles(int NV) { return (int)(kMaxTmemCols / NV) - 2; }
 
 size_t tc_stage_bytes(int NV) { return (size_t)(kXStageBytes + 4 * NV * kBoxK * 2); }
 int tc_stages(int NV) {
-  int st = (int)((kSmemBudget - 1024) / tc_stage_bytes(NV));
+  int st = (int)((kSmemBudget - 1024 - kStageArea) / tc_stage_bytes(NV));
   return st > kMaxStages ? kMaxStages : st;
 }
-size_t tc_smem_bytes(int NV) { return (size_t)tc_stages(NV) * tc_stage_bytes(NV) + 1024; }
+size_t tc_smem_bytes(int NV) { return (size_t)tc_stages(NV) * tc_stage_bytes(NV) + kStageArea + 1024; }
+
+// X (n x m float32, row-major) to bfloat16 tiles of kTM x kTK: tile (rt, ct)
+// at element (rt * tiles_c + ct) * kTM * kTK, laid out as the two 128 x 64
+// boxes the kernel's shared memory holds, box h at byte h * kTM * 128, row r
+// at byte r * 128 of its box, the 16-byte chunk j of a row at chunk
+// j ^ (r mod 8) (the 128-byte swizzle). Entries outside X are zero. One
+// thread per 8 consecutive elements of a row: the reads of a warp are
+// contiguous, and every 8 threads fill one 128-byte row of a box.
+__global__ void to_tiles_kernel(const float* __restrict__ X, int n, int m, int tiles_r, int tiles_c,
+                                uint4* __restrict__ Xt, Control* ctrl) {
+  if (call_failed(ctrl)) return;
+  const long long chunks_row = (long long)tiles_c * (kTK / 8);
+  const long long total = (long long)tiles_r * kTM * chunks_row;
+  const bool vec = (m & 3) == 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / chunks_row), cj = (int)(i % chunks_row);
+    const int c0 = cj * 8;
+    float v[8];
+    if (vec && r < n && c0 + 8 <= m) {
+      const float4* src = reinterpret_cast<const float4*>(X + (size_t)r * m + c0);
+      const float4 a = __ldcs(src), b = __ldcs(src + 1);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+      v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = (r < n && c0 + k < m) ? X[(size_t)r * m + c0 + k] : 0.f;
+    }
+    uint4 out;
+    uint32_t* o = reinterpret_cast<uint32_t*>(&out);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+      o[k] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    const int rt = r / kTM, rr = r % kTM, ct = cj / (kTK / 8), h = (cj / 8) & 1, j = cj & 7;
+    const size_t byte = ((size_t)rt * tiles_c + ct) * kXStageBytes + (size_t)h * (kTM * 128) + (size_t)rr * 128 +
+                        (size_t)((j ^ (rr & 7)) * 16);
+    Xt[byte / 16] = out;
+  }
+}
 
 template <int NV>
-cudaError_t launch_nv(const CUtensorMap& mX, const CUtensorMap& mA, const CUtensorMap& mB, const TcParams& P,
-                      int ctas, cudaStream_t s) {
+cudaError_t launch_nv(const CUtensorMap& mA, const CUtensorMap& mB, const TcParams& P, int ctas, cudaStream_t s) {
   const size_t smem = tc_smem_bytes(NV);
   cudaError_t e = allow_dynamic_smem((const void*)xpass_tc_kernel<NV>, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  xpass_tc_kernel<NV><<<ctas, kThreads, smem, s>>>(mX, mA, mB, P);
+  xpass_tc_kernel<NV><<<ctas, kThreads, smem, s>>>(mA, mB, P);
   return cudaGetLastError();
 }
 
@@ -412,15 +482,28 @@ XPassPlan xpass_tc_plan(int n, int m, int nu, int num_sms) {
   pl.S_r = bestr;
   pl.S_c = bestc;
   pl.ctas = bestr * bestc;
+  pl.tiled = 1;
   return pl;
 }
 
+cudaError_t xpass_tc_convert(const XPassPlan& pl, const float* X, int n, int m, void* Xt, Control* ctrl,
+                             cudaStream_t s) {
+  // a grid-stride loop over 16-byte chunks, eight 256-thread CTAs per SM
+  const long long chunks = (long long)pl.tiles_r * kTM * pl.tiles_c * (kTK / 8);
+  const long long ctas = std::min<long long>((chunks + 255) / 256, 8ll * device_sm_count());
+  count_launches(1);
+  to_tiles_kernel<<<(int)ctas, 256, 0, s>>>(X, n, m, pl.tiles_r, pl.tiles_c, static_cast<uint4*>(Xt),
+                                                        ctrl);
+  return cudaGetLastError();
+}
+
 cudaError_t xpass_tc_launch(const XPassPlan& pl, const XPassArgs& a, cudaStream_t s) {
-  CUtensorMap mX, mA, mB;
-  if (!make_map(&mX, a.X, a.ldx, a.n, kBoxK, kTM)) return cudaErrorInvalidValue;
+  CUtensorMap mA, mB;
+  if (!pl.tiled || (reinterpret_cast<uintptr_t>(a.X) & 15u)) return cudaErrorInvalidValue;
   if (!make_map(&mA, a.opA, a.lda, pl.NV, kBoxK, pl.NV)) return cudaErrorInvalidValue;
   if (!make_map(&mB, a.opB, a.ldb, pl.NV, kBoxK, pl.NV)) return cudaErrorInvalidValue;
   TcParams P{};
+  P.Xt = static_cast<const uint8_t*>(a.X);
   P.n = a.n;
   P.m = a.m;
   P.stages = tc_stages(pl.NV);
@@ -435,10 +518,10 @@ cudaError_t xpass_tc_launch(const XPassPlan& pl, const XPassArgs& a, cudaStream_
   P.ctrl = a.ctrl;
   P.tmem_cols = tmem_cols_for(pl.NV, ceil_div(pl.tiles_c, pl.S_c));
   switch (pl.NV) {
-    case 16: return launch_nv<16>(mX, mA, mB, P, pl.ctas, s);
-    case 32: return launch_nv<32>(mX, mA, mB, P, pl.ctas, s);
-    case 48: return launch_nv<48>(mX, mA, mB, P, pl.ctas, s);
-    case 64: return launch_nv<64>(mX, mA, mB, P, pl.ctas, s);
+    case 16: return launch_nv<16>(mA, mB, P, pl.ctas, s);
+    case 32: return launch_nv<32>(mA, mB, P, pl.ctas, s);
+    case 48: return launch_nv<48>(mA, mB, P, pl.ctas, s);
+    case 64: return launch_nv<64>(mA, mB, P, pl.ctas, s);
     default: return cudaErrorInvalidValue;
   }
 }
