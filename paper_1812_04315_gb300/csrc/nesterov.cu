@@ -19,11 +19,14 @@
 //           Only the gradient at f is formed (H f - b); the gradient at the
 //           extrapolated y' follows by linearity,
 //           grad(y') = grad(f) + beta_k (grad(f) - grad(f_prev)).
-//           Optional stop test ||P grad(f_k)||_F <= eps: every CTA publishes
-//           its partial as one tagged 64-bit word and every CTA sums all
-//           partials in the same fixed order; the result of the test at
-//           iteration k is read at iteration k + kLag, so the wait overlaps
-//           compute, and f_k is kept until then (bounded waits);
+//           For p <= 12 the loop reads H from registers (packed upper
+//           triangle). Optional stop test ||P grad(f_k)||_F <= eps: every CTA
+//           publishes its partial as one tagged 64-bit word and every CTA sums
+//           all partials in the same fixed order; a test's warp sums run in
+//           the next iteration, beside its independent product, so the
+//           shuffles hide behind the FMAs; the result of test k is read kLag
+//           tests after it was posted, so the wait overlaps compute, and f_k
+//           is kept until then (bounded waits);
 // epilogue  the returned iterate is stored (and copied for the next X pass,
 //           the snapshot, the stats); the next phase's W (f times rows of R or
 //           columns of L) or Gram matrix f f^T is summed per CTA; for large
@@ -38,7 +41,8 @@ namespace {
 
 constexpr int T = kSolveThreads;
 constexpr int kLag = 4;
-constexpr int kKeep = kLag + 1;
+constexpr int kKeep = kLag + 2;  // a test's iterate is kept until its decision is read (posted one iteration late)
+constexpr int kPackedMax = 12;   // largest padded rank whose H the loop keeps in registers
 static_assert(kStopSlots >= 2 * kLag + 1, "stop-test slots are reused after kStopSlots tests");
 constexpr int kFs = T + 4;                  // column-vector rows: 16-byte aligned, rows 4 banks apart
 constexpr int kWs = NMF_MAX_SKETCH + 1;     // rows of W: consecutive rows in different banks
@@ -234,7 +238,7 @@ __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepc
 // (template parameters, so launches without them carry none of their code in
 // the inner loop, which then stays small enough for the instruction cache).
 template <int PM, bool TEST, bool RESTART>
-__global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
+__global__ void __launch_bounds__(kThreadsAll, PM <= 16 ? 2 : 1) solve_kernel(KParams kp) {
   const SolveArgs& a = kp.a;
   Control* ctrl = a.ctrl;
   const int p = a.p, nu = a.nu, N = a.N;
@@ -431,8 +435,13 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
     const double s = block_sum_df(active ? pg_sq<PM>(f, g) : 0.f, red);
     if (tid == 0) a.pg2_init[cta] = s;
   } else if (kp.mode == MODE_SOLVE && Lc > 0.f) {
+    // PM <= kPackedMax: the loop's products read H from registers
+    constexpr bool packed = PM <= kPackedMax;
+    float Hp[packed ? PM * (PM + 1) / 2 : 1];
+    if constexpr (packed) load_packed<PM>(Hs, Hp);
     float g[PM], fp[PM], gp[PM];
-    hmatvec<PM>(Hs, y, b, g);
+    if constexpr (packed) hmatvec_packed<PM>(Hp, y, b, g);
+    else hmatvec<PM>(Hs, y, b, g);
 #pragma unroll
     for (int c = 0; c < PM; ++c) {
       fp[c] = y[c];
@@ -445,7 +454,9 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
     const float inv_Lc = 1.f / Lc;
     constexpr bool test = TEST;
     const double eps2 = ctrl->eps2;
-    int tests = 0, stop_j = -1;
+    int tests = 0, stop_j = -1;  // tests: posted so far
+    int made = 0;                // tests computed (made - tests: the one whose warp sum is deferred)
+    float pend = 0.f;            // this column's ||P grad||^2 term of that test
     bool aborted = false;
     if (!colthr) {
       // collector warp
@@ -463,8 +474,11 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
         for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
         float beta = beta_next;
         if (k + 1 < a.max_inner) beta_next = __ldg(kp.beta + k + 1);  // in flight during the product
+        // the deferred test's warp sum, independent of this product
+        const float ws = test ? warp_sum(pend) : 0.f;
         float gf[PM];
-        hmatvec<PM>(Hs, f, b, gf);
+        if constexpr (packed) hmatvec_packed<PM>(Hp, f, b, gf);
+        else hmatvec<PM>(Hs, f, b, gf);
         if (RESTART) {
           // adaptive restart: this vector's objective 1/2 f^T H f - b^T f = 1/2 f^T (gf - b);
           // when it rises the vector drops its momentum (beta_0 = 0 now, beta_1 next)
@@ -489,14 +503,11 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
           gp[c] = gf[c];
         }
         iters = k + 1;
-        if (test && k + 1 >= a.min_inner) {
-          const float ws = warp_sum(active ? pg_sq<PM>(f, gf) : 0.f);
-          const int sl = tests % kStopSlots;
+        if (test && made > tests) {
+          // post the deferred test, then read the decision kLag tests back
           if ((tid & 31) == 0)
-            *((volatile unsigned long long*)&stop_s.part[sl][tid >> 5]) = stop_word(tests, __float_as_uint(ws));
-          float* slot = keep + (size_t)(tests % kKeep) * PM * T;
-#pragma unroll
-          for (int c = 0; c < PM; ++c) slot[c * T + tid] = f[c];
+            *((volatile unsigned long long*)&stop_s.part[tests % kStopSlots][tid >> 5]) =
+                stop_word(tests, __float_as_uint(ws));
           ++tests;
           if (tests > kLag) {
             const int j = tests - 1 - kLag;
@@ -508,6 +519,22 @@ __global__ void __launch_bounds__(kThreadsAll) solve_kernel(KParams kp) {
             }
           }
         }
+        if (test && k + 1 >= a.min_inner) {
+          // this iterate's test: its term now, its warp sum next iteration
+          pend = active ? pg_sq<PM>(f, gf) : 0.f;
+          float* slot = keep + (size_t)(made % kKeep) * PM * T;
+#pragma unroll
+          for (int c = 0; c < PM; ++c) slot[c * T + tid] = f[c];
+          ++made;
+        }
+      }
+      if (test && stop_j < 0 && !aborted && made > tests) {
+        // the last test's warp sum
+        const float ws = warp_sum(pend);
+        if ((tid & 31) == 0)
+          *((volatile unsigned long long*)&stop_s.part[tests % kStopSlots][tid >> 5]) =
+              stop_word(tests, __float_as_uint(ws));
+        ++tests;
       }
       if (test && stop_j < 0 && !aborted) {
         // tests still pending when the loop ended, in order

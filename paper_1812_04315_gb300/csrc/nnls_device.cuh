@@ -37,6 +37,33 @@ __device__ __forceinline__ void hmatvec(const float* Hs, const float* y, const f
   }
 }
 
+// Index of H_ij in the packed upper triangle (row-major, i <= j).
+template <int PM>
+__host__ __device__ constexpr int packed_index(int i, int j) {
+  return i <= j ? i * PM - i * (i - 1) / 2 + (j - i) : j * PM - j * (j - 1) / 2 + (i - j);
+}
+// Small PM: the upper triangle of H held in registers (every index below is
+// a compile-time constant), loaded once per solve.
+template <int PM>
+__device__ __forceinline__ void load_packed(const float* Hs, float* Hp) {
+#pragma unroll
+  for (int i = 0; i < PM; ++i)
+#pragma unroll
+    for (int j = i; j < PM; ++j) Hp[packed_index<PM>(i, j)] = Hs[i * PM + j];
+}
+// g = H y - b from the packed registers: the operations of hmatvec in the
+// same order (H is exactly symmetric: H_cd and H_dc are the same products
+// summed in the same order), so the results are identical.
+template <int PM>
+__device__ __forceinline__ void hmatvec_packed(const float* Hp, const float* y, const float* b, float* g) {
+#pragma unroll
+  for (int c = 0; c < PM; ++c) g[c] = -b[c];
+#pragma unroll
+  for (int d = 0; d < PM; ++d)
+#pragma unroll
+    for (int c = 0; c < PM; ++c) g[c] = fmaf(Hp[packed_index<PM>(d, c)], y[d], g[c]);
+}
+
 // The same product with the loop over d kept rolled: one row of H live at a
 // time, for kernels with enough warps per SM to hide the shared-memory
 // latency and too many other live values to hold more of H.
