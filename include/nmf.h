@@ -233,6 +233,57 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
                          size_t workspace_bytes);
 
 /* ------------------------------------------------------------------------ */
+/* float64 twins (Alg. 2, Alg. 1, plain NeNMF, the inner loop of Sec. 2)     */
+/* ------------------------------------------------------------------------ */
+/*
+ * The same computations as nmf_compress and nenmf_solve, every step in
+ * float64 on the GPU, for parity at tight tolerances on small problems. They
+ * are not a fast path (float64 runs at 1/64 of the float32 rate on this GPU):
+ * products are one-output-per-thread loops, the small factorisations run in
+ * one thread, each inner solve in one CTA. Results are deterministic.
+ */
+typedef struct nenmf_problem_f64 {
+  int mode;          /* nenmf_mode_t */
+  int n, m, p, nu;   /* 1 <= p <= min(32, n, m); compressed: p <= nu <= min(NMF_MAX_SKETCH, n, m) */
+  const double* X;   /* plain mode: n x m; ignored in compressed mode */
+  const double* L;   /* compressed: nu x n */
+  const double* R;   /* compressed: m x nu */
+  const double* XL;  /* compressed: nu x m */
+  const double* XR;  /* compressed: n x nu */
+} nenmf_problem_f64_t;
+
+size_t nmf_compress_f64_workspace_size(int n, int m, int nu);
+
+/*
+ * Alg. 2 with q power steps and X_L = L X, X_R = X R, in float64. Layouts,
+ * sketches and outputs as nmf_compress (omega_L m x nu, omega_R nu x n, both
+ * device or both NULL: NULL draws the float32 sketches of nmf_gaussian_sketch
+ * from `seed`, streams 0 and 1, and widens them). Each orthonormalisation is
+ * CholeskyQR in three float64 passes, the first shifted (S + 1e-14 tr(S) I)
+ * when a pivot is below 1e-24 of the largest diagonal entry: the Q of the QR
+ * with a positive diagonal for a well-conditioned basis.
+ * Errors: NMF_ERR_INVALID_ARG (sizes: 1 <= nu <= min(NMF_MAX_SKETCH, n, m),
+ * 0 <= q <= 64; null outputs; one sketch NULL and the other not),
+ * NMF_ERR_WORKSPACE; device: NMF_ERR_NOT_SPD, NMF_ERR_NONFINITE.
+ */
+nmf_status_t nmf_compress_f64(nmf_stream_t stream, int n, int m, int nu, int q, const double* X,
+                              const double* omega_L, const double* omega_R, uint64_t seed, double* L, double* R,
+                              double* XL, double* XR, void* workspace, size_t workspace_bytes);
+
+size_t nenmf_solve_f64_workspace_size(const nenmf_problem_f64_t* problem);
+
+/*
+ * nenmf_solve in float64 (both modes): max_outer outer iterations from
+ * (G, F) (device, n x p and p x m, updated in place), the inner loop, stop
+ * test, eps rule and adaptive restart of nenmf_solve; L_c = lambda_max(H) by
+ * cyclic Jacobi. record_G, record_F and record_time_ns must be NULL
+ * (NMF_ERR_UNSUPPORTED otherwise). stats as nenmf_solve (device, may be NULL).
+ */
+nmf_status_t nenmf_solve_f64(nmf_stream_t stream, const nenmf_problem_f64_t* problem, double* G, double* F,
+                             const nenmf_params_t* params, nenmf_stats_t* stats, void* workspace,
+                             size_t workspace_bytes);
+
+/* ------------------------------------------------------------------------ */
 /* Many independent compressed problems of different sizes (Alg. 1)          */
 /* ------------------------------------------------------------------------ */
 /*

@@ -40,6 +40,12 @@ class Problem(ctypes.Structure):
                 ("R", ctypes.c_void_p), ("XL", ctypes.c_void_p), ("XR", ctypes.c_void_p)]
 
 
+class ProblemF64(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("n", ctypes.c_int), ("m", ctypes.c_int), ("p", ctypes.c_int),
+                ("nu", ctypes.c_int), ("X", ctypes.c_void_p), ("L", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                ("XL", ctypes.c_void_p), ("XR", ctypes.c_void_p)]
+
+
 class Params(ctypes.Structure):
     _fields_ = [("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int), ("min_inner", ctypes.c_int),
                 ("tol_mode", ctypes.c_int), ("tol", ctypes.c_double), ("record_G", ctypes.c_void_p),
@@ -85,6 +91,10 @@ def lib() -> ctypes.CDLL:
         "nmf_compress_batched_workspace_size": (sz, [i, vp, i]),
         "nmf_compress_batched": (i, [vp, i, vp, i, i, vp, sz]),
         "nenmf_solve_workspace_size": (sz, [ctypes.POINTER(Problem)]),
+        "nmf_compress_f64_workspace_size": (sz, [i, i, i]),
+        "nmf_compress_f64": (i, [vp, i, i, i, i, vp, vp, vp, u64, vp, vp, vp, vp, vp, sz]),
+        "nenmf_solve_f64_workspace_size": (sz, [ctypes.POINTER(ProblemF64)]),
+        "nenmf_solve_f64": (i, [vp, ctypes.POINTER(ProblemF64), vp, vp, ctypes.POINTER(Params), vp, vp, sz]),
         "nenmf_solve": (i, [vp, ctypes.POINTER(Problem), vp, vp, ctypes.POINTER(Params), vp, vp, sz]),
         "nmf_rre_workspace_size": (sz, [i, i, i]),
         "nmf_rre": (i, [vp, i, i, i, vp, vp, vp, vp, vp, sz]),
@@ -117,7 +127,8 @@ def exported_symbols():
             "nmf_set_kernel_path", "nmf_kernel_launches", "nmf_rre_static",
             "nenmf_solve_batched_workspace_size", "nenmf_batch_plan_info", "nenmf_solve_batched",
             "nenmf_backward_workspace_size", "nenmf_backward", "nmf_compress_variant",
-            "nmf_compress_batched_workspace_size", "nmf_compress_batched"]
+            "nmf_compress_batched_workspace_size", "nmf_compress_batched", "nmf_compress_f64_workspace_size",
+            "nmf_compress_f64", "nenmf_solve_f64_workspace_size", "nenmf_solve_f64"]
 
 
 # ---------------------------------------------------------------------------
@@ -143,6 +154,14 @@ def _check_f32(name, t, shape):
         raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
     if tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def _check_f64(name, t, shape):
+    torch = _torch()
+    if t.device.type != "cuda" or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
 
 
 def _ok(code, where):
@@ -448,3 +467,65 @@ def dual_product(X, A=None, B=None, prec: int = PREC_FP32, ws=None):
     _ok(lib().nmf_dual_product(_stream(), n, m, k, prec, _ptr(X), _ptr(A), _ptr(B), _ptr(YN), _ptr(YT), _ptr(ws),
                                ws.numel()), "nmf_dual_product")
     return YN, YT
+
+
+# ---------------------------------------------------------------------------
+# float64 twins
+# ---------------------------------------------------------------------------
+
+def compress_f64(X, nu: int, q: int, omega_L=None, omega_R=None, seed: int = 0, ws=None):
+    """nmf_compress_f64: (L nu x n, R m x nu, X_L nu x m, X_R n x nu) in float64."""
+    torch = _torch()
+    n, m = X.shape
+    _check_f64("X", X, (n, m))
+    if omega_L is not None:
+        _check_f64("omega_L", omega_L, (m, nu))
+        _check_f64("omega_R", omega_R, (nu, n))
+    L = torch.empty((nu, n), dtype=torch.float64, device="cuda")
+    R = torch.empty((m, nu), dtype=torch.float64, device="cuda")
+    XL = torch.empty((nu, m), dtype=torch.float64, device="cuda")
+    XR = torch.empty((n, nu), dtype=torch.float64, device="cuda")
+    if ws is None:
+        ws = workspace(int(lib().nmf_compress_f64_workspace_size(n, m, nu)))
+    _ok(lib().nmf_compress_f64(_stream(), n, m, nu, q, _ptr(X), _ptr(omega_L), _ptr(omega_R), seed, _ptr(L), _ptr(R),
+                               _ptr(XL), _ptr(XR), _ptr(ws), ws.numel()), "nmf_compress_f64")
+    return L, R, XL, XR
+
+
+def plain_problem_f64(X, p: int) -> ProblemF64:
+    n, m = X.shape
+    _check_f64("X", X, (n, m))
+    pr = ProblemF64()
+    pr.mode, pr.n, pr.m, pr.p, pr.nu, pr.X = PLAIN, n, m, p, 0, X.data_ptr()
+    pr._keep = (X,)
+    return pr
+
+
+def compressed_problem_f64(L, R, XL, XR, p: int) -> ProblemF64:
+    nu, n = L.shape
+    m = R.shape[0]
+    for name, t, shp in (("L", L, (nu, n)), ("R", R, (m, nu)), ("XL", XL, (nu, m)), ("XR", XR, (n, nu))):
+        _check_f64(name, t, shp)
+    pr = ProblemF64()
+    pr.mode, pr.n, pr.m, pr.p, pr.nu = COMPRESSED, n, m, p, nu
+    pr.L, pr.R, pr.XL, pr.XR = L.data_ptr(), R.data_ptr(), XL.data_ptr(), XR.data_ptr()
+    pr._keep = (L, R, XL, XR)
+    return pr
+
+
+def solve_f64(problem: ProblemF64, G, F, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
+              tol_mode: int = TOL_REL, restart: bool = False, stats=None, ws=None):
+    """nenmf_solve_f64 in place on G (n x p) and F (p x m), float64; returns the device stats buffer."""
+    torch = _torch()
+    _check_f64("G", G, (problem.n, problem.p))
+    _check_f64("F", F, (problem.p, problem.m))
+    pa = Params()
+    pa.max_outer, pa.max_inner, pa.min_inner, pa.tol_mode, pa.tol = max_outer, max_inner, min_inner, tol_mode, tol
+    pa.restart = int(bool(restart))
+    if stats is None:
+        stats = torch.zeros(ctypes.sizeof(Stats), dtype=torch.uint8, device="cuda")
+    if ws is None:
+        ws = workspace(int(lib().nenmf_solve_f64_workspace_size(ctypes.byref(problem))))
+    _ok(lib().nenmf_solve_f64(_stream(), ctypes.byref(problem), _ptr(G), _ptr(F), ctypes.byref(pa), _ptr(stats),
+                              _ptr(ws), ws.numel()), "nenmf_solve_f64")
+    return stats

@@ -110,3 +110,37 @@ def test_variant_argument_errors_are_host_side(L):
                                   v(256), 1 << 30) == 1
     assert L.nmf_compress_variant(None, 10, 10, 4, 0, 0, 1, v(256), None, None, 0, v(256), v(256), v(256), v(256),
                                   v(256), 1 << 30) == 1
+
+
+def test_f64_twin_argument_errors_are_host_side(L):
+    import paper_1812_04315_gb300 as pkg
+    v = ctypes.c_void_p
+    assert L.nmf_compress_f64_workspace_size(500, 400, 10) > 500 * 400
+    assert L.nmf_compress_f64_workspace_size(10, 10, 11) == 0
+    # nu > min(n, m), q out of range, null output, one sketch only, bad workspace
+    assert L.nmf_compress_f64(None, 10, 10, 11, 1, v(256), None, None, 0, v(256), v(256), v(256), v(256), v(256), 1 << 30) == 1
+    assert L.nmf_compress_f64(None, 10, 10, 4, 65, v(256), None, None, 0, v(256), v(256), v(256), v(256), v(256), 1 << 30) == 1
+    assert L.nmf_compress_f64(None, 10, 10, 4, 1, v(256), None, None, 0, None, v(256), v(256), v(256), v(256), 1 << 30) == 1
+    assert L.nmf_compress_f64(None, 10, 10, 4, 1, v(256), v(256), None, 0, v(256), v(256), v(256), v(256), v(256), 1 << 30) == 1
+    assert L.nmf_compress_f64(None, 10, 10, 4, 1, v(256), None, None, 0, v(256), v(256), v(256), v(256), v(100), 1 << 30) == 2
+    assert L.nmf_compress_f64(None, 10, 10, 4, 1, v(256), None, None, 0, v(256), v(256), v(256), v(256), v(256), 16) == 2
+    pr = pkg.ProblemF64()
+    pr.mode, pr.n, pr.m, pr.p, pr.nu, pr.X = pkg.PLAIN, 50, 40, 5, 0, 256
+    assert L.nenmf_solve_f64_workspace_size(ctypes.byref(pr)) > 0
+    pa = pkg.Params()
+    pa.max_outer, pa.max_inner, pa.min_inner, pa.tol = 1, 10, 1, 0.0
+    big = 1 << 30
+    pa.record_G = 256
+    assert L.nenmf_solve_f64(None, ctypes.byref(pr), v(256), v(256), ctypes.byref(pa), None, v(256), big) == 7
+    pa.record_G = None
+    pa.max_inner = 0
+    assert L.nenmf_solve_f64(None, ctypes.byref(pr), v(256), v(256), ctypes.byref(pa), None, v(256), big) == 1
+    pa.max_inner = 10
+    pr.p = 33  # above the float64 twin's limit
+    assert L.nenmf_solve_f64_workspace_size(ctypes.byref(pr)) == 0
+    assert L.nenmf_solve_f64(None, ctypes.byref(pr), v(256), v(256), ctypes.byref(pa), None, v(256), big) == 1
+    pr.p, pr.mode, pr.nu = 5, pkg.COMPRESSED, 4  # nu < p
+    assert L.nenmf_solve_f64(None, ctypes.byref(pr), v(256), v(256), ctypes.byref(pa), None, v(256), big) == 1
+    pr.nu = 8
+    pr.L = pr.R = pr.XL = pr.XR = 256
+    assert L.nenmf_solve_f64(None, ctypes.byref(pr), v(256), v(256), ctypes.byref(pa), None, v(100), big) == 2
