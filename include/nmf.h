@@ -8,8 +8,8 @@
  * the randomized subspace iteration of Alg. 2.
  *
  * Conventions shared by every call
- *  - Matrices are dense, row-major, float32, with the leading dimension equal
- *    to the number of columns (no padding): X is n x m, G is n x p, F is p x m,
+ *  - Matrices are dense, row-major, float32 (float64 in the *_f64 twins), with
+ *    the leading dimension equal to the number of columns (no padding): X is n x m, G is n x p, F is p x m,
  *    L is nu x n, R is m x nu, X_L is nu x m, X_R is n x nu.
  *  - Every matrix pointer is DEVICE memory owned by the caller, unless a
  *    parameter says "host". The library keeps no pointer after a call returns.
@@ -282,6 +282,24 @@ size_t nenmf_solve_f64_workspace_size(const nenmf_problem_f64_t* problem);
 nmf_status_t nenmf_solve_f64(nmf_stream_t stream, const nenmf_problem_f64_t* problem, double* G, double* F,
                              const nenmf_params_t* params, nenmf_stats_t* stats, void* workspace,
                              size_t workspace_bytes);
+
+size_t nenmf_backward_f64_workspace_size(const nenmf_problem_f64_t* problem, const nenmf_params_t* params);
+
+/*
+ * nenmf_backward in float64 (compressed mode; NMF_ERR_UNSUPPORTED in plain
+ * mode): the cotangents of X_L, X_R, G0, F0 (and optionally of X through
+ * X_L = L X, X_R = X R: dX = L^T dXL + dXR R^T, n x m) given those of the
+ * returned G_T (n x p) and F_T (p x m), for max_outer T outer iterations of
+ * exactly max_inner K inner iterations (tol <= 0, restart 0, T <= 4096,
+ * K <= 1024; NMF_ERR_INVALID_ARG otherwise). The forward is recomputed from
+ * (G0, F0), so no snapshots are passed. Readings as nenmf_backward: the
+ * projection's derivative 1[z > 0], d lambda_max = v v^T for the unit top
+ * eigenvector v (cyclic Jacobi).
+ */
+nmf_status_t nenmf_backward_f64(nmf_stream_t stream, const nenmf_problem_f64_t* problem,
+                                const nenmf_params_t* params, const double* G0, const double* F0,
+                                const double* dG_T, const double* dF_T, double* dXL, double* dXR, double* dG0,
+                                double* dF0, double* dX, void* workspace, size_t workspace_bytes);
 
 /* ------------------------------------------------------------------------ */
 /* Many independent compressed problems of different sizes (Alg. 1)          */

@@ -95,6 +95,9 @@ def lib() -> ctypes.CDLL:
         "nmf_compress_f64": (i, [vp, i, i, i, i, vp, vp, vp, u64, vp, vp, vp, vp, vp, sz]),
         "nenmf_solve_f64_workspace_size": (sz, [ctypes.POINTER(ProblemF64)]),
         "nenmf_solve_f64": (i, [vp, ctypes.POINTER(ProblemF64), vp, vp, ctypes.POINTER(Params), vp, vp, sz]),
+        "nenmf_backward_f64_workspace_size": (sz, [ctypes.POINTER(ProblemF64), ctypes.POINTER(Params)]),
+        "nenmf_backward_f64": (i, [vp, ctypes.POINTER(ProblemF64), ctypes.POINTER(Params), vp, vp, vp, vp, vp, vp, vp,
+                                   vp, vp, vp, sz]),
         "nenmf_solve": (i, [vp, ctypes.POINTER(Problem), vp, vp, ctypes.POINTER(Params), vp, vp, sz]),
         "nmf_rre_workspace_size": (sz, [i, i, i]),
         "nmf_rre": (i, [vp, i, i, i, vp, vp, vp, vp, vp, sz]),
@@ -128,7 +131,8 @@ def exported_symbols():
             "nenmf_solve_batched_workspace_size", "nenmf_batch_plan_info", "nenmf_solve_batched",
             "nenmf_backward_workspace_size", "nenmf_backward", "nmf_compress_variant",
             "nmf_compress_batched_workspace_size", "nmf_compress_batched", "nmf_compress_f64_workspace_size",
-            "nmf_compress_f64", "nenmf_solve_f64_workspace_size", "nenmf_solve_f64"]
+            "nmf_compress_f64", "nenmf_solve_f64_workspace_size", "nenmf_solve_f64",
+            "nenmf_backward_f64_workspace_size", "nenmf_backward_f64"]
 
 
 # ---------------------------------------------------------------------------
@@ -529,3 +533,22 @@ def solve_f64(problem: ProblemF64, G, F, max_outer: int, max_inner: int, min_inn
     _ok(lib().nenmf_solve_f64(_stream(), ctypes.byref(problem), _ptr(G), _ptr(F), ctypes.byref(pa), _ptr(stats),
                               _ptr(ws), ws.numel()), "nenmf_solve_f64")
     return stats
+
+
+def backward_f64(problem: ProblemF64, G0, F0, dG_T, dF_T, max_outer: int, max_inner: int, want_dX: bool = False,
+                 ws=None):
+    """nenmf_backward_f64: (dX_L, dX_R, dG0, dF0, dX or None), float64."""
+    torch = _torch()
+    n, m, p, nu = problem.n, problem.m, problem.p, problem.nu
+    for name, t, shp in (("G0", G0, (n, p)), ("F0", F0, (p, m)), ("dG_T", dG_T, (n, p)), ("dF_T", dF_T, (p, m))):
+        _check_f64(name, t, shp)
+    pa = Params()
+    pa.max_outer, pa.max_inner, pa.min_inner, pa.tol = max_outer, max_inner, 1, 0.0
+    out = [torch.empty(shp, dtype=torch.float64, device="cuda") for shp in ((nu, m), (n, nu), (n, p), (p, m))]
+    dX = torch.empty((n, m), dtype=torch.float64, device="cuda") if want_dX else None
+    if ws is None:
+        ws = workspace(int(lib().nenmf_backward_f64_workspace_size(ctypes.byref(problem), ctypes.byref(pa))))
+    _ok(lib().nenmf_backward_f64(_stream(), ctypes.byref(problem), ctypes.byref(pa), _ptr(G0), _ptr(F0), _ptr(dG_T),
+                                 _ptr(dF_T), *[_ptr(t) for t in out], _ptr(dX), _ptr(ws), ws.numel()),
+        "nenmf_backward_f64")
+    return (*out, dX)

@@ -34,7 +34,7 @@ int grid64(long long work, int threads) {
 // and B(k, j) = B[k brs + j bcs]; one output per thread, k ascending.
 __global__ void gemm_f64_kernel(int M, int N, int K, const double* __restrict__ A, long long ars, long long acs,
                                 const double* __restrict__ B, long long brs, long long bcs, double* __restrict__ C,
-                                long long ldc, Control* ctrl) {
+                                long long ldc, int accumulate, double alpha, Control* ctrl) {
   if (call_failed(ctrl)) return;
   const long long total = (long long)M * N;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -42,14 +42,25 @@ __global__ void gemm_f64_kernel(int M, int N, int K, const double* __restrict__ 
     const long long i = idx / N, j = idx % N;
     double s = 0.0;
     for (int k = 0; k < K; ++k) s = fma(A[i * ars + k * acs], B[k * brs + j * bcs], s);
-    C[i * ldc + j] = s;
+    C[i * ldc + j] = accumulate ? C[i * ldc + j] + alpha * s : alpha * s;
   }
 }
 
 cudaError_t gemm64(int M, int N, int K, const double* A, long long ars, long long acs, const double* B, long long brs,
                    long long bcs, double* C, long long ldc, Control* ctrl, cudaStream_t s) {
   count_launches(1);
-  gemm_f64_kernel<<<grid64((long long)M * N, 256), 256, 0, s>>>(M, N, K, A, ars, acs, B, brs, bcs, C, ldc, ctrl);
+  gemm_f64_kernel<<<grid64((long long)M * N, 256), 256, 0, s>>>(M, N, K, A, ars, acs, B, brs, bcs, C, ldc, 0, 1.0,
+                                                                  ctrl);
+  return cudaGetLastError();
+}
+
+// C += alpha A B (same layouts as gemm64).
+cudaError_t gemm64_acc(int M, int N, int K, const double* A, long long ars, long long acs, const double* B,
+                       long long brs, long long bcs, double* C, long long ldc, double alpha, Control* ctrl,
+                       cudaStream_t s) {
+  count_launches(1);
+  gemm_f64_kernel<<<grid64((long long)M * N, 256), 256, 0, s>>>(M, N, K, A, ars, acs, B, brs, bcs, C, ldc, 1, alpha,
+                                                                  ctrl);
   return cudaGetLastError();
 }
 
@@ -175,9 +186,13 @@ __global__ void beta_f64_kernel(double* beta, int K) {
 }
 
 // lambda_max of the symmetric p x p H by cyclic Jacobi rotations (one
-// thread; A is p x p scratch), written to *lam.
-__global__ void lambda_f64_kernel(const double* H, int p, double* A, double* lam, Control* ctrl) {
+// thread; A is p x p scratch), written to *lam; with V (p x p scratch) and
+// v (p), also the unit eigenvector of lambda_max (the rotations accumulated).
+__global__ void lambda_f64_kernel(const double* H, int p, double* A, double* lam, double* V, double* v,
+                                  Control* ctrl) {
   if (call_failed(ctrl) || threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (V)
+    for (int i = 0; i < p * p; ++i) V[i] = (i / p == i % p) ? 1.0 : 0.0;
   double nrm = 0.0;
   for (int i = 0; i < p * p; ++i) {
     A[i] = H[i];
@@ -211,11 +226,20 @@ __global__ void lambda_f64_kernel(const double* H, int p, double* A, double* lam
           A[i * p + l] = c * x - sn * y;
           A[j * p + l] = sn * x + c * y;
         }
+        if (V)
+          for (int l = 0; l < p; ++l) {  // V J: eigenvectors in the columns of V
+            const double x = V[l * p + i], y = V[l * p + j];
+            V[l * p + i] = c * x - sn * y;
+            V[l * p + j] = sn * x + c * y;
+          }
       }
   }
-  double mx = A[0];
-  for (int i = 1; i < p; ++i) mx = fmax(mx, A[i * p + i]);
-  *lam = mx;
+  int im = 0;
+  for (int i = 1; i < p; ++i)
+    if (A[i * p + i] > A[im * p + im]) im = i;
+  *lam = A[im * p + im];
+  if (V)
+    for (int l = 0; l < p; ++l) v[l] = V[l * p + im];
 }
 
 // Fixed-order sum over the block of one double per thread (valid in thread 0).
@@ -350,6 +374,116 @@ __global__ void nnls_f64_kernel(const double* H, const double* B, double* F, int
     st->pg_norm[side] = sqrt(pg2);
     st->lipschitz[side] = Lc;
   }
+}
+
+// ---- reverse mode (the derivative of K unrolled inner iterations) ----------
+// Tapes are [p][K][N] (row c of every iteration contiguous), so that
+// dH = -(1/L_c) sum_k dz_k Y_k^T is one product over the (k, j) pairs.
+
+// K iterations of the inner loop (no stop test, no restart) on the columns
+// of Y0 (p x N), recording Y_k (the point the step starts from) and z_k
+// (before the projection); Fout = F_{K-1}. With L_c <= 0, Fout = Y0.
+__global__ void nnls_tape_f64_kernel(const double* H, const double* B, const double* Y0, double* Fout, int p, int N,
+                                     int K, const double* lam_p, const double* beta, double* tapeY, double* tapeZ,
+                                     Control* ctrl) {
+  __shared__ double Hs[kMaxP64 * kMaxP64];
+  if (call_failed(ctrl)) return;
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) Hs[i] = H[i];
+  __syncthreads();
+  const double Lc = *lam_p;
+  const size_t KN = (size_t)K * N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    double y[kMaxP64], f[kMaxP64], fp[kMaxP64];
+    for (int c = 0; c < p; ++c) y[c] = fp[c] = f[c] = Y0[(size_t)c * N + j];
+    if (Lc > 0.0) {
+      for (int k = 0; k < K; ++k) {
+        for (int c = 0; c < p; ++c) {
+          double g = -B[(size_t)c * N + j];
+          for (int d = 0; d < p; ++d) g = fma(Hs[c * p + d], y[d], g);
+          const double z = y[c] - g / Lc;
+          tapeY[c * KN + (size_t)k * N + j] = y[c];
+          tapeZ[c * KN + (size_t)k * N + j] = z;
+          f[c] = fmax(0.0, z);
+        }
+        for (int c = 0; c < p; ++c) {
+          y[c] = f[c] + beta[k] * (f[c] - fp[c]);
+          fp[c] = f[c];
+        }
+      }
+    }
+    for (int c = 0; c < p; ++c) Fout[(size_t)c * N + j] = f[c];
+  }
+}
+
+// The adjoint of those K iterations for cotangent dOut (p x N), k = K-1..0:
+//   dF_k = dOut [k = K-1] + carry + (1 + beta_k) dY_{k+1},  carry' = -beta_k dY_{k+1};
+//   dz_k = 1[z_k > 0] dF_k;  dY_k = dz_k - H dz_k / L_c;
+//   dB += dz_k / L_c;  dL_c += <Y_k - z_k, dz_k> / L_c;
+// then dY0 = dY_0 + carry (F_{-1} = Y_0). Writes dY0 and dB (p x N), dz_k to
+// tapeDZ, and dL_c (summed over the block in a fixed order) to *dL.
+// With L_c <= 0 the map is the identity: dY0 = dOut, dB = 0, dL = 0.
+__global__ void nnls_adj_f64_kernel(const double* H, const double* dOut, int p, int N, int K, const double* lam_p,
+                                    const double* beta, const double* tapeY, const double* tapeZ, double* tapeDZ,
+                                    double* dY0, double* dB, double* dL, Control* ctrl) {
+  __shared__ double red[kNnlsThreads];
+  __shared__ double Hs[kMaxP64 * kMaxP64];
+  if (call_failed(ctrl)) return;
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) Hs[i] = H[i];
+  __syncthreads();
+  const double Lc = *lam_p;
+  const size_t KN = (size_t)K * N;
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    if (!(Lc > 0.0)) {
+      for (int c = 0; c < p; ++c) {
+        dY0[(size_t)c * N + j] = dOut[(size_t)c * N + j];
+        dB[(size_t)c * N + j] = 0.0;
+      }
+      continue;
+    }
+    double dyn[kMaxP64], carry[kMaxP64], dz[kMaxP64], db[kMaxP64];
+    for (int c = 0; c < p; ++c) dyn[c] = carry[c] = db[c] = 0.0;
+    for (int k = K - 1; k >= 0; --k) {
+      for (int c = 0; c < p; ++c) {
+        const double dF = (k == K - 1 ? dOut[(size_t)c * N + j] : 0.0) + carry[c] + (1.0 + beta[k]) * dyn[c];
+        carry[c] = -beta[k] * dyn[c];
+        const size_t t = c * KN + (size_t)k * N + j;
+        const double z = tapeZ[t];
+        dz[c] = z > 0.0 ? dF : 0.0;
+        tapeDZ[t] = dz[c];
+        db[c] += dz[c] / Lc;
+        acc += (tapeY[t] - z) * dz[c] / Lc;
+      }
+      for (int c = 0; c < p; ++c) {
+        double h = 0.0;
+        for (int d = 0; d < p; ++d) h = fma(Hs[c * p + d], dz[d], h);
+        dyn[c] = dz[c] - h / Lc;
+      }
+    }
+    for (int c = 0; c < p; ++c) {
+      dY0[(size_t)c * N + j] = dyn[c] + carry[c];
+      dB[(size_t)c * N + j] = db[c];
+    }
+  }
+  const double s = block_sum64(acc, red);
+  if (threadIdx.x == 0) *dL = s;
+}
+
+// dH (p x p) := (dH + dL v v^T), then S := dH + dH^T (one thread per entry).
+__global__ void dh_finish_f64_kernel(double* dH, const double* dL, const double* v, int p, double* S,
+                                     Control* ctrl) {
+  if (call_failed(ctrl)) return;
+  __shared__ double T[kMaxP64 * kMaxP64];
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) T[i] = dH[i] + (*dL) * v[i / p] * v[i % p];
+  __syncthreads();
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) S[i] = T[i] + T[(i % p) * p + i / p];
+}
+
+// dH *= -1 / L_c (0 when L_c <= 0: the solve made no step).
+__global__ void scale_by_lam_kernel(double* dH, int p, const double* lam_p, Control* ctrl) {
+  if (call_failed(ctrl)) return;
+  const double Lc = *lam_p;
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) dH[i] = Lc > 0.0 ? -dH[i] / Lc : 0.0;
 }
 
 __global__ void finish_f64_kernel(nenmf_stats_t* st, int outer, Control* ctrl) {
@@ -488,9 +622,134 @@ cudaError_t f_side(const nenmf_problem_f64_t& pr, const double* Gt, const Solve6
 cudaError_t inner64(const nenmf_problem_f64_t& pr, double* U, int N, const nenmf_params_t& pa, const Solve64Ws& w,
                     nenmf_stats_t* st, int side, cudaStream_t s) {
   count_launches(2);
-  lambda_f64_kernel<<<1, 1, 0, s>>>(w.H, pr.p, w.J, w.lam, w.ctrl);
+  lambda_f64_kernel<<<1, 1, 0, s>>>(w.H, pr.p, w.J, w.lam, nullptr, nullptr, w.ctrl);
   nnls_f64_kernel<<<1, kNnlsThreads, 0, s>>>(w.H, w.Bm, U, pr.p, N, w.lam, w.beta, pa.max_inner, pa.min_inner,
                                               w.eps2, pa.restart, w.Y, w.Fp, w.obj, w.rc, st, side, w.ctrl);
+  return cudaGetLastError();
+}
+
+// ---- reverse mode, host side ----------------------------------------------
+struct Back64Ws {
+  Control* ctrl;
+  double* snapGt;  // [T][p][n]: G^t transposed before outer iteration t
+  double* snapF;   // [T][p][m]
+  double* Gt;      // p x n (running forward; then G^{t+1} of the sweep)
+  double* F;       // p x m
+  double* tYg;     // [p][K][n] tapes of the G update
+  double* tZg;
+  double* tDg;
+  double* tYf;     // [p][K][m] tapes of the F update
+  double* tZf;
+  double* tDf;
+  double* FR;      // p x nu
+  double* GL;      // nu x p
+  double* HG;      // p x p
+  double* HF;
+  double* dH;      // p x p
+  double* S;       // p x p
+  double* J;       // p x p Jacobi scratch
+  double* V;       // p x p eigenvectors
+  double* vG;      // p
+  double* vF;
+  double* lamG;
+  double* lamF;
+  double* dL;
+  double* Bg;      // p x n
+  double* Bf;      // p x m
+  double* dBg;     // p x n
+  double* dBf;     // p x m
+  double* dGt;     // p x n (cotangent of G^T)
+  double* dGo;     // p x n (cotangent of the previous G^T)
+  double* dG;      // n x p
+  double* dFo;     // p x m (cotangent of the previous F)
+  double* dF;      // p x m
+  double* dGL;     // nu x p
+  double* dFR;     // p x nu
+  double* beta;    // K
+  size_t bytes;
+};
+
+Back64Ws carve_back64(void* base, const nenmf_problem_f64_t& pr, int T, int K) {
+  Back64Ws w{};
+  Carver cv(base);
+  const size_t n = pr.n, m = pr.m, p = pr.p, nu = pr.nu;
+  w.ctrl = cv.take<Control>(1);
+  w.snapGt = cv.take<double>((size_t)T * p * n);
+  w.snapF = cv.take<double>((size_t)T * p * m);
+  w.Gt = cv.take<double>(p * n);
+  w.F = cv.take<double>(p * m);
+  w.tYg = cv.take<double>(p * K * n);
+  w.tZg = cv.take<double>(p * K * n);
+  w.tDg = cv.take<double>(p * K * n);
+  w.tYf = cv.take<double>(p * K * m);
+  w.tZf = cv.take<double>(p * K * m);
+  w.tDf = cv.take<double>(p * K * m);
+  w.FR = cv.take<double>(p * nu);
+  w.GL = cv.take<double>(nu * p);
+  w.HG = cv.take<double>(p * p);
+  w.HF = cv.take<double>(p * p);
+  w.dH = cv.take<double>(p * p);
+  w.S = cv.take<double>(p * p);
+  w.J = cv.take<double>(p * p);
+  w.V = cv.take<double>(p * p);
+  w.vG = cv.take<double>(p);
+  w.vF = cv.take<double>(p);
+  w.lamG = cv.take<double>(1);
+  w.lamF = cv.take<double>(1);
+  w.dL = cv.take<double>(1);
+  w.Bg = cv.take<double>(p * n);
+  w.Bf = cv.take<double>(p * m);
+  w.dBg = cv.take<double>(p * n);
+  w.dBf = cv.take<double>(p * m);
+  w.dGt = cv.take<double>(p * n);
+  w.dGo = cv.take<double>(p * n);
+  w.dG = cv.take<double>(n * p);
+  w.dFo = cv.take<double>(p * m);
+  w.dF = cv.take<double>(p * m);
+  w.dGL = cv.take<double>(nu * p);
+  w.dFR = cv.take<double>(p * nu);
+  w.beta = cv.take<double>(K > 0 ? K : 1);
+  w.bytes = cv.size();
+  return w;
+}
+
+bool back64_args_ok(const nenmf_problem_f64_t* pr, const nenmf_params_t* pa) {
+  return problem64_ok(pr) && pr->mode == NENMF_COMPRESSED && pa && pa->max_outer >= 0 && pa->max_outer <= 4096 &&
+         pa->max_inner >= 1 && pa->max_inner <= 1024 && pa->tol <= 0.0 && !pa->restart;
+}
+
+// The G update's H, B (the unknown is G^T) from F, with lambda_max and its eigenvector.
+cudaError_t back_g_inputs(const nenmf_problem_f64_t& pr, const double* F, const Back64Ws& w, cudaStream_t s) {
+  const int n = pr.n, m = pr.m, p = pr.p, nu = pr.nu;
+  F64_CU(gemm64(p, nu, m, F, m, 1, pr.R, nu, 1, w.FR, nu, w.ctrl, s));      // F_R = F R
+  F64_CU(gemm64(p, p, nu, w.FR, nu, 1, w.FR, 1, nu, w.HG, p, w.ctrl, s));   // F_R F_R^T
+  F64_CU(gemm64(p, n, nu, w.FR, nu, 1, pr.XR, 1, nu, w.Bg, n, w.ctrl, s));  // F_R X_R^T
+  count_launches(1);
+  lambda_f64_kernel<<<1, 1, 0, s>>>(w.HG, p, w.J, w.lamG, w.V, w.vG, w.ctrl);
+  return cudaGetLastError();
+}
+
+// The F update's H, B from G^T.
+cudaError_t back_f_inputs(const nenmf_problem_f64_t& pr, const double* Gt, const Back64Ws& w, cudaStream_t s) {
+  const int n = pr.n, m = pr.m, p = pr.p, nu = pr.nu;
+  F64_CU(gemm64(nu, p, n, pr.L, n, 1, Gt, 1, n, w.GL, p, w.ctrl, s));      // G_L = L G
+  F64_CU(gemm64(p, p, nu, w.GL, 1, p, w.GL, p, 1, w.HF, p, w.ctrl, s));    // G_L^T G_L
+  F64_CU(gemm64(p, m, nu, w.GL, 1, p, pr.XL, m, 1, w.Bf, m, w.ctrl, s));   // G_L^T X_L
+  count_launches(1);
+  lambda_f64_kernel<<<1, 1, 0, s>>>(w.HF, p, w.J, w.lamF, w.V, w.vF, w.ctrl);
+  return cudaGetLastError();
+}
+
+// S = dH + dH^T of one inner solve: dH = -(1/L_c) sum_k dz_k Y_k^T + dL v v^T.
+cudaError_t back_sym_dh(int p, int N, int K, const double* tD, const double* tY, const double* lam, const double* v,
+                        const Back64Ws& w, double lam_host_unused, cudaStream_t s) {
+  (void)lam_host_unused;
+  // dH = sum over (k, j) of dz (p x KN) times Y^T, scaled by -1/L_c on the device
+  F64_CU(gemm64(p, p, K * N, tD, (long long)K * N, 1, tY, 1, (long long)K * N, w.dH, p, w.ctrl, s));
+  count_launches(1);
+  scale_by_lam_kernel<<<1, kMaxP64 * kMaxP64, 0, s>>>(w.dH, p, lam, w.ctrl);
+  count_launches(1);
+  dh_finish_f64_kernel<<<1, kMaxP64 * kMaxP64, 0, s>>>(w.dH, w.dL, v, p, w.S, w.ctrl);
   return cudaGetLastError();
 }
 
@@ -603,6 +862,101 @@ nmf_status_t nenmf_solve_f64(nmf_stream_t stream, const nenmf_problem_f64_t* pro
     count_launches(1);
     finish_f64_kernel<<<1, 1, 0, s>>>(stats, pa.max_outer, c);
     NMF_CU(cudaGetLastError());
+  }
+  return NMF_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+size_t nenmf_backward_f64_workspace_size(const nenmf_problem_f64_t* problem, const nenmf_params_t* params) {
+  if (!back64_args_ok(problem, params)) return 0;
+  return carve_back64(nullptr, *problem, params->max_outer, params->max_inner).bytes;
+}
+
+nmf_status_t nenmf_backward_f64(nmf_stream_t stream, const nenmf_problem_f64_t* problem,
+                                const nenmf_params_t* params, const double* G0, const double* F0,
+                                const double* dG_T, const double* dF_T, double* dXL, double* dXR, double* dG0,
+                                double* dF0, double* dX, void* workspace, size_t workspace_bytes) {
+  if (problem && problem->mode != NENMF_COMPRESSED) return NMF_ERR_UNSUPPORTED;
+  if (!back64_args_ok(problem, params) || !G0 || !F0 || !dG_T || !dF_T || !dXL || !dXR || !dG0 || !dF0)
+    return NMF_ERR_INVALID_ARG;
+  const nenmf_problem_f64_t pr = *problem;
+  const int T = params->max_outer, K = params->max_inner;
+  const Back64Ws w = carve_back64(workspace, pr, T, K);
+  if (!ws64_ok(workspace, workspace_bytes, w.bytes)) return NMF_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Control* c = w.ctrl;
+  const int n = pr.n, m = pr.m, p = pr.p, nu = pr.nu;
+  NMF_CU(cudaMemsetAsync(c, 0, sizeof(Control), s));
+  count_launches(1);
+  beta_f64_kernel<<<1, 1, 0, s>>>(w.beta, K);
+  NMF_CU(cudaGetLastError());
+  // forward, keeping (G^t, F^t) before every outer iteration
+  NMF_CU(transpose64(G0, n, p, w.Gt, c, s));
+  NMF_CU(cudaMemcpyAsync(w.F, F0, sizeof(double) * (size_t)p * m, cudaMemcpyDeviceToDevice, s));
+  for (int t = 0; t < T; ++t) {
+    NMF_CU(cudaMemcpyAsync(w.snapGt + (size_t)t * p * n, w.Gt, sizeof(double) * (size_t)p * n,
+                           cudaMemcpyDeviceToDevice, s));
+    NMF_CU(cudaMemcpyAsync(w.snapF + (size_t)t * p * m, w.F, sizeof(double) * (size_t)p * m,
+                           cudaMemcpyDeviceToDevice, s));
+    NMF_CU(back_g_inputs(pr, w.F, w, s));
+    count_launches(1);
+    nnls_tape_f64_kernel<<<1, kNnlsThreads, 0, s>>>(w.HG, w.Bg, w.Gt, w.Gt, p, n, K, w.lamG, w.beta, w.tYg, w.tZg,
+                                                     c);
+    NMF_CU(back_f_inputs(pr, w.Gt, w, s));
+    count_launches(1);
+    nnls_tape_f64_kernel<<<1, kNnlsThreads, 0, s>>>(w.HF, w.Bf, w.F, w.F, p, m, K, w.lamF, w.beta, w.tYf, w.tZf, c);
+    NMF_CU(cudaGetLastError());
+  }
+  // reverse sweep
+  NMF_CU(cudaMemcpyAsync(w.dG, dG_T, sizeof(double) * (size_t)n * p, cudaMemcpyDeviceToDevice, s));
+  NMF_CU(cudaMemcpyAsync(w.dF, dF_T, sizeof(double) * (size_t)p * m, cudaMemcpyDeviceToDevice, s));
+  NMF_CU(cudaMemsetAsync(dXL, 0, sizeof(double) * (size_t)nu * m, s));
+  NMF_CU(cudaMemsetAsync(dXR, 0, sizeof(double) * (size_t)n * nu, s));
+  for (int t = T - 1; t >= 0; --t) {
+    const double* Gt0 = w.snapGt + (size_t)t * p * n;
+    const double* Fs = w.snapF + (size_t)t * p * m;
+    // recompute the two updates of outer iteration t with their tapes
+    NMF_CU(back_g_inputs(pr, Fs, w, s));
+    count_launches(1);
+    nnls_tape_f64_kernel<<<1, kNnlsThreads, 0, s>>>(w.HG, w.Bg, Gt0, w.Gt, p, n, K, w.lamG, w.beta, w.tYg, w.tZg, c);
+    NMF_CU(back_f_inputs(pr, w.Gt, w, s));
+    count_launches(1);
+    nnls_tape_f64_kernel<<<1, kNnlsThreads, 0, s>>>(w.HF, w.Bf, Fs, w.F, p, m, K, w.lamF, w.beta, w.tYf, w.tZf, c);
+    NMF_CU(cudaGetLastError());
+    // F update: (dF_old, dH_F, dB_F); dG_L = G_L (dH_F + dH_F^T) + X_L dB_F^T; dX_L += G_L dB_F; dG += L^T dG_L
+    count_launches(1);
+    nnls_adj_f64_kernel<<<1, kNnlsThreads, 0, s>>>(w.HF, w.dF, p, m, K, w.lamF, w.beta, w.tYf, w.tZf, w.tDf, w.dFo,
+                                                    w.dBf, w.dL, c);
+    NMF_CU(cudaGetLastError());
+    NMF_CU(back_sym_dh(p, m, K, w.tDf, w.tYf, w.lamF, w.vF, w, 0.0, s));
+    NMF_CU(gemm64(nu, p, p, w.GL, p, 1, w.S, p, 1, w.dGL, p, c, s));
+    NMF_CU(gemm64_acc(nu, p, m, pr.XL, m, 1, w.dBf, 1, m, w.dGL, p, 1.0, c, s));
+    NMF_CU(gemm64_acc(nu, m, p, w.GL, p, 1, w.dBf, m, 1, dXL, m, 1.0, c, s));
+    NMF_CU(gemm64_acc(n, p, nu, pr.L, 1, n, w.dGL, p, 1, w.dG, p, 1.0, c, s));
+    // G update on G^T: (dG^T_old, dH_G, dB_G); dF_R = (dH_G + dH_G^T) F_R + dB_G X_R;
+    // dX_R += dB_G^T F_R; dF = dF_old + dF_R R^T; dG = (dG^T_old)^T
+    NMF_CU(transpose64(w.dG, n, p, w.dGt, c, s));
+    count_launches(1);
+    nnls_adj_f64_kernel<<<1, kNnlsThreads, 0, s>>>(w.HG, w.dGt, p, n, K, w.lamG, w.beta, w.tYg, w.tZg, w.tDg, w.dGo,
+                                                    w.dBg, w.dL, c);
+    NMF_CU(cudaGetLastError());
+    NMF_CU(back_sym_dh(p, n, K, w.tDg, w.tYg, w.lamG, w.vG, w, 0.0, s));
+    NMF_CU(gemm64(p, nu, p, w.S, p, 1, w.FR, nu, 1, w.dFR, nu, c, s));
+    NMF_CU(gemm64_acc(p, nu, n, w.dBg, n, 1, pr.XR, nu, 1, w.dFR, nu, 1.0, c, s));
+    NMF_CU(gemm64_acc(n, nu, p, w.dBg, 1, n, w.FR, nu, 1, dXR, nu, 1.0, c, s));
+    NMF_CU(cudaMemcpyAsync(w.dF, w.dFo, sizeof(double) * (size_t)p * m, cudaMemcpyDeviceToDevice, s));
+    NMF_CU(gemm64_acc(p, m, nu, w.dFR, nu, 1, pr.R, 1, nu, w.dF, m, 1.0, c, s));
+    NMF_CU(transpose64(w.dGo, p, n, w.dG, c, s));
+  }
+  NMF_CU(cudaMemcpyAsync(dG0, w.dG, sizeof(double) * (size_t)n * p, cudaMemcpyDeviceToDevice, s));
+  NMF_CU(cudaMemcpyAsync(dF0, w.dF, sizeof(double) * (size_t)p * m, cudaMemcpyDeviceToDevice, s));
+  if (dX) {
+    // dX = L^T dX_L + dX_R R^T
+    NMF_CU(gemm64(n, m, nu, pr.L, 1, n, dXL, m, 1, dX, m, c, s));
+    NMF_CU(gemm64_acc(n, m, nu, dXR, nu, 1, pr.R, 1, nu, dX, m, 1.0, c, s));
   }
   return NMF_OK;
 }

@@ -144,3 +144,25 @@ def test_f64_twin_argument_errors_are_host_side(L):
     pr.nu = 8
     pr.L = pr.R = pr.XL = pr.XR = 256
     assert L.nenmf_solve_f64(None, ctypes.byref(pr), v(256), v(256), ctypes.byref(pa), None, v(100), big) == 2
+
+
+def test_f64_backward_argument_errors_are_host_side(L):
+    import paper_1812_04315_gb300 as pkg
+    v = ctypes.c_void_p
+    pr = pkg.ProblemF64()
+    pr.mode, pr.n, pr.m, pr.p, pr.nu = pkg.COMPRESSED, 50, 40, 4, 8
+    pr.L = pr.R = pr.XL = pr.XR = 256
+    pa = pkg.Params()
+    pa.max_outer, pa.max_inner, pa.min_inner, pa.tol = 3, 5, 1, 0.0
+    assert L.nenmf_backward_f64_workspace_size(ctypes.byref(pr), ctypes.byref(pa)) > 0
+    args = [v(256)] * 8
+    big = 1 << 30
+    pa.tol = 1e-6  # the stop test is not differentiated
+    assert L.nenmf_backward_f64(None, ctypes.byref(pr), ctypes.byref(pa), *args, None, v(256), big) == 1
+    pa.tol, pa.restart = 0.0, 1
+    assert L.nenmf_backward_f64(None, ctypes.byref(pr), ctypes.byref(pa), *args, None, v(256), big) == 1
+    pa.restart = 0
+    assert L.nenmf_backward_f64(None, ctypes.byref(pr), ctypes.byref(pa), *args, None, v(100), big) == 2
+    pr.mode = pkg.PLAIN
+    pr.X = 256
+    assert L.nenmf_backward_f64(None, ctypes.byref(pr), ctypes.byref(pa), *args, None, v(256), big) == 7

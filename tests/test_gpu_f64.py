@@ -25,7 +25,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import nenmf, philox, subspace
+from oracle import adjoint, nenmf, philox, subspace
 
 pytestmark = pytest.mark.gpu
 
@@ -176,3 +176,61 @@ def test_f64_twin_is_deterministic(nmf):
         out.append((_np(G), _np(F)))
     np.testing.assert_array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def _backward_case(nmf, n, m, p, nu, q, seed):
+    X, _, _ = synth.lowrank_data(n, m, p, seed=seed, snr_db=20.0)
+    G0, F0 = synth.initial_factors(n, m, p, seed=seed + 1)
+    OmL, OmR = synth.gaussian_sketches(n, m, nu, seed=seed + 2)
+    L, R, _, _ = subspace.compress(X, nu, q, OmL, OmR)
+    return X, L, R, G0, F0
+
+
+def _gpu_loss_and_gradient(nmf, X, L, R, G0, F0, T, K):
+    # loss ||X - G_T F_T||^2 with X_L = L X, X_R = X R (L, R fixed), every step on the GPU in float64
+    pr = nmf.compressed_problem_f64(_t(L), _t(R), _t(L @ X), _t(X @ R), G0.shape[1])
+    G, F = _t(G0), _t(F0)
+    nmf.solve_f64(pr, G, F, T, K)
+    Gd, Fd = _np(G), _np(F)
+    E = X - Gd @ Fd
+    dXL, dXR, dG0, dF0, dX = nmf.backward_f64(pr, _t(G0), _t(F0), _t(-2.0 * E @ Fd.T), _t(-2.0 * Gd.T @ E), T, K,
+                                               want_dX=True)
+    return float(np.sum(E * E)), 2.0 * E + _np(dX), _np(dG0), _np(dF0)
+
+
+@pytest.mark.parametrize("T,K", [(1, 1), (4, 5), (2, 10)])
+def test_backward_f64_matches_oracle(nmf, T, K):
+    n, m, p, nu, q = 64, 48, 4, 8, 2
+    X, L, R, G0, F0 = _backward_case(nmf, n, m, p, nu, q, seed=21)
+    loss, dX, dG0, dF0 = _gpu_loss_and_gradient(nmf, X, L, R, G0, F0, T, K)
+    lo, dXo, dG0o, dF0o = adjoint.loss_and_gradient(X, L, R, G0, F0, T, K)
+    assert abs(loss - lo) <= 1e-12 * lo
+    for a, b in ((dX, dXo), (dG0, dG0o), (dF0, dF0o)):
+        assert _rel(a, b) <= 1e-10, _rel(a, b)
+
+
+def test_backward_f64_central_differences(nmf):
+    # the GPU float64 gradient against central differences of the GPU float64
+    # forward (h = 1e-6: truncation ~h^2, rounding ~1e-16 / h), along random
+    # directions that keep every projection's sign
+    n, m, p, nu, q, T, K = 64, 48, 4, 8, 2, 4, 5
+    X, L, R, G0, F0 = _backward_case(nmf, n, m, p, nu, q, seed=21)
+    loss, dX, dG0, dF0 = _gpu_loss_and_gradient(nmf, X, L, R, G0, F0, T, K)
+    base = adjoint.projection_signs(X, L, R, G0, F0, T, K)
+    h = 1e-6
+    checked = 0
+    for d in synth.random_directions((n * m + n * p + p * m,), 12, seed=5):
+        dXd = d[:n * m].reshape(n, m)
+        dGd = d[n * m:n * m + n * p].reshape(n, p)
+        dFd = d[n * m + n * p:].reshape(p, m)
+        if not all(all(np.array_equal(a, b) for a, b in zip(
+                base, adjoint.projection_signs(X + s * h * dXd, L, R, G0 + s * h * dGd, F0 + s * h * dFd, T, K)))
+                   for s in (1, -1)):
+            continue
+        lp = _gpu_loss_and_gradient(nmf, X + h * dXd, L, R, G0 + h * dGd, F0 + h * dFd, T, K)[0]
+        lm = _gpu_loss_and_gradient(nmf, X - h * dXd, L, R, G0 - h * dGd, F0 - h * dFd, T, K)[0]
+        fd = (lp - lm) / (2 * h)
+        an = float(np.sum(dX * dXd) + np.sum(dG0 * dGd) + np.sum(dF0 * dFd))
+        assert an == pytest.approx(fd, rel=1e-6, abs=1e-8 * loss), (an, fd)
+        checked += 1
+    assert checked >= 8
