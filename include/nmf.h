@@ -397,6 +397,19 @@ nmf_status_t nmf_dual_product(nmf_stream_t stream, int n, int m, int k, nmf_prec
                               const float* A, const float* B, float* YN, float* YT, void* workspace,
                               size_t workspace_bytes);
 
+size_t nmf_project_workspace_size(int n, int m, int nu, nmf_prec_t prec);
+
+/*
+ * The first line of Alg. 1 for given bases: X_L = L X (nu x m) and
+ * X_R = X R (n x nu) from one pass over X (as nmf_compress ends). L is
+ * nu x n, R is m x nu (device, row-major); prec as nmf_compress. Used where
+ * the bases stay fixed while X changes (the differentiated map of
+ * nenmf_backward). Errors: NMF_ERR_INVALID_ARG (1 <= nu <= min(NMF_MAX_SKETCH,
+ * n, m), null pointers), NMF_ERR_WORKSPACE.
+ */
+nmf_status_t nmf_project(nmf_stream_t stream, int n, int m, int nu, nmf_prec_t prec, const float* X, const float* L,
+                         const float* R, float* XL, float* XR, void* workspace, size_t workspace_bytes);
+
 /*
  * Selects the kernel for NMF_PREC_BF16 X passes: 0 (default) uses tcgen05
  * tensor cores, 1 uses float32 CUDA cores on the same bfloat16 inputs (same

@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
         "nmf_compress_batched_workspace_size": (sz, [i, vp, i]),
         "nmf_compress_batched": (i, [vp, i, vp, i, i, vp, sz]),
         "nenmf_solve_workspace_size": (sz, [ctypes.POINTER(Problem)]),
+        "nmf_project_workspace_size": (sz, [i, i, i, i]),
+        "nmf_project": (i, [vp, i, i, i, i, vp, vp, vp, vp, vp, vp, sz]),
         "nmf_compress_f64_workspace_size": (sz, [i, i, i]),
         "nmf_compress_f64": (i, [vp, i, i, i, i, vp, vp, vp, u64, vp, vp, vp, vp, vp, sz]),
         "nenmf_solve_f64_workspace_size": (sz, [ctypes.POINTER(ProblemF64)]),
@@ -132,7 +134,7 @@ def exported_symbols():
             "nenmf_backward_workspace_size", "nenmf_backward", "nmf_compress_variant",
             "nmf_compress_batched_workspace_size", "nmf_compress_batched", "nmf_compress_f64_workspace_size",
             "nmf_compress_f64", "nenmf_solve_f64_workspace_size", "nenmf_solve_f64",
-            "nenmf_backward_f64_workspace_size", "nenmf_backward_f64"]
+            "nenmf_backward_f64_workspace_size", "nenmf_backward_f64", "nmf_project_workspace_size", "nmf_project"]
 
 
 # ---------------------------------------------------------------------------
@@ -471,6 +473,74 @@ def dual_product(X, A=None, B=None, prec: int = PREC_FP32, ws=None):
     _ok(lib().nmf_dual_product(_stream(), n, m, k, prec, _ptr(X), _ptr(A), _ptr(B), _ptr(YN), _ptr(YT), _ptr(ws),
                                ws.numel()), "nmf_dual_product")
     return YN, YT
+
+
+def project(X, L, R, prec: int = PREC_FP32, ws=None):
+    """nmf_project: (X_L = L X, X_R = X R) for given bases L (nu x n), R (m x nu)."""
+    torch = _torch()
+    n, m = X.shape
+    nu = L.shape[0]
+    _check_f32("X", X, (n, m))
+    _check_f32("L", L, (nu, n))
+    _check_f32("R", R, (m, nu))
+    XL = torch.empty((nu, m), dtype=torch.float32, device=X.device)
+    XR = torch.empty((n, nu), dtype=torch.float32, device=X.device)
+    if ws is None:
+        ws = workspace(lib().nmf_project_workspace_size(n, m, nu, prec))
+    _ok(lib().nmf_project(_stream(), n, m, nu, prec, _ptr(X), _ptr(L), _ptr(R), _ptr(XL), _ptr(XR), _ptr(ws),
+                          ws.numel()), "nmf_project")
+    return XL, XR
+
+
+_autograd_cls = None
+
+
+def _compressed_nenmf_function():
+    """torch.autograd.Function of (X, G0, F0) -> (G_T, F_T): T outer iterations of
+    compressed NeNMF (Alg. 1) with exactly K inner iterations each, for fixed bases
+    L, R (X reaches the map through X_L = L X, X_R = X R). forward: nmf_project,
+    then nenmf_solve with per-outer snapshots; backward: nenmf_backward, which
+    recomputes each outer iteration's inner steps from its snapshot."""
+    global _autograd_cls
+    if _autograd_cls is not None:
+        return _autograd_cls
+    torch = _torch()
+
+    class CompressedNeNMF(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X, G0, F0, L, R, T, K):
+            n, m = X.shape
+            p = G0.shape[1]
+            X, G0, F0, L, R = (t.detach().contiguous() for t in (X, G0, F0, L, R))
+            XL, XR = project(X, L, R)
+            prob = compressed_problem(L, R, XL, XR, p)
+            G, F = G0.clone(), F0.clone()
+            rec = SolveRecord(G=torch.empty((max(T, 1), n, p), dtype=torch.float32, device=X.device),
+                              F=torch.empty((max(T, 1), p, m), dtype=torch.float32, device=X.device))
+            if T > 0:
+                solve(prob, G, F, T, K, tol=0.0, record=rec)
+            ctx.save_for_backward(G0, F0, L, R, XL, XR, rec.G, rec.F)
+            ctx.T, ctx.K, ctx.p = T, K, p
+            return G, F
+
+        @staticmethod
+        def backward(ctx, dG, dF):
+            G0, F0, L, R, XL, XR, rG, rF = ctx.saved_tensors
+            zeros = lambda t: torch.zeros_like(t)
+            dG = zeros(G0) if dG is None else dG.contiguous()
+            dF = zeros(F0) if dF is None else dF.contiguous()
+            prob = compressed_problem(L, R, XL, XR, ctx.p)
+            _, _, dG0, dF0, dX = backward(prob, G0, F0, SolveRecord(G=rG, F=rF), dG, dF, ctx.T, ctx.K, want_dX=True)
+            return dX, dG0, dF0, None, None, None, None
+
+    _autograd_cls = CompressedNeNMF
+    return _autograd_cls
+
+
+def compressed_nenmf(X, G0, F0, L, R, T: int, K: int):
+    """Differentiable compressed NeNMF: (G_T, F_T) = CompressedNeNMF.apply(X, G0, F0, L, R, T, K);
+    gradients flow to X, G0 and F0 (float32 CUDA tensors), not to the bases."""
+    return _compressed_nenmf_function().apply(X, G0, F0, L, R, T, K)
 
 
 # ---------------------------------------------------------------------------

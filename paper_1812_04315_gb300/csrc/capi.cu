@@ -855,4 +855,43 @@ nmf_status_t nmf_dual_product(nmf_stream_t stream, int n, int m, int k, nmf_prec
   return NMF_OK;
 }
 
+size_t nmf_project_workspace_size(int n, int m, int nu, nmf_prec_t prec) {
+  if (n < 1 || m < 1 || nu < 1 || nu > NMF_MAX_SKETCH || nu > n || nu > m) return 0;
+  return carve_dual(nullptr, n, m, nu, prec).bytes;
+}
+
+nmf_status_t nmf_project(nmf_stream_t stream, int n, int m, int nu, nmf_prec_t prec, const float* X, const float* L,
+                         const float* R, float* XL, float* XR, void* workspace, size_t workspace_bytes) {
+  if (n < 1 || m < 1 || nu < 1 || nu > NMF_MAX_SKETCH || nu > n || nu > m || !X || !L || !R || !XL || !XR)
+    return NMF_ERR_INVALID_ARG;
+  if (prec != NMF_PREC_FP32 && prec != NMF_PREC_BF16) return NMF_ERR_INVALID_ARG;
+  const DualWs w = carve_dual(workspace, n, m, nu, prec);
+  if (!ws_ok(workspace, workspace_bytes, w.bytes)) return NMF_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool bf16 = prec == NMF_PREC_BF16;
+  const size_t es = bf16 ? 2 : 4;
+  NMF_CU(cudaMemsetAsync(w.ctrl, 0, sizeof(Control), s));
+  NMF_CU(cudaMemsetAsync(w.opA, 0, (size_t)w.plan.NV * w.lda * es, s));
+  NMF_CU(cudaMemsetAsync(w.opB, 0, (size_t)w.plan.NV * w.ldb * es, s));
+  if (bf16) NMF_CU(xb_convert(w.plan, X, n, m, w.Xb, w.ldxb, w.ctrl, s));
+  // X_R = X R: R is the N-product operand (stored transposed); X_L^T = X^T L^T:
+  // the T-product operand is (L^T)^T = L itself, copied row by row
+  NMF_CU(transpose_launch(R, m, nu, w.opA, w.lda, bf16, w.ctrl, s));
+  NMF_CU(copy_rows_launch(L, nu, n, w.opB, w.ldb, bf16, w.ctrl, s));
+  XPassArgs xa{};
+  xa.n = n; xa.m = m;
+  xa.X = bf16 ? (const void*)w.Xb : (const void*)X;
+  xa.ldx = bf16 ? w.ldxb : m;
+  xa.opA = w.opA; xa.lda = w.lda; xa.opB = w.opB; xa.ldb = w.ldb;
+  xa.partN = w.partN; xa.partT = w.partT; xa.nu = nu;
+  xa.doN = true; xa.doT = true;
+  xa.ctrl = w.ctrl;
+  NMF_CU(xpass_launch(w.plan, xa, prec, s));
+  RowJob r[2] = {};
+  r[0].part = w.partN; r[0].S = w.plan.S_c; r[0].ldp = w.plan.NV; r[0].N = n; r[0].nu = nu; r[0].Y = XR;
+  r[1].part = w.partT; r[1].S = w.plan.S_r; r[1].ldp = w.plan.NV; r[1].N = m; r[1].nu = nu; r[1].Yt = XL;
+  NMF_CU(rows_launch(r, 2, w.ctrl, s));
+  return NMF_OK;
+}
+
 }  // extern "C"

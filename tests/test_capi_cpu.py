@@ -166,3 +166,12 @@ def test_f64_backward_argument_errors_are_host_side(L):
     pr.mode = pkg.PLAIN
     pr.X = 256
     assert L.nenmf_backward_f64(None, ctypes.byref(pr), ctypes.byref(pa), *args, None, v(256), big) == 7
+
+
+def test_project_argument_errors_are_host_side(L):
+    v = ctypes.c_void_p
+    assert L.nmf_project_workspace_size(100, 80, 8, 1) > 0
+    assert L.nmf_project_workspace_size(100, 80, 81, 1) == 0
+    assert L.nmf_project(None, 100, 80, 8, 0, v(256), None, v(256), v(256), v(256), v(256), 1 << 30) == 1
+    assert L.nmf_project(None, 100, 80, 8, 2, v(256), v(256), v(256), v(256), v(256), v(256), 1 << 30) == 1
+    assert L.nmf_project(None, 100, 80, 8, 0, v(256), v(256), v(256), v(256), v(256), v(100), 1 << 30) == 2
