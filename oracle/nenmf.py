@@ -17,7 +17,7 @@ The G-subproblem of eq. (2) is put in this form by transposition:
     min_{G >= 0} 1/2 ||X - G F||^2 = min_{G^T >= 0} 1/2 ||X^T - F^T G^T||^2,
 so  H = F F^T  and  B = F X^T, and the unknown is G^T.
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
   * step size 1/L_c with L_c = lambda_max(H), the Lipschitz constant of the
     gradient (Sec. 2 cites Guan et al. 2012, whose step this is);
   * the inner loop returns the projected iterate F_k, not Y_K (the text's

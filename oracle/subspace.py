@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 Shapes (Sec. 3): L is nu x n, R is m x nu, X_L = L X is nu x m, X_R = X R is
 n x nu, with p <= nu << min(n, m).
 
-Readings (listed in DESIGN.md):
+Readings of points the paper leaves open:
   * "orthonormal basis" / "QR decomposition" = the Q factor of the thin
     Householder QR with the signs fixed so that diag(R) > 0 (unique when the
     input has full column rank). A wide input (nu x m, orthonormal rows
