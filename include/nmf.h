@@ -345,6 +345,25 @@ nmf_status_t nenmf_solve_batched(nmf_stream_t stream, int count, const nenmf_pro
                                  const nenmf_batch_config_t* config, nenmf_stats_t* stats, void* workspace,
                                  size_t workspace_bytes);
 
+/*
+ * Measured choice of the cluster size (CTAs per problem) for
+ * nenmf_solve_batched: each candidate 1, 2, 4, 8 with a valid plan runs
+ * trial_outer outer iterations of these problems (params otherwise as
+ * given; record_* ignored) from scratch copies of G and F, once untimed and
+ * once timed with CUDA events; best->cluster receives the fastest.
+ * trial_ms (host, 4 floats, may be NULL) receives each candidate's time in
+ * ms (-1: not a valid plan). The caller's G and F are not modified.
+ * Synchronous: returns after the trials ran (it reads their times).
+ * Errors: as nenmf_solve_batched; NMF_ERR_INVALID_ARG if trial_outer < 1,
+ * count < 1 or best is NULL; the first device error of a trial.
+ */
+size_t nenmf_batch_autotune_workspace_size(int count, const nenmf_problem_t* problems,
+                                           const nenmf_params_t* params, int trial_outer);
+nmf_status_t nenmf_batch_autotune(nmf_stream_t stream, int count, const nenmf_problem_t* problems,
+                                  float* const* G, float* const* F, const nenmf_params_t* params, int trial_outer,
+                                  nenmf_batch_config_t* best, float* trial_ms, void* workspace,
+                                  size_t workspace_bytes);
+
 /* ------------------------------------------------------------------------ */
 /* Reverse-mode derivative of the compressed solve (Alg. 1, Sec. 2)          */
 /* ------------------------------------------------------------------------ */

@@ -92,6 +92,9 @@ def lib() -> ctypes.CDLL:
         "nmf_compress_batched": (i, [vp, i, vp, i, i, vp, sz]),
         "nenmf_solve_workspace_size": (sz, [ctypes.POINTER(Problem)]),
         "nmf_project_workspace_size": (sz, [i, i, i, i]),
+        "nenmf_batch_autotune_workspace_size": (sz, [i, vp, ctypes.POINTER(Params), i]),
+        "nenmf_batch_autotune": (i, [vp, i, vp, vp, vp, ctypes.POINTER(Params), i, ctypes.POINTER(BatchConfig),
+                                     ctypes.POINTER(ctypes.c_float), vp, sz]),
         "nmf_project": (i, [vp, i, i, i, i, vp, vp, vp, vp, vp, vp, sz]),
         "nmf_compress_f64_workspace_size": (sz, [i, i, i]),
         "nmf_compress_f64": (i, [vp, i, i, i, i, vp, vp, vp, u64, vp, vp, vp, vp, vp, sz]),
@@ -134,7 +137,8 @@ def exported_symbols():
             "nenmf_backward_workspace_size", "nenmf_backward", "nmf_compress_variant",
             "nmf_compress_batched_workspace_size", "nmf_compress_batched", "nmf_compress_f64_workspace_size",
             "nmf_compress_f64", "nenmf_solve_f64_workspace_size", "nenmf_solve_f64",
-            "nenmf_backward_f64_workspace_size", "nenmf_backward_f64", "nmf_project_workspace_size", "nmf_project"]
+            "nenmf_backward_f64_workspace_size", "nenmf_backward_f64", "nmf_project_workspace_size", "nmf_project",
+            "nenmf_batch_autotune_workspace_size", "nenmf_batch_autotune"]
 
 
 # ---------------------------------------------------------------------------
@@ -418,6 +422,28 @@ def backward(problem: Problem, G0, F0, record: SolveRecord, dG_T, dF_T, max_oute
                              _ptr(dG_T), _ptr(dF_T), _ptr(dXL), _ptr(dXR), _ptr(dG0), _ptr(dF0), _ptr(dX),
                              _ptr(ws), ws.numel()), "nenmf_backward")
     return dXL, dXR, dG0, dF0, dX
+
+
+def batch_autotune(problems, Gs, Fs, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
+                   tol_mode: int = TOL_REL, restart: bool = False, trial_outer: int = 2, ws=None):
+    """nenmf_batch_autotune: (fastest cluster size, {cluster: trial ms}) for these problems;
+    Gs, Fs are left unchanged. Synchronous."""
+    count = len(problems)
+    for pr, G, F in zip(problems, Gs, Fs):
+        _check_f32("G", G, (pr.n, pr.p))
+        _check_f32("F", F, (pr.p, pr.m))
+    arr, pa, _ = _batch_args(problems, max_outer, max_inner, min_inner, tol, tol_mode, 0, restart)
+    gp = (ctypes.c_void_p * count)(*[G.data_ptr() for G in Gs])
+    fp = (ctypes.c_void_p * count)(*[F.data_ptr() for F in Fs])
+    if ws is None:
+        ws = workspace(lib().nenmf_batch_autotune_workspace_size(count, ctypes.cast(arr, ctypes.c_void_p),
+                                                                 ctypes.byref(pa), trial_outer))
+    best = BatchConfig()
+    ms = (ctypes.c_float * 4)()
+    _ok(lib().nenmf_batch_autotune(_stream(), count, ctypes.cast(arr, ctypes.c_void_p), ctypes.cast(gp, ctypes.c_void_p),
+                                   ctypes.cast(fp, ctypes.c_void_p), ctypes.byref(pa), trial_outer, ctypes.byref(best),
+                                   ms, _ptr(ws), ws.numel()), "nenmf_batch_autotune")
+    return best.cluster, {c: float(ms[k]) for k, c in enumerate((1, 2, 4, 8)) if ms[k] >= 0.0}
 
 
 def read_batch_stats(stats, count: int):

@@ -843,3 +843,129 @@ extern "C" nmf_status_t nenmf_solve_batched(nmf_stream_t stream, int count, cons
   NMF_CU(cudaLaunchKernelExC(&cfg, fn, args));
   return NMF_OK;
 }
+
+// ---- measured choice of the cluster size -----------------------------------
+namespace {
+
+constexpr int kTuneCandidates[4] = {1, 2, 4, 8};
+
+// Scratch copies of every problem's G and F (each 256-byte aligned), then the
+// largest batched-solve workspace over the candidates.
+struct TuneWs {
+  std::vector<float*> G, F;
+  void* solve_ws;
+  size_t solve_bytes;
+  size_t bytes;
+};
+
+TuneWs carve_tune(void* base, int count, const nenmf_problem_t* pr, const nenmf_params_t& trial) {
+  TuneWs w{};
+  Carver cv(base);
+  w.G.resize(count);
+  w.F.resize(count);
+  for (int i = 0; i < count; ++i) {
+    w.G[i] = cv.take<float>((size_t)pr[i].n * pr[i].p);
+    w.F[i] = cv.take<float>((size_t)pr[i].p * pr[i].m);
+  }
+  size_t need = 0;
+  for (int c : kTuneCandidates) {
+    const nenmf_batch_config_t cfg{c};
+    need = std::max(need, nenmf_solve_batched_workspace_size(count, pr, &trial, &cfg));
+  }
+  w.solve_ws = cv.take<char>(need);
+  w.solve_bytes = need;
+  w.bytes = cv.size();
+  return w;
+}
+
+nenmf_params_t trial_params(const nenmf_params_t& pa, int trial_outer) {
+  nenmf_params_t t = pa;
+  t.max_outer = trial_outer;
+  t.record_G = nullptr;
+  t.record_F = nullptr;
+  t.record_time_ns = nullptr;
+  return t;
+}
+
+}  // namespace
+
+extern "C" size_t nenmf_batch_autotune_workspace_size(int count, const nenmf_problem_t* problems,
+                                                      const nenmf_params_t* params, int trial_outer) {
+  if (trial_outer < 1 || count < 1 || !params) return 0;
+  const nenmf_params_t t = trial_params(*params, trial_outer);
+  if (check_batch(count, problems, &t) != NMF_OK) return 0;
+  return carve_tune(nullptr, count, problems, t).bytes;
+}
+
+extern "C" nmf_status_t nenmf_batch_autotune(nmf_stream_t stream, int count, const nenmf_problem_t* problems,
+                                             float* const* G, float* const* F, const nenmf_params_t* params,
+                                             int trial_outer, nenmf_batch_config_t* best, float* trial_ms,
+                                             void* workspace, size_t workspace_bytes) {
+  if (trial_outer < 1 || count < 1 || !params || !best || !G || !F) return NMF_ERR_INVALID_ARG;
+  const nenmf_params_t t = trial_params(*params, trial_outer);
+  nmf_status_t st = check_batch(count, problems, &t);
+  if (st != NMF_OK) return st;
+  for (int i = 0; i < count; ++i)
+    if (!G[i] || !F[i]) return NMF_ERR_INVALID_ARG;
+  const TuneWs w = carve_tune(workspace, count, problems, t);
+  if (!workspace || workspace_bytes < w.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return NMF_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  NMF_CU(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return NMF_ERR_CUDA;
+  }
+  float best_ms = -1.f;
+  int best_c = 0;
+  st = NMF_OK;
+  for (int k = 0; k < 4 && st == NMF_OK; ++k) {
+    const int c = kTuneCandidates[k];
+    const nenmf_batch_config_t cfg{c};
+    if (trial_ms) trial_ms[k] = -1.f;
+    if (nenmf_solve_batched_workspace_size(count, problems, &t, &cfg) == 0) continue;  // not a valid plan
+    // one untimed run (first-use costs), then the timed one, each from the caller's factors
+    for (int rep = 0; rep < 2 && st == NMF_OK; ++rep) {
+      for (int i = 0; i < count && st == NMF_OK; ++i) {
+        if (cudaMemcpyAsync(w.G[i], G[i], sizeof(float) * (size_t)problems[i].n * problems[i].p,
+                            cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(w.F[i], F[i], sizeof(float) * (size_t)problems[i].p * problems[i].m,
+                            cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+          st = NMF_ERR_CUDA;
+      }
+      if (st != NMF_OK) break;
+      if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = NMF_ERR_CUDA;
+      if (st == NMF_OK)
+        st = nenmf_solve_batched(stream, count, problems, w.G.data(), w.F.data(), &t, &cfg, nullptr, w.solve_ws,
+                                 w.solve_bytes);
+      if (st == NMF_OK && rep == 1 && cudaEventRecord(e1, s) != cudaSuccess) st = NMF_ERR_CUDA;
+    }
+    if (st != NMF_OK) break;
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = NMF_ERR_CUDA;
+      break;
+    }
+    int dstatus = 0;
+    if (cudaMemcpy(&dstatus, w.solve_ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = NMF_ERR_CUDA;
+      break;
+    }
+    if (dstatus != 0) {
+      st = (nmf_status_t)dstatus;
+      break;
+    }
+    if (trial_ms) trial_ms[k] = ms;
+    if (best_ms < 0.f || ms < best_ms) {
+      best_ms = ms;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != NMF_OK) return st;
+  if (best_c == 0) return NMF_ERR_UNSUPPORTED;
+  best->cluster = best_c;
+  return NMF_OK;
+}

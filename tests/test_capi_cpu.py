@@ -175,3 +175,22 @@ def test_project_argument_errors_are_host_side(L):
     assert L.nmf_project(None, 100, 80, 8, 0, v(256), None, v(256), v(256), v(256), v(256), 1 << 30) == 1
     assert L.nmf_project(None, 100, 80, 8, 2, v(256), v(256), v(256), v(256), v(256), v(256), 1 << 30) == 1
     assert L.nmf_project(None, 100, 80, 8, 0, v(256), v(256), v(256), v(256), v(256), v(100), 1 << 30) == 2
+
+
+def test_autotune_argument_errors_are_host_side(L):
+    import paper_1812_04315_gb300 as pkg
+    v = ctypes.c_void_p
+    pr = pkg._problem(pkg.COMPRESSED, 100, 90, 4, 8, 0)
+    pr.L = pr.R = pr.XL = pr.XR = 256
+    arr = (pkg.Problem * 1)(pr)
+    pa = pkg.Params()
+    pa.max_outer, pa.max_inner, pa.min_inner, pa.tol = 10, 10, 1, 0.0
+    best = pkg.BatchConfig()
+    ptrs = (ctypes.c_void_p * 1)(256)
+    a = ctypes.cast(arr, ctypes.c_void_p)
+    p = ctypes.cast(ptrs, ctypes.c_void_p)
+    assert L.nenmf_batch_autotune_workspace_size(1, a, ctypes.byref(pa), 0) == 0
+    assert L.nenmf_batch_autotune(None, 1, a, p, p, ctypes.byref(pa), 0, ctypes.byref(best), None, v(256), 1 << 30) == 1
+    assert L.nenmf_batch_autotune(None, 1, a, p, p, ctypes.byref(pa), 2, None, None, v(256), 1 << 30) == 1
+    assert L.nenmf_batch_autotune(None, 0, a, p, p, ctypes.byref(pa), 2, ctypes.byref(best), None, v(256), 1 << 30) == 1
+    assert L.nenmf_batch_autotune(None, 1, a, p, p, ctypes.byref(pa), 2, ctypes.byref(best), None, v(100), 1 << 30) == 2

@@ -186,3 +186,24 @@ def test_full_size_batch(nmf):
     Go, Fo, _ = nenmf.nenmf_compressed(_np(L), _np(R), _np(XL), _np(XR), G0s[i], F0s[i], T, inner, tol=tol)
     Xd = _np(X)
     assert abs(metrics.rre(Xd, _np(Gs[i]), _np(Fs[i])) - metrics.rre(Xd, Go, Fo)) <= 1e-5
+
+
+def test_autotune_picks_a_measured_cluster_size(nmf, batch):
+    # the autotuner times every valid cluster size on copies of the factors:
+    # it returns the fastest of its own measurements and leaves G, F alone
+    probs, Gs, Fs = [], [], []
+    for b in batch:
+        probs.append(nmf.compressed_problem(_t(b["L"]), _t(b["R"]), _t(b["XL"]), _t(b["XR"]), b["p"]))
+        Gs.append(_t(b["G0"]))
+        Fs.append(_t(b["F0"]))
+    best, times = nmf.batch_autotune(probs, Gs, Fs, 20, 10, tol=1e-6, trial_outer=2)
+    assert best in (1, 2, 4, 8) and best in times
+    assert times[best] == min(times.values()) and all(t > 0.0 for t in times.values())
+    for b, G, F in zip(batch, Gs, Fs):
+        np.testing.assert_array_equal(_np(G), b["G0"].astype(np.float64))
+        np.testing.assert_array_equal(_np(F), b["F0"].astype(np.float64))
+    # the tuned size is an ordinary configuration: same result as asking for it
+    G1, F1, _ = _run(nmf, batch, 3, 10, cluster=best)
+    G2, F2, _ = _run(nmf, batch, 3, 10, cluster=best)
+    for a, c in zip(G1 + F1, G2 + F2):
+        assert bool((a == c).all())
