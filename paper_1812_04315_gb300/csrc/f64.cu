@@ -742,8 +742,7 @@ cudaError_t back_f_inputs(const nenmf_problem_f64_t& pr, const double* Gt, const
 
 // S = dH + dH^T of one inner solve: dH = -(1/L_c) sum_k dz_k Y_k^T + dL v v^T.
 cudaError_t back_sym_dh(int p, int N, int K, const double* tD, const double* tY, const double* lam, const double* v,
-                        const Back64Ws& w, double lam_host_unused, cudaStream_t s) {
-  (void)lam_host_unused;
+                        const Back64Ws& w, cudaStream_t s) {
   // dH = sum over (k, j) of dz (p x KN) times Y^T, scaled by -1/L_c on the device
   F64_CU(gemm64(p, p, K * N, tD, (long long)K * N, 1, tY, 1, (long long)K * N, w.dH, p, w.ctrl, s));
   count_launches(1);
@@ -931,7 +930,7 @@ nmf_status_t nenmf_backward_f64(nmf_stream_t stream, const nenmf_problem_f64_t* 
     nnls_adj_f64_kernel<<<1, kNnlsThreads, 0, s>>>(w.HF, w.dF, p, m, K, w.lamF, w.beta, w.tYf, w.tZf, w.tDf, w.dFo,
                                                     w.dBf, w.dL, c);
     NMF_CU(cudaGetLastError());
-    NMF_CU(back_sym_dh(p, m, K, w.tDf, w.tYf, w.lamF, w.vF, w, 0.0, s));
+    NMF_CU(back_sym_dh(p, m, K, w.tDf, w.tYf, w.lamF, w.vF, w, s));
     NMF_CU(gemm64(nu, p, p, w.GL, p, 1, w.S, p, 1, w.dGL, p, c, s));
     NMF_CU(gemm64_acc(nu, p, m, pr.XL, m, 1, w.dBf, 1, m, w.dGL, p, 1.0, c, s));
     NMF_CU(gemm64_acc(nu, m, p, w.GL, p, 1, w.dBf, m, 1, dXL, m, 1.0, c, s));
@@ -943,7 +942,7 @@ nmf_status_t nenmf_backward_f64(nmf_stream_t stream, const nenmf_problem_f64_t* 
     nnls_adj_f64_kernel<<<1, kNnlsThreads, 0, s>>>(w.HG, w.dGt, p, n, K, w.lamG, w.beta, w.tYg, w.tZg, w.tDg, w.dGo,
                                                     w.dBg, w.dL, c);
     NMF_CU(cudaGetLastError());
-    NMF_CU(back_sym_dh(p, n, K, w.tDg, w.tYg, w.lamG, w.vG, w, 0.0, s));
+    NMF_CU(back_sym_dh(p, n, K, w.tDg, w.tYg, w.lamG, w.vG, w, s));
     NMF_CU(gemm64(p, nu, p, w.S, p, 1, w.FR, nu, 1, w.dFR, nu, c, s));
     NMF_CU(gemm64_acc(p, nu, n, w.dBg, n, 1, pr.XR, nu, 1, w.dFR, nu, 1.0, c, s));
     NMF_CU(gemm64_acc(n, nu, p, w.dBg, 1, n, w.FR, nu, 1, dXR, nu, 1.0, c, s));
