@@ -234,3 +234,34 @@ def test_backward_f64_central_differences(nmf):
         assert an == pytest.approx(fd, rel=1e-6, abs=1e-8 * loss), (an, fd)
         checked += 1
     assert checked >= 8
+
+
+def test_full_sketch_reduces_to_plain_f64(nmf):
+    # nu = n = m: L and R are square orthogonal, so G_L^T G_L = G^T G,
+    # G_L^T X_L = G^T X (and likewise for F): the compressed trajectory is the
+    # plain one up to float64 rounding
+    n = m = 64
+    p, T, K = 3, 6, 10
+    X, _, _ = synth.lowrank_data(n, m, p, seed=8, snr_db=30.0)
+    OmL, OmR = synth.gaussian_sketches(n, m, n, seed=9)
+    L, R, XL, XR = nmf.compress_f64(_t(X), n, 0, omega_L=_t(OmL), omega_R=_t(OmR))
+    np.testing.assert_allclose(_np(L) @ _np(L).T, np.eye(n), atol=1e-12)
+    np.testing.assert_allclose(_np(R).T @ _np(R), np.eye(n), atol=1e-12)
+    G0, F0 = synth.initial_factors(n, m, p, seed=10)
+    Gc, Fc = _t(G0), _t(F0)
+    nmf.solve_f64(nmf.compressed_problem_f64(L, R, XL, XR, p), Gc, Fc, T, K)
+    Gp, Fp = _t(G0), _t(F0)
+    nmf.solve_f64(nmf.plain_problem_f64(_t(X), p), Gp, Fp, T, K)
+    assert _rel(_np(Gc), _np(Gp)) <= 1e-10 and _rel(_np(Fc), _np(Fp)) <= 1e-10
+
+
+@pytest.mark.parametrize("n,m,p,nu", [(33, 17, 1, 1), (80, 90, 32, 40), (70, 50, 2, 50)])
+def test_solve_f64_rank_limits(nmf, n, m, p, nu):
+    X, pr, comp = _problem(nmf, "compressed", n, m, p, nu, 1, seed=n)
+    G0, F0 = synth.initial_factors(n, m, p, seed=m)
+    G, F = _t(G0), _t(F0)
+    st = nmf.read_stats(nmf.solve_f64(pr, G, F, 5, 8, tol=1e-4))
+    Go, Fo, info = _oracle("compressed", X, comp, G0, F0, 5, 8, tol=1e-4)
+    assert st.status == 0
+    assert list(st.total_inner) == [sum(k for k, _ in info["inner"]), sum(k for _, k in info["inner"])]
+    assert _rel(_np(G), Go) <= 1e-8 and _rel(_np(F), Fo) <= 1e-8
