@@ -319,44 +319,72 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
   bool extra_gram = false;
   if (J.part) {
     // Y = sum over the S partials: four accumulators (partial k feeds
-    // accumulator k mod 4, in increasing k), float4 over four columns, up to
-    // 16 partials' loads in flight per thread. Rows of a partial are ldp
-    // floats, ldp a multiple of 16, so the float4 loads are aligned.
+    // accumulator k mod 4, in increasing k), float4 over four columns. A
+    // thread takes two (row, column block) items at a time with up to 8
+    // partials of each in flight (16 loads). Rows of a partial are ldp floats,
+    // ldp a multiple of 16, so the float4 loads are aligned.
     const int nu4 = (nu + 3) >> 2;
     const size_t stride4 = (size_t)J.N * J.ldp / 4;
     const int S4 = J.S & ~3;
-    for (int i = tid; i < rows * nu4; i += kRowThreads) {
-      const int r = i / nu4, c4 = i % nu4;
-      const float4* pp = reinterpret_cast<const float4*>(J.part + (size_t)(r0 + r) * J.ldp) + c4;
-      float4 acc[4];
+    const int items = rows * nu4;
+    for (int i0 = tid; i0 < items; i0 += 2 * kRowThreads) {
+      const int ib = i0 + kRowThreads;
+      const bool two = ib < items;
+      const int ia_r = i0 / nu4, ia_c = i0 % nu4;
+      const int ib_r = two ? ib / nu4 : ia_r, ib_c = two ? ib % nu4 : ia_c;
+      const float4* pa = reinterpret_cast<const float4*>(J.part + (size_t)(r0 + ia_r) * J.ldp) + ia_c;
+      const float4* pb = reinterpret_cast<const float4*>(J.part + (size_t)(r0 + ib_r) * J.ldp) + ib_c;
+      float4 acc[2][4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int k0 = 0; k0 < S4; k0 += 16) {
-        float4 v[16];
+      for (int u = 0; u < 4; ++u) acc[0][u] = acc[1][u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k0 = 0; k0 < S4; k0 += 8) {
+        float4 va[8], vb[8];
 #pragma unroll
-        for (int u = 0; u < 16; ++u)
-          if (k0 + u < S4) v[u] = __ldcg(pp + (k0 + u) * stride4);
-#pragma unroll
-        for (int u = 0; u < 16; ++u)
+        for (int u = 0; u < 8; ++u)
           if (k0 + u < S4) {
-            acc[u & 3].x += v[u].x;
-            acc[u & 3].y += v[u].y;
-            acc[u & 3].z += v[u].z;
-            acc[u & 3].w += v[u].w;
+            va[u] = __ldcg(pa + (k0 + u) * stride4);
+            if (two) vb[u] = __ldcg(pb + (k0 + u) * stride4);
+          }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (k0 + u < S4) {
+            acc[0][u & 3].x += va[u].x;
+            acc[0][u & 3].y += va[u].y;
+            acc[0][u & 3].z += va[u].z;
+            acc[0][u & 3].w += va[u].w;
+            if (two) {
+              acc[1][u & 3].x += vb[u].x;
+              acc[1][u & 3].y += vb[u].y;
+              acc[1][u & 3].z += vb[u].z;
+              acc[1][u & 3].w += vb[u].w;
+            }
           }
       }
       for (int k = S4; k < J.S; ++k) {
-        const float4 v = __ldcg(pp + k * stride4);
-        acc[0].x += v.x;
-        acc[0].y += v.y;
-        acc[0].z += v.z;
-        acc[0].w += v.w;
+        const float4 v = __ldcg(pa + k * stride4);
+        acc[0][0].x += v.x;
+        acc[0][0].y += v.y;
+        acc[0][0].z += v.z;
+        acc[0][0].w += v.w;
+        if (two) {
+          const float4 w = __ldcg(pb + k * stride4);
+          acc[1][0].x += w.x;
+          acc[1][0].y += w.y;
+          acc[1][0].z += w.z;
+          acc[1][0].w += w.w;
+        }
       }
-      const float o[4] = {(acc[0].x + acc[1].x) + (acc[2].x + acc[3].x), (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y),
-                          (acc[0].z + acc[1].z) + (acc[2].z + acc[3].z), (acc[0].w + acc[1].w) + (acc[2].w + acc[3].w)};
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (4 * c4 + t < nu) Ys[r * kYsStride + 4 * c4 + t] = o[t];
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !two) break;
+        const int r = h ? ib_r : ia_r, c4 = h ? ib_c : ia_c;
+        const float4* A = acc[h];
+        const float o[4] = {(A[0].x + A[1].x) + (A[2].x + A[3].x), (A[0].y + A[1].y) + (A[2].y + A[3].y),
+                            (A[0].z + A[1].z) + (A[2].z + A[3].z), (A[0].w + A[1].w) + (A[2].w + A[3].w)};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (4 * c4 + t < nu) Ys[r * kYsStride + 4 * c4 + t] = o[t];
+      }
     }
   } else {
     const int sh = factor_gram(J.gram_in, J.gram_parts, nu, Ys, Ahi, Alo, Ihi, Ilo, ctrl, J.diag_only != 0);
