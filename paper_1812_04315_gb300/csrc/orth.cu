@@ -399,9 +399,31 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
       __syncthreads();
       if (cta == 0 && tid == 0 && shifted_s && !before) *J.shift_flag = 1;
     }
-    for (int i = tid; i < rows * nu; i += kRowThreads) {
-      const int r = i / nu, c = i % nu;
-      Ys[r * kYsStride + c] = J.src[(size_t)(r0 + r) * nu + c];
+    // this CTA's rows of src: one contiguous block of rows * nu floats, read
+    // as float4 with up to 8 loads in flight per thread when the block is
+    // 16-byte aligned (it starts kOrthRows * nu floats after its
+    // predecessor; src itself may be a caller's buffer), else as floats
+    {
+      const float* blk = J.src + (size_t)r0 * nu;
+      const int total = rows * nu;
+      const int n4 = (reinterpret_cast<uintptr_t>(blk) & 15u) == 0 ? total >> 2 : 0;
+      const float4* b4 = reinterpret_cast<const float4*>(blk);
+      for (int i0 = tid; i0 < n4; i0 += 8 * kRowThreads) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (i0 + u * kRowThreads < n4) v[u] = __ldcg(b4 + i0 + u * kRowThreads);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = 4 * (i0 + u * kRowThreads);
+          if (i0 + u * kRowThreads < n4) {
+            const float e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) Ys[((i + t) / nu) * kYsStride + (i + t) % nu] = e[t];
+          }
+        }
+      }
+      for (int i = 4 * n4 + tid; i < total; i += kRowThreads) Ys[(i / nu) * kYsStride + i % nu] = blk[i];
     }
     __syncthreads();
     // q = y R^{-1}: q_c = sum_{k<=c} y_k (R^{-1})_kc, a compensated dot
