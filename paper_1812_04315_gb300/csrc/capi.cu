@@ -82,6 +82,10 @@ cudaError_t xb_convert(const XPassPlan& plan, const float* X, int n, int m, __nv
 
 namespace {
 
+// The second CholeskyQR pass is skipped when the first pass's basis has a
+// Gram matrix within this of I (every entry, float-float value).
+constexpr float kSecondPassSkip = 1e-6f;
+
 // ----------------------------------------------------------------------------
 // nmf_compress workspace
 // ----------------------------------------------------------------------------
@@ -177,6 +181,10 @@ nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16
     c.Y = Q; c.op = isN ? w.opB : w.opA; c.ldop = isN ? w.ldb : w.lda; c.op_bf16 = bf16;
     if (isN) c.Yt = Lout;
     c.gram_part = g0; c.gram_on_shift = 1; c.shift_flag = flag;
+    // the first pass's float-float Gram and factor leave Q1 orthonormal to
+    // about float32 rounding unless Y is ill conditioned: then the second
+    // pass would change Q1 by as little, and is skipped
+    c.skip_tol = kSecondPassSkip;
     // apply 3, in place, only where a shift was taken
     RowJob& d = r4[k];
     d = c;

@@ -110,6 +110,7 @@ struct RowJob {
   int* shift_flag;      // apply step: raised (by CTA 0) when the factorisation needed the shift
   const int* run_flag;  // optional: skip the job unless *run_flag != 0
   int diag_only;        // apply step: R = diag(sqrt(S_cc)) (columns rescaled to unit norm, span kept)
+  float skip_tol;       // apply step: keep src as it is when its Gram is within this of I (0: never)
 };
 
 cudaError_t rows_launch(const RowJob* jobs, int njobs, Control* ctrl, cudaStream_t s);

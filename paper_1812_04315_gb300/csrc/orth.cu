@@ -90,10 +90,11 @@ __device__ __forceinline__ void tri_index(int e, int nu, int& a, int& b) {
 
 // Sum of the Gram partials (fixed order), float-float Cholesky S = R^T R and
 // the float-float inverse R^{-1}, redundantly in every CTA. Leaves R^{-1}
-// (upper, stride kAs) in (Ihi, Ilo). Returns 0 (ok), 1 (ok, shifted) or -1
-// (failure: status set).
+// (upper, stride kAs) in (Ihi, Ilo). Returns 0 (ok), 1 (ok, shifted), 2 (S
+// within skip_tol of I: R = I, nothing left in Ihi, Ilo) or -1 (failure:
+// status set).
 __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, float* Ahi, float* Alo, float* Ihi,
-                           float* Ilo, Control* ctrl, bool diag_only) {
+                           float* Ilo, Control* ctrl, bool diag_only, float skip_tol) {
   __shared__ float maxdiag_s, trace_s;
   __shared__ float Sdiag[NMF_MAX_SKETCH], Sdiag_lo[NMF_MAX_SKETCH];
   __shared__ float Dinv_hi[NMF_MAX_SKETCH], Dinv_lo[NMF_MAX_SKETCH];
@@ -140,6 +141,22 @@ __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, 
       Alo[a * kAs + b] = s.lo;
     }
     __syncthreads();
+  }
+  // A basis already orthonormal to skip_tol (every entry of S - I within it,
+  // the float-float value): nothing to factorise, the caller keeps its rows.
+  // Every CTA sums the same partials in the same order, so all decide alike.
+  if (skip_tol > 0.f) {
+    __shared__ int off_s;
+    if (tid == 0) off_s = 0;
+    __syncthreads();
+    for (int e = tid; e < E; e += blockDim.x) {
+      int a, b;
+      tri_index(e, nu, a, b);
+      const float v = (Ahi[a * kAs + b] - (a == b ? 1.f : 0.f)) + Alo[a * kAs + b];
+      if (!(fabsf(v) <= skip_tol)) off_s = 1;
+    }
+    __syncthreads();
+    if (!off_s) return 2;
   }
   // S kept in the upper triangle; the diagonal bounds the pivots
   if (tid == 0) {
@@ -387,9 +404,13 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
       }
     }
   } else {
-    const int sh = factor_gram(J.gram_in, J.gram_parts, nu, Ys, Ahi, Alo, Ihi, Ilo, ctrl, J.diag_only != 0);
+    // the skip is only taken while no factorisation of this basis has shifted
+    const int shifted_before = J.shift_flag ? *((volatile const int*)J.shift_flag) : 0;
+    const int sh = factor_gram(J.gram_in, J.gram_parts, nu, Ys, Ahi, Alo, Ihi, Ilo, ctrl, J.diag_only != 0,
+                               shifted_before ? 0.f : J.skip_tol);
     if (sh < 0) return;
-    if (tid == 0) shifted_s = sh;
+    const bool keep_rows = sh == 2;
+    if (tid == 0) shifted_s = keep_rows ? 0 : sh;
     __syncthreads();
     if (J.shift_flag) {
       // pass 1 records its shift; later passes add theirs; a shift anywhere
@@ -433,7 +454,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
     // correction added once at the end, so q_c is as accurate as if summed in
     // twice the precision, then rounded. Columns from the last to the first,
     // so the row is overwritten in place.
-    if (tid < rows) {
+    if (tid < rows && !keep_rows) {
       float* y = Ys + tid * kYsStride;
       for (int c = nu - 1; c >= 0; --c) {
         float sum = 0.f, corr = 0.f;
