@@ -130,20 +130,35 @@ def _threshold(tol: float, tol_mode: str, initial_pg: float) -> float | None:
     raise ValueError("tol_mode must be 'rel' or 'abs'")
 
 
-def initial_pg_plain(X, G, F) -> float:
-    """||[P grad_G ; P grad_F]||_F of 1/2||X - GF||^2 at (G, F)."""
+def initial_pg_parts_plain(X, G, F):
+    """(P grad_G, P grad_F) of 1/2||X - GF||^2 at (G, F): n x p and p x m."""
     gG = G @ (F @ F.T) - X @ F.T
     gF = (G.T @ G) @ F - G.T @ X
-    return float(np.sqrt(np.sum(projected_gradient(G, gG) ** 2) + np.sum(projected_gradient(F, gF) ** 2)))
+    return projected_gradient(G, gG), projected_gradient(F, gF)
 
 
-def initial_pg_compressed(L, R, XL, XR, G, F) -> float:
-    """Same norm for the compressed objectives of Alg. 1 at (G, F)."""
+def initial_pg_parts_compressed(L, R, XL, XR, G, F):
+    """(P grad_G, P grad_F) of the two compressed objectives of Alg. 1 at (G, F):
+    1/2||X_R - G F R||^2 in G and 1/2||X_L - L G F||^2 in F."""
     FR = F @ R
     gG = G @ (FR @ FR.T) - XR @ FR.T
     GL = L @ G
     gF = (GL.T @ GL) @ F - GL.T @ XL
-    return float(np.sqrt(np.sum(projected_gradient(G, gG) ** 2) + np.sum(projected_gradient(F, gF) ** 2)))
+    return projected_gradient(G, gG), projected_gradient(F, gF)
+
+
+def _joint_norm(parts) -> float:
+    return float(np.sqrt(sum(np.sum(a * a) for a in parts)))
+
+
+def initial_pg_plain(X, G, F) -> float:
+    """||[P grad_G ; P grad_F]||_F of 1/2||X - GF||^2 at (G, F)."""
+    return _joint_norm(initial_pg_parts_plain(X, G, F))
+
+
+def initial_pg_compressed(L, R, XL, XR, G, F) -> float:
+    """Same norm for the compressed objectives of Alg. 1 at (G, F)."""
+    return _joint_norm(initial_pg_parts_compressed(L, R, XL, XR, G, F))
 
 
 def nenmf_plain(X, G0, F0, max_outer: int, max_inner: int, min_inner: int = 1,
