@@ -247,6 +247,27 @@ def make_inputs(rank: int = 0):
     return X, G0.astype(np.float32), F0.astype(np.float32)
 
 
+def check_device_status(nmf, stats_rows, comp_status=None, outer=None, what="timed region"):
+    """Raises unless every step's solve stats (and compression status word, if
+    given) report success: a failed call turns the rest of its kernels into
+    no-ops and would otherwise time as a faster step."""
+    for k, row in enumerate(stats_rows):
+        st = nmf.read_stats(row)
+        if st.status != 0 or (outer is not None and st.outer_done != outer):
+            raise RuntimeError(f"{what}: step {k}: device status {st.status}, outer iterations {st.outer_done}")
+    if comp_status is not None:
+        bad = [int(v) for v in comp_status.cpu().tolist() if int(v) != 0]
+        if bad:
+            raise RuntimeError(f"{what}: compression status {bad}")
+
+
+def check_same(ref, got, what):
+    """Bitwise equality of the final factors with the warm-up run (every call is deterministic)."""
+    for a, b in zip(ref, got):
+        if not bool((a == b).all()):
+            raise RuntimeError(f"{what}: final factors differ from the warm-up run")
+
+
 def solve_kernel_bytes(n, m, p, nu):
     """Algorithmic bytes of one fused inner-solve launch (mean of the G and F sides).
 
@@ -313,19 +334,31 @@ def run_batched(args):
     tune = {"cluster": 0}  # 0: the planner's choice until the autotuner has measured
     ws_s = nmf.workspace(nmf.batch_workspace_size(probs, T, K_in, tol=tol))
     stats = torch.zeros(len(probs) * 256, dtype=torch.uint8, device=dev)
+    stats_rows = torch.zeros((max(args.steps, 1), len(probs) * 256), dtype=torch.uint8, device=dev)
+    comp_status = torch.zeros(max(args.steps, 1), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(ev=None):
+    def step(ev=None, k=None):
         if ev is not None:
             ev[0].record(stream)
         nmf.compress_batched(Xs, nus, b["q"], prec=prec, seeds=seeds, outs=outs, ws=ws_c)
+        if k is not None:
+            comp_status[k:k + 1].copy_(ws_c[:4].view(torch.int32))
         if ev is not None:
             ev[1].record(stream)
         torch._foreach_copy_(Gs, G0s)
         torch._foreach_copy_(Fs, F0s)
-        nmf.solve_batched(probs, Gs, Fs, T, K_in, tol=tol, stats=stats, ws=ws_s, cluster=tune["cluster"])
+        nmf.solve_batched(probs, Gs, Fs, T, K_in, tol=tol, stats=stats if k is None else stats_rows[k], ws=ws_s,
+                          cluster=tune["cluster"])
         if ev is not None:
             ev[2].record(stream)
+
+    def check_batch(rows, what):
+        for k, row in enumerate(rows):
+            for i, st in enumerate(nmf.read_batch_stats(row, len(probs))):
+                if st.status != 0 or st.outer_done != T:
+                    raise RuntimeError(f"{what}: step {k}, problem {i}: device status {st.status}, "
+                                       f"outer iterations {st.outer_done}")
 
     for _ in range(args.warmup):
         step()
@@ -339,9 +372,8 @@ def run_batched(args):
     ws_s = nmf.workspace(nmf.batch_workspace_size(probs, T, K_in, tol=tol, cluster=tuned))
     step()
     torch.cuda.synchronize()
-    for st in nmf.read_batch_stats(stats, len(probs)):
-        if st.status != 0:
-            raise RuntimeError(f"device status {st.status} in the warm-up")
+    check_batch([stats], "warm-up")
+    ref_GF = ([g.clone() for g in Gs], [f.clone() for f in Fs])
     sampler = clock_sampler(local_rank)
     time.sleep(0.3)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
@@ -350,7 +382,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     t0 = datetime.datetime.now()
     for k in range(args.steps):
-        step(evs[k])
+        step(evs[k], k)
     torch.cuda.synchronize()
     t1 = datetime.datetime.now()
     barrier(dist, local_rank)
@@ -358,6 +390,10 @@ def run_batched(args):
     sampler.mark(t0, t1)
     time.sleep(0.2)
     clocks = sampler.stop()
+    check_batch(stats_rows[:args.steps], "eager timed steps")
+    if any(int(v) != 0 for v in comp_status[:args.steps].cpu().tolist()):
+        raise RuntimeError("eager timed steps: compression status")
+    check_same(ref_GF[0] + ref_GF[1], Gs + Fs, "eager timed steps")
     ms_compress = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     ms_solve = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
     ms_eager = statistics.mean(e[0].elapsed_time(e[2]) for e in evs)
@@ -376,6 +412,9 @@ def run_batched(args):
         graph.replay()
     g1.record(stream)
     torch.cuda.synchronize()
+    # the captured step wrote `stats` and the factors on its last replay
+    check_batch([stats], "graph replays")
+    check_same(ref_GF[0] + ref_GF[1], Gs + Fs, "graph replays")
     ms_step = max_over_ranks(dist, g0.elapsed_time(g1) / args.steps, dev)
     units = len(probs) * T
     peaks = {}
@@ -430,26 +469,30 @@ def run_ours(args):
     prob = nmf.compressed_problem(*out, p)
     ws_s = nmf.workspace(nmf.solve_workspace_size(prob))
     stats = torch.zeros(256, dtype=torch.uint8, device=dev)
+    # one stats block and one compression status word per timed step
+    stats_rows = torch.zeros((max(args.steps, 1), 256), dtype=torch.uint8, device=dev)
+    comp_status = torch.zeros(max(args.steps, 1), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(ev=None):
+    def step(ev=None, k=None, prec=prec, ws_c=ws_c):
         if ev is not None:
             ev[0].record(stream)
         nmf.compress(Xg, nu, q, prec=prec, seed=w["sketch_seed"], ws=ws_c, out=out)
+        if k is not None:
+            comp_status[k:k + 1].copy_(ws_c[:4].view(torch.int32))
         if ev is not None:
             ev[1].record(stream)
         G.copy_(G0g)
         F.copy_(F0g)
-        nmf.solve(prob, G, F, T, K_in, tol=tol, stats=stats, ws=ws_s)
+        nmf.solve(prob, G, F, T, K_in, tol=tol, stats=stats if k is None else stats_rows[k], ws=ws_s)
         if ev is not None:
             ev[2].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    st = nmf.read_stats(stats)
-    if st.status != 0:
-        raise RuntimeError(f"device status {st.status} in the warm-up")
+    check_device_status(nmf, [stats], outer=T, what="warm-up")
+    ref_GF = (G.clone(), F.clone())
 
     sampler = clock_sampler(local_rank)
     time.sleep(0.3)
@@ -461,7 +504,7 @@ def run_ours(args):
     t0 = datetime.datetime.now()
     e_start.record(stream)
     for k in range(args.steps):
-        step(evs[k])
+        step(evs[k], k)
     e_end.record(stream)
     torch.cuda.synchronize()
     t1 = datetime.datetime.now()
@@ -470,11 +513,31 @@ def run_ours(args):
     sampler.mark(t0, t1)
     time.sleep(0.2)
     clocks = sampler.stop()
+    check_device_status(nmf, stats_rows[:args.steps], comp_status[:args.steps], outer=T)
+    check_same(ref_GF, (G, F), "timed region")
     ms_total = e_start.elapsed_time(e_end)
     ms_step = max_over_ranks(dist, ms_total / args.steps, dev)
     ms_compress = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     ms_solve = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
     value = aggregate_value(T, world, ms_step / 1e3)
+
+    # ---- the float32 arm of the same workload: X products on CUDA cores in float32 ----
+    ws_c32 = nmf.workspace(nmf.compress_workspace_size(n, m, nu, nmf.PREC_FP32))
+    fp32_steps = max(1, min(args.steps, 5))
+    for _ in range(2):
+        step(prec=nmf.PREC_FP32, ws_c=ws_c32)
+    torch.cuda.synchronize()
+    evs32 = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(fp32_steps)]
+    for k in range(fp32_steps):
+        step(evs32[k], k, prec=nmf.PREC_FP32, ws_c=ws_c32)
+    torch.cuda.synchronize()
+    check_device_status(nmf, stats_rows[:fp32_steps], comp_status[:fp32_steps], outer=T, what="float32 arm")
+    ms32 = max_over_ranks(dist, statistics.mean(e[0].elapsed_time(e[2]) for e in evs32), dev)
+    fp32_arm = {"value": round(aggregate_value(T, world, ms32 / 1e3), 3), "unit": UNIT, "dtype": "f32",
+                "steps": fp32_steps, "ms_per_step": round(ms32, 4),
+                "breakdown_ms": {"compress": round(statistics.mean(e[0].elapsed_time(e[1]) for e in evs32), 4),
+                                 "solve": round(statistics.mean(e[1].elapsed_time(e[2]) for e in evs32), 4)},
+                "config": "same workload; the 2q+2 passes over X in float32 (NMF_PREC_FP32)"}
 
     # ---- end to end: host buffers, copies inside the timed region ----
     Xh = torch.from_numpy(X).pin_memory()
@@ -507,8 +570,9 @@ def run_ours(args):
             G.copy_(G0h, non_blocking=True)
             F.copy_(F0h, non_blocking=True)
             nmf.compress(Xbufs[j], nu, q, prec=prec, seed=w["sketch_seed"], ws=ws_c, out=out)
+            comp_status[k:k + 1].copy_(ws_c[:4].view(torch.int32))
             freed[j].record(stream)
-            nmf.solve(prob, G, F, T, K_in, tol=tol, stats=stats, ws=ws_s)
+            nmf.solve(prob, G, F, T, K_in, tol=tol, stats=stats_rows[k], ws=ws_s)
             Gh.copy_(G, non_blocking=True)
             Fh.copy_(F, non_blocking=True)
 
@@ -522,6 +586,8 @@ def run_ours(args):
     e2e_run(args.steps, a)
     b.record(stream)
     torch.cuda.synchronize()
+    check_device_status(nmf, stats_rows[:args.steps], comp_status[:args.steps], outer=T, what="e2e")
+    check_same((ref_GF[0].cpu(), ref_GF[1].cpu()), (Gh, Fh), "e2e")
     ms_e2e = max_over_ranks(dist, a.elapsed_time(b) / args.steps, dev)
     barrier(dist, local_rank)
     h2d = X.nbytes + G0.nbytes + F0.nbytes
@@ -557,12 +623,19 @@ def run_ours(args):
               "clocks": clocks, "gpu_launches": launches,
               "e2e": {"value": round(aggregate_value(T, world, ms_e2e / 1e3), 3), "unit": UNIT,
                       "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-              "roofline": roofline}
+              "roofline": roofline, "fp32_arm": fp32_arm}
 
+    curves = None
     if not args.no_rre and rank == 0:
-        result["time_to_rre"] = time_to_rre(nmf, Xg, G0g, F0g, dev)
+        curves = rre_curves(nmf, Xg, G0g, F0g, dev)
+        result["time_to_rre"] = time_to_rre(curves)
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        result["cpu_baseline"] = cpu_baseline(X, G0, F0)
+        result["cpu_baseline"], oracle_rre = cpu_baseline(X, G0, F0)
+        if curves is not None:
+            # SURVEY-defined threshold: (1 + 1e-3) x the oracle's final compressed RRE
+            result["time_to_rre_oracle_tau"] = time_to_rre(curves, tau=(1 + 1e-3) * oracle_rre,
+                                                           tau_rule="(1 + 1e-3) * final RRE of the float64 oracle's "
+                                                                    "compressed run on the same workload")
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist is not None:
@@ -585,8 +658,9 @@ def profile_traffic(kernel: str):
     return rec["dram_bytes_per_launch"] if digest == rec.get("source_sha256_16") else None
 
 
-def time_to_rre(nmf, Xg, G0g, F0g, dev):
-    """RRE-versus-time curves of compressed and plain NeNMF (bf16 X products) on the GPU."""
+def rre_curves(nmf, Xg, G0g, F0g, dev):
+    """RRE-versus-device-time curves of compressed and plain NeNMF (bf16 X products) on the GPU,
+    with the inner iterations each run made."""
     import torch
     w = WORKLOAD
     n, m, p, nu, q, T, K_in, tol = w["n"], w["m"], w["p"], w["nu"], w["q"], w["max_outer"], w["max_inner"], w["tol"]
@@ -605,35 +679,48 @@ def time_to_rre(nmf, Xg, G0g, F0g, dev):
     L, R, XL, XR = nmf.compress(Xg, nu, q, prec=nmf.PREC_BF16, seed=w["sketch_seed"])
     b.record(stream)
     G, F = G0g.clone(), F0g.clone()
-    nmf.solve(nmf.compressed_problem(L, R, XL, XR, p), G, F, T, K_in, tol=tol, record=rec)
+    st = nmf.solve(nmf.compressed_problem(L, R, XL, XR, p), G, F, T, K_in, tol=tol, record=rec)
     torch.cuda.synchronize()
+    check_device_status(nmf, [st], outer=T, what="time to RRE, compressed")
+    inner_c = sum(nmf.read_stats(st).total_inner)
     t_comp = a.elapsed_time(b) / 1e3
     ts = rec.times.cpu().numpy().astype(np.float64)
     t_c = t_comp + (ts[1:] - ts[0]) / 1e9
     r_c = rre_curve()
     # plain, same precision policy for the X products
     G, F = G0g.clone(), F0g.clone()
-    nmf.solve(nmf.plain_problem(Xg, p, nmf.PREC_BF16), G, F, T, K_in, tol=tol, record=rec)
+    st = nmf.solve(nmf.plain_problem(Xg, p, nmf.PREC_BF16), G, F, T, K_in, tol=tol, record=rec)
     torch.cuda.synchronize()
+    check_device_status(nmf, [st], outer=T, what="time to RRE, plain")
+    inner_p = sum(nmf.read_stats(st).total_inner)
     ts = rec.times.cpu().numpy().astype(np.float64)
     t_p = (ts[1:] - ts[0]) / 1e9
     r_p = rre_curve()
-    tau = (1 + 1e-3) * max(r_c[-1], r_p[-1])
+    return {"t_c": t_c, "r_c": r_c, "t_comp": t_comp, "inner_c": inner_c, "t_p": t_p, "r_p": r_p,
+            "inner_p": inner_p}
+
+
+def time_to_rre(c, tau=None, tau_rule=None):
+    """Device seconds to the first outer iteration with RRE <= tau for both runs."""
+    T = WORKLOAD["max_outer"]
+    if tau is None:
+        tau = (1 + 1e-3) * max(c["r_c"][-1], c["r_p"][-1])
+        tau_rule = "(1 + 1e-3) * max(final RRE of the two GPU runs)"
 
     def first(t, r):
         idx = np.nonzero(r <= tau)[0]
         return (float(t[idx[0]]), int(idx[0]) + 1) if idx.size else (None, None)
 
-    tc, kc = first(t_c, r_c)
-    tp, kp = first(t_p, r_p)
-    return {"tau": tau, "rre_final": {"compressed": float(r_c[-1]), "plain": float(r_p[-1])},
-            "compressed": {"seconds": tc, "outer_iters": kc, "compress_s": t_comp,
-                           "outer_iters_per_s": T / t_c[-1]},
-            "plain": {"seconds": tp, "outer_iters": kp, "outer_iters_per_s": T / t_p[-1]},
+    tc, kc = first(c["t_c"], c["r_c"])
+    tp, kp = first(c["t_p"], c["r_p"])
+    return {"tau": tau, "rre_final": {"compressed": float(c["r_c"][-1]), "plain": float(c["r_p"][-1])},
+            "compressed": {"seconds": tc, "outer_iters": kc, "compress_s": c["t_comp"],
+                           "outer_iters_per_s": T / c["t_c"][-1], "inner_iters_total": c["inner_c"]},
+            "plain": {"seconds": tp, "outer_iters": kp, "outer_iters_per_s": T / c["t_p"][-1],
+                      "inner_iters_total": c["inner_p"]},
             "speedup": (tp / tc) if (tc and tp) else None,
-            "definition": "tau = (1 + 1e-3) * max(final RRE of the two runs); time from the start of the "
-                          "compression (compressed) or of the solve (plain) to the first outer iteration "
-                          "with RRE <= tau; device time"}
+            "definition": f"tau = {tau_rule}; time from the start of the compression (compressed) or of the "
+                          "solve (plain) to the first outer iteration with RRE <= tau; device time"}
 
 
 PAPER = dict(sizes=(500, 5000, 10000), draws=3, p=15, nu=25, q=4, snr_db=30.0, max_outer=60, max_inner=500,
@@ -665,13 +752,14 @@ def run_paper(args):
 
             def curve(prob, t0=0.0):
                 G, F = G0g.clone(), F0g.clone()
-                nmf.solve(prob, G, F, T, K, tol=tol, record=rec)
+                st = nmf.solve(prob, G, F, T, K, tol=tol, record=rec)
                 torch.cuda.synchronize()
+                check_device_status(nmf, [st], outer=T, what="paper setting")
                 ts = rec.times.cpu().numpy().astype(np.float64)
                 terms = [nmf.rre_terms(Xg, rec.G[t], rec.F[t]) for t in range(T)]
                 torch.cuda.synchronize()
                 r = np.array([float((x[0] / x[1]).sqrt()) for x in (t.cpu() for t in terms)])
-                return t0 + (ts[1:] - ts[0]) / 1e9, r
+                return t0 + (ts[1:] - ts[0]) / 1e9, r, sum(nmf.read_stats(st).total_inner), t0
 
             runs = {"plain": curve(nmf.plain_problem(Xg, p, nmf.PREC_BF16))}
             for v in w["variants"]:
@@ -683,20 +771,32 @@ def run_paper(args):
                 torch.cuda.synchronize()
                 runs[v] = curve(nmf.compressed_problem(L, R, XL, XR, p), a.elapsed_time(b) / 1e3)
             tau = (1 + 1e-2) * runs["plain"][1][-1]
-            for name, (t, r) in runs.items():
+            for name, (t, r, inner, t0) in runs.items():
                 idx = np.nonzero(r <= tau)[0]
-                e = per.setdefault(name, {"seconds_to_tau": [], "final_rre": [], "seconds_total": []})
+                e = per.setdefault(name, {"seconds_to_tau": [], "final_rre": [], "seconds_total": [],
+                                          "outer_to_tau": [], "inner_total": [], "us_per_inner": [],
+                                          "compress_s": []})
                 e["seconds_to_tau"].append(float(t[idx[0]]) if idx.size else None)
+                e["outer_to_tau"].append(int(idx[0]) + 1 if idx.size else None)
                 e["final_rre"].append(float(r[-1]))
                 e["seconds_total"].append(float(t[-1]))
+                e["inner_total"].append(int(inner))
+                # device time of the solve per inner iteration (both factors' iterations counted)
+                e["us_per_inner"].append(1e6 * (float(t[-1]) - t0) / max(1, int(inner)))
+                e["compress_s"].append(t0)
             del Xg
         summ = {}
         for name, e in per.items():
             reached = [x for x in e["seconds_to_tau"] if x is not None]
+            outer = [x for x in e["outer_to_tau"] if x is not None]
             summ[name] = {"median_seconds_to_tau": statistics.median(reached) if reached else None,
                           "reached": f"{len(reached)}/{len(e['seconds_to_tau'])}",
+                          "median_outer_to_tau": statistics.median(outer) if outer else None,
                           "median_final_rre": statistics.median(e["final_rre"]),
-                          "median_seconds_total": statistics.median(e["seconds_total"])}
+                          "median_seconds_total": statistics.median(e["seconds_total"]),
+                          "median_inner_total": statistics.median(e["inner_total"]),
+                          "median_us_per_inner": round(statistics.median(e["us_per_inner"]), 3),
+                          "median_compress_s": statistics.median(e["compress_s"])}
         out[str(n)] = summ
     print(json.dumps({"metric": "paper setting: device seconds to RRE tau, plain vs compressed variants",
                       "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "bf16",
@@ -712,24 +812,29 @@ def run_paper(args):
 # ---------------------------------------------------------------------------
 
 def oracle_step(X64, G0, F0, T=None):
-    """One step of the oracle on the host: Alg. 2 then Alg. 1, same sketch seed as the GPU."""
+    """One step of the oracle on the host: Alg. 2 then Alg. 1, same sketch seed as the GPU.
+    Returns the final (G, F)."""
     from oracle import nenmf, philox, subspace
     w = WORKLOAD
     T = w["max_outer"] if T is None else T
     OmL, OmR = philox.sketches(w["n"], w["m"], w["nu"], w["sketch_seed"])
     L, R, XL, XR = subspace.compress(X64, w["nu"], w["q"], OmL, OmR)
-    nenmf.nenmf_compressed(L, R, XL, XR, G0, F0, T, w["max_inner"], tol=w["tol"])
+    G, F, _ = nenmf.nenmf_compressed(L, R, XL, XR, G0, F0, T, w["max_inner"], tol=w["tol"])
+    return G, F
 
 
 def cpu_baseline(X, G0, F0):
+    """The oracle timed on the host cores for one full step; also returns its final RRE."""
+    from oracle import metrics
     X64 = X.astype(np.float64)
     t0 = time.perf_counter()
-    oracle_step(X64, G0, F0)
+    G, F = oracle_step(X64, G0, F0)
     dt = time.perf_counter() - t0
-    return {"value": round(WORKLOAD["max_outer"] / dt, 4), "unit": UNIT, "cores": os.cpu_count(),
-            "kind": "oracle", "seconds": round(dt, 3),
-            "sample": "one full step on the host (numpy float64, all cores): Alg. 2 compression plus "
-                      f"{WORKLOAD['max_outer']} outer iterations of Alg. 1 on the same workload"}
+    return ({"value": round(WORKLOAD["max_outer"] / dt, 4), "unit": UNIT, "cores": os.cpu_count(),
+             "kind": "oracle", "seconds": round(dt, 3),
+             "sample": "one full step on the host (numpy float64, all cores): Alg. 2 compression plus "
+                       f"{WORKLOAD['max_outer']} outer iterations of Alg. 1 on the same workload"},
+            float(metrics.rre(X64, G, F)))
 
 
 def run_reference(args):

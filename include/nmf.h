@@ -222,11 +222,15 @@ size_t nenmf_solve_workspace_size(const nenmf_problem_t* problem);
  *  problem  host pointer; its matrix pointers are device memory.
  *  params   host pointer.
  *  stats    device pointer to one nenmf_stats_t (may be NULL).
- * The stop test of the per-update kernels needs all their CTAs resident at
- * once; a compressed problem with more vectors than that (about 150 x 128 at
- * p = 32) runs on the batched kernel instead (one problem, one cluster; no
- * snapshots there: NMF_ERR_UNSUPPORTED if record_* is set), plain mode
- * returns NMF_ERR_UNSUPPORTED. The workspace query covers both.
+ * Compressed mode runs all outer iterations in one persistent cooperative
+ * launch when its CTAs (one per 128 columns of the larger side) fit on the
+ * device at once and their shares of the p x nu products stay small
+ * (ceil(max(n, m) / 128) * p * nu <= 16384); otherwise one launch per factor
+ * update. The stop test of the per-update kernels needs all their CTAs
+ * resident at once; a compressed problem with more vectors than that (about
+ * 150 x 128 at p = 32) runs on the batched kernel instead (one problem, one
+ * cluster; no snapshots there: NMF_ERR_UNSUPPORTED if record_* is set),
+ * plain mode returns NMF_ERR_UNSUPPORTED. The workspace query covers all.
  */
 nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, float* G, float* F,
                          const nenmf_params_t* params, nenmf_stats_t* stats, void* workspace,
@@ -430,12 +434,20 @@ nmf_status_t nmf_project(nmf_stream_t stream, int n, int m, int nu, nmf_prec_t p
                          const float* R, float* XL, float* XR, void* workspace, size_t workspace_bytes);
 
 /*
- * Selects the kernel for NMF_PREC_BF16 X passes: 0 (default) uses tcgen05
- * tensor cores, 1 uses float32 CUDA cores on the same bfloat16 inputs (same
- * input rounding, different summation order). Process-wide; not thread-safe
- * against concurrent calls. Workspace sizes depend on it: query after setting.
+ * Selects kernels, for cross-checks between paths (flags, OR-ed; 0 is the
+ * default, the fastest path):
+ *  NMF_PATH_XPASS_CUDA_CORES  NMF_PREC_BF16 X passes on float32 CUDA cores
+ *                             instead of tcgen05 tensor cores (same input
+ *                             rounding, different summation order);
+ *  NMF_PATH_SOLVE_PER_UPDATE  nenmf_solve in compressed mode as one launch
+ *                             per factor update instead of one persistent
+ *                             launch for all outer iterations (same
+ *                             arithmetic in the same order: identical results).
+ * Process-wide; not thread-safe against concurrent calls. Workspace sizes
+ * depend on it: query after setting.
  */
-void nmf_set_kernel_path(int force_cuda_cores);
+enum { NMF_PATH_XPASS_CUDA_CORES = 1, NMF_PATH_SOLVE_PER_UPDATE = 2 };
+void nmf_set_kernel_path(int flags);
 
 /*
  * Number of kernel launches this library has enqueued in the process so far
@@ -445,13 +457,39 @@ void nmf_set_kernel_path(int force_cuda_cores);
 long long nmf_kernel_launches(void);
 
 /* ------------------------------------------------------------------------ */
+/* Failure-path testing                                                       */
+/* ------------------------------------------------------------------------ */
+/*
+ * Makes later kernels fail one of their bounded device waits on purpose, so
+ * that a test can exercise the NMF_ERR_DEVICE_TIMEOUT path (status word set,
+ * every CTA leaving its waits, the call's later kernels turning into no-ops)
+ * without hanging or faulting the GPU. Not for production use.
+ *  NMF_FAULT_NONE        normal operation (the default).
+ *  NMF_FAULT_STOP_TEST   in the solve kernels, CTA 0 never publishes its
+ *                        stop-test partials, so every CTA that needs the
+ *                        global sum waits until the limit runs out.
+ *  NMF_FAULT_XPASS_COPY  in the tensor-core X pass, CTA 0 arms its first
+ *                        pipeline stage but issues none of its copies, so the
+ *                        MMA issuer's wait for that stage runs out.
+ * wait_limit_ns > 0 replaces the 2-second limit of every bounded device wait
+ * (stop test, grid barrier, pipeline stages); 0 restores it.
+ * Process-wide; a kernel takes the setting when it is enqueued; not
+ * thread-safe against concurrent calls. Errors: NMF_ERR_INVALID_ARG for an
+ * unknown fault or a negative limit.
+ */
+typedef enum nmf_fault { NMF_FAULT_NONE = 0, NMF_FAULT_STOP_TEST = 1, NMF_FAULT_XPASS_COPY = 2 } nmf_fault_t;
+
+nmf_status_t nmf_inject_fault(int fault, long long wait_limit_ns);
+
+/* ------------------------------------------------------------------------ */
 /* Relative reconstruction error, eq. (4)                                     */
 /* ------------------------------------------------------------------------ */
 size_t nmf_rre_workspace_size(int n, int m, int p);
 
 /*
  * out (device, 2 doubles) <- { ||X - G F||_F^2, ||X||_F^2 } in one pass over X,
- * products in float32 and sums in float64 (fixed reduction order).
+ * products in float32 and sums in float64 (fixed reduction order). Any n >= 1
+ * is accepted: beyond 64 x 65535 rows each block walks several row blocks.
  */
 nmf_status_t nmf_rre(nmf_stream_t stream, int n, int m, int p, const float* X, const float* G,
                      const float* F, double* out, void* workspace, size_t workspace_bytes);
@@ -474,14 +512,17 @@ nmf_status_t nmf_rre(nmf_stream_t stream, int n, int m, int p, const float* X, c
  * the library keeps until the process exits.
  *  - The first call on a device looks up that array's device address
  *    (cudaGetSymbolAddress) with the device current; make that first call
- *    before starting any stream capture.
+ *    before starting any stream capture. A cudaDeviceReset replaces the
+ *    device's context and the array with it: the next call notices the new
+ *    context and looks the address up again, so make that call before any
+ *    capture too.
  *  - All calls share the array: calls that can overlap on the GPU (other
  *    streams, other host threads) race and must be serialised by the caller.
  *  - Every partial is written before it is read, so nothing has to start at
  *    zero; the array keeps the last call's contents.
  *  - Sizes needing more than NMF_RRE_STATIC_MAX_PARTS blocks, where blocks =
- *    ceil(m / 256) * ceil(n / 64), return NMF_ERR_WORKSPACE before anything
- *    is enqueued.
+ *    ceil(m / 256) * min(ceil(n / 64), 65535), return NMF_ERR_WORKSPACE
+ *    before anything is enqueued.
  */
 #define NMF_RRE_STATIC_MAX_PARTS 65536
 nmf_status_t nmf_rre_static(nmf_stream_t stream, int n, int m, int p, const float* X, const float* G,

@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
         "nmf_set_kernel_path": (None, [i]),
         "nmf_kernel_launches": (ctypes.c_longlong, []),
         "nmf_rre_static": (i, [vp, i, i, i, vp, vp, vp, vp]),
+        "nmf_inject_fault": (i, [i, ctypes.c_longlong]),
         "nenmf_solve_batched_workspace_size": (sz, [i, vp, ctypes.POINTER(Params), ctypes.POINTER(BatchConfig)]),
         "nenmf_batch_plan_info": (i, [i, vp, ctypes.POINTER(Params), ctypes.POINTER(BatchConfig),
                                       ctypes.POINTER(BatchConfig), ctypes.POINTER(i)]),
@@ -138,7 +139,7 @@ def exported_symbols():
             "nmf_compress_batched_workspace_size", "nmf_compress_batched", "nmf_compress_f64_workspace_size",
             "nmf_compress_f64", "nenmf_solve_f64_workspace_size", "nenmf_solve_f64",
             "nenmf_backward_f64_workspace_size", "nenmf_backward_f64", "nmf_project_workspace_size", "nmf_project",
-            "nenmf_batch_autotune_workspace_size", "nenmf_batch_autotune"]
+            "nenmf_batch_autotune_workspace_size", "nenmf_batch_autotune", "nmf_inject_fault"]
 
 
 # ---------------------------------------------------------------------------
@@ -195,8 +196,24 @@ def kernel_launches() -> int:
     return int(lib().nmf_kernel_launches())
 
 
-def set_kernel_path(force_cuda_cores: bool):
-    lib().nmf_set_kernel_path(1 if force_cuda_cores else 0)
+PATH_XPASS_CUDA_CORES = 1
+PATH_SOLVE_PER_UPDATE = 2
+
+
+def set_kernel_path(force_cuda_cores: bool = False, per_update_solve: bool = False):
+    """nmf_set_kernel_path: alternative kernels for cross-checks (defaults: the fastest path)."""
+    lib().nmf_set_kernel_path((PATH_XPASS_CUDA_CORES if force_cuda_cores else 0) |
+                              (PATH_SOLVE_PER_UPDATE if per_update_solve else 0))
+
+
+FAULT_NONE = 0
+FAULT_STOP_TEST = 1
+FAULT_XPASS_COPY = 2
+
+
+def inject_fault(fault: int, wait_limit_ns: int = 0):
+    """nmf_inject_fault: failure-path testing only (see include/nmf.h)."""
+    _ok(lib().nmf_inject_fault(fault, wait_limit_ns), "nmf_inject_fault")
 
 
 # ---------------------------------------------------------------------------

@@ -1,6 +1,9 @@
 // aux.cu -- small kernels around the hot path: Gaussian sketches (Alg. 2,
 // "Draw Gaussian random matrices"), the one-time bfloat16 copy of X, layout
 // changes, timestamps, and the RRE of eq. (4).
+#include <cuda.h>
+
+#include <algorithm>
 #include <mutex>
 
 #include "internal.h"
@@ -105,37 +108,44 @@ __global__ void timestamp_kernel(unsigned long long* t) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *t = global_ns();
 }
 
-// RRE partials: block (bx, by) owns 256 columns and kRreRows rows; each
-// thread keeps its column of F in registers and walks the rows; squared
-// residuals and squared entries accumulate in float-float.
+// RRE partials: block (bx, by) owns 256 columns and the row blocks of
+// kRreRows rows by, by + gridDim.y, ... (one row block per block unless
+// ceil(n / kRreRows) exceeds the grid's y limit); each thread keeps its
+// column of F in registers and walks the rows; squared residuals and squared
+// entries accumulate in float-float.
 constexpr int kRreRows = 64;
 constexpr int kRreThreads = 256;
+constexpr int kRreMaxGridY = 65535;
 
 __global__ void __launch_bounds__(kRreThreads) rre_kernel(int n, int m, int p, const float* X, const float* G,
                                                           const float* F, double* part) {
   __shared__ float Gs[kRreRows][NMF_MAX_RANK];
   __shared__ double red[2][kRreThreads / 32];
   const int j = blockIdx.x * kRreThreads + threadIdx.x;
-  const int r0 = blockIdx.y * kRreRows;
-  const int rows = min(kRreRows, n - r0);
-  for (int i = threadIdx.x; i < kRreRows * NMF_MAX_RANK; i += kRreThreads) {
-    const int r = i / NMF_MAX_RANK, c = i % NMF_MAX_RANK;
-    Gs[r][c] = (r < rows && c < p) ? G[(size_t)(r0 + r) * p + c] : 0.f;
-  }
   float f[NMF_MAX_RANK];
 #pragma unroll
   for (int c = 0; c < NMF_MAX_RANK; ++c) f[c] = (j < m && c < p) ? F[(size_t)c * m + j] : 0.f;
-  __syncthreads();
   DF se{0.f, 0.f}, sx{0.f, 0.f};
-  if (j < m) {
-    for (int r = 0; r < rows; ++r) {
-      const float x = X[(size_t)(r0 + r) * m + j];
-      float gf = 0.f;
+  const int row_blocks = ceil_div(n, kRreRows);
+  for (int by = blockIdx.y; by < row_blocks; by += gridDim.y) {
+    const int r0 = by * kRreRows;
+    const int rows = min(kRreRows, n - r0);
+    __syncthreads();  // the previous row block's Gs is consumed
+    for (int i = threadIdx.x; i < kRreRows * NMF_MAX_RANK; i += kRreThreads) {
+      const int r = i / NMF_MAX_RANK, c = i % NMF_MAX_RANK;
+      Gs[r][c] = (r < rows && c < p) ? G[(size_t)(r0 + r) * p + c] : 0.f;
+    }
+    __syncthreads();
+    if (j < m) {
+      for (int r = 0; r < rows; ++r) {
+        const float x = X[(size_t)(r0 + r) * m + j];
+        float gf = 0.f;
 #pragma unroll
-      for (int c = 0; c < NMF_MAX_RANK; ++c) gf = fmaf(Gs[r][c], f[c], gf);
-      const float d = x - gf;
-      df_add_product(se, d, d);
-      df_add_product(sx, x, x);
+        for (int c = 0; c < NMF_MAX_RANK; ++c) gf = fmaf(Gs[r][c], f[c], gf);
+        const float d = x - gf;
+        df_add_product(se, d, d);
+        df_add_product(sx, x, x);
+      }
     }
   }
   double e = (double)se.hi + (double)se.lo, xx = (double)sx.hi + (double)sx.lo;
@@ -233,11 +243,11 @@ cudaError_t timestamp_launch(unsigned long long* t, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int rre_parts(int n, int m) { return ceil_div(m, kRreThreads) * ceil_div(n, kRreRows); }
+int rre_parts(int n, int m) { return ceil_div(m, kRreThreads) * std::min(ceil_div(n, kRreRows), kRreMaxGridY); }
 
 cudaError_t rre_launch(int n, int m, int p, const float* X, const float* G, const float* F, double* out, double* part,
                        int parts, cudaStream_t s) {
-  dim3 grid(ceil_div(m, kRreThreads), ceil_div(n, kRreRows));
+  dim3 grid(ceil_div(m, kRreThreads), std::min(ceil_div(n, kRreRows), kRreMaxGridY));
   count_launches(1);
   rre_kernel<<<grid, kRreThreads, 0, s>>>(n, m, p, X, G, F, part);
   cudaError_t e = cudaGetLastError();
@@ -259,6 +269,34 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_rre_static_mu;
 double* g_rre_static_ptr[kMaxDevices] = {};
+unsigned long long g_rre_static_ctx[kMaxDevices] = {};
+
+// Unique id of the calling thread's current context (0 if unknown), through
+// the driver entry points the runtime hands out: a cudaDeviceReset replaces
+// the device's primary context, and with it the module holding the array.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 }  // namespace
 
 extern "C" nmf_status_t nmf_rre_static(nmf_stream_t stream, int n, int m, int p, const float* X, const float* G,
@@ -272,12 +310,15 @@ extern "C" nmf_status_t nmf_rre_static(nmf_stream_t stream, int n, int m, int p,
   double* scratch = nullptr;
   {
     // Host code cannot use the array's name as a device address: look the
-    // address up once per device, with that device current.
+    // address up with the device current, once per device and again when
+    // the device's context has been replaced (after a cudaDeviceReset).
     std::lock_guard<std::mutex> lock(g_rre_static_mu);
-    if (!g_rre_static_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_rre_static_ptr[dev] || (ctx != 0 && ctx != g_rre_static_ctx[dev])) {
       void* addr = nullptr;
       if (cudaGetSymbolAddress(&addr, g_rre_static_scratch) != cudaSuccess || addr == nullptr) return NMF_ERR_CUDA;
       g_rre_static_ptr[dev] = static_cast<double*>(addr);
+      g_rre_static_ctx[dev] = current_context_id();  // the lookup made the primary context current
     }
     scratch = g_rre_static_ptr[dev];
   }

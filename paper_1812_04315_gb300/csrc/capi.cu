@@ -1,6 +1,7 @@
 // capi.cu -- the extern "C" entry points of include/nmf.h: argument checks,
 // workspace carving and the stream-ordered schedules of Alg. 2 (nmf_compress)
 // and of Alg. 1 / plain NeNMF (nenmf_solve).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -15,7 +16,8 @@ using namespace nmf;
 namespace {
 
 
-int g_force_simt = 0;  // nmf_set_kernel_path
+int g_force_simt = 0;     // nmf_set_kernel_path bit 0
+int g_per_update = 0;     // nmf_set_kernel_path bit 1
 
 int sm_count() {
   int dev = 0, sms = 0;
@@ -36,6 +38,12 @@ namespace nmf {
 
 static std::atomic<long long> g_launches{0};
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;  // 2 s
+static std::atomic<int> g_fault{NMF_FAULT_NONE};
+static std::atomic<unsigned long long> g_wait_ns{kDefaultWaitNs};
+int injected_fault() { return g_fault.load(std::memory_order_relaxed); }
+unsigned long long wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
 
 cudaError_t allow_dynamic_smem(const void* kernel, int bytes) {
   static std::mutex mu;
@@ -252,6 +260,8 @@ struct SolveWs {
   unsigned long long* slots;  // stop-test words: G side [kMaxInnerIters][ctasG], then F side
   double* initG;   // [ctasG]
   double* initF;   // [ctasF]
+  unsigned int* bar;  // persistent solve: grid barrier arrivals
+  float* keep;     // persistent solve: pending stop-test iterates, when they are not in shared memory
   __nv_bfloat16* Xb;
   int ldxb;
   void* opF;       // NV x ldF: F as the N-product operand (A^T = F)
@@ -290,6 +300,8 @@ SolveWs carve_solve(void* base, const nenmf_problem_t& pr) {
   w.slots = cv.take<unsigned long long>((size_t)kMaxInnerIters * (w.ctasG + w.ctasF));
   w.initG = cv.take<double>(w.ctasG);
   w.initF = cv.take<double>(w.ctasF);
+  w.bar = cv.take<unsigned int>(1);
+  if (!plain) w.keep = cv.take<float>(persist_keep_floats(n, m, p, nu));
   if (plain) {
     const nmf_prec_t prec = (nmf_prec_t)pr.prec;
     w.plan = xpass_plan(n, m, p, prec, sm_count());
@@ -388,9 +400,21 @@ nmf_status_t nmf_workspace_status(nmf_stream_t stream, const void* workspace, in
   return NMF_OK;
 }
 
-void nmf_set_kernel_path(int force_cuda_cores) { g_force_simt = force_cuda_cores ? 1 : 0; }
+void nmf_set_kernel_path(int flags) {
+  g_force_simt = (flags & NMF_PATH_XPASS_CUDA_CORES) ? 1 : 0;
+  g_per_update = (flags & NMF_PATH_SOLVE_PER_UPDATE) ? 1 : 0;
+}
 
 long long nmf_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+nmf_status_t nmf_inject_fault(int fault, long long wait_limit_ns) {
+  if (fault != NMF_FAULT_NONE && fault != NMF_FAULT_STOP_TEST && fault != NMF_FAULT_XPASS_COPY)
+    return NMF_ERR_INVALID_ARG;
+  if (wait_limit_ns < 0) return NMF_ERR_INVALID_ARG;
+  g_fault.store(fault, std::memory_order_relaxed);
+  g_wait_ns.store(wait_limit_ns > 0 ? (unsigned long long)wait_limit_ns : kDefaultWaitNs, std::memory_order_relaxed);
+  return NMF_OK;
+}
 
 nmf_status_t nmf_gaussian_sketch(nmf_stream_t stream, int rows, int cols, uint64_t seed, uint32_t stream_id,
                                  float* out) {
@@ -693,6 +717,42 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
   const nmf_prec_t prec = (nmf_prec_t)pr.prec;
   const bool bf16 = plain && prec == NMF_PREC_BF16;
   unsigned long long* times = reinterpret_cast<unsigned long long*>(pa.record_time_ns);
+
+  if (!plain && !g_per_update) {
+    // Alg. 1 in one persistent launch when every CTA fits at once
+    const PersistPlan pp = persist_plan(n, m, p, nu, test, pa.restart != 0);
+    // (pending iterates outside shared memory need the workspace's keep buffer)
+    if (pp.ok && (pp.keep_shared || persist_keep_floats(n, m, p, nu) > 0)) {
+      NMF_CU(cudaMemsetAsync(ctrl, 0, sizeof(Control), s));
+      NMF_CU(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int), s));
+      if (test)
+        NMF_CU(cudaMemsetAsync(w.slots, 0, sizeof(unsigned long long) * pa.max_inner * pp.ctas, s));
+      if (stats) NMF_CU(cudaMemsetAsync(stats, 0, sizeof(nenmf_stats_t), s));
+      if (times) {
+        NMF_CU(cudaMemsetAsync(times, 0, sizeof(long long) * ((size_t)pa.max_outer + 1), s));
+        NMF_CU(timestamp_launch(times, s));
+      }
+      NMF_CU(beta_launch(w.beta, pa.max_inner, s));
+      PersistLaunch L{};
+      L.n = n; L.m = m; L.p = p; L.nu = nu;
+      L.L = pr.L; L.R = pr.R; L.XL = pr.XL; L.XR = pr.XR;
+      L.G = G; L.F = F;
+      L.max_outer = pa.max_outer; L.max_inner = pa.max_inner; L.min_inner = pa.min_inner;
+      L.restart = pa.restart ? 1 : 0;
+      L.beta = w.beta;
+      L.partG = w.partG; L.partF = w.partF;
+      L.pg2G = w.pg2G; L.pg2F = w.pg2F; L.initG = w.initG; L.initF = w.initF;
+      L.slots = w.slots; L.bar = w.bar; L.keep = w.keep;
+      L.record_G = pa.record_G; L.record_F = pa.record_F; L.times = times;
+      L.tol = pa.tol; L.tol_mode = pa.tol_mode;
+      L.stats = stats; L.ctrl = ctrl;
+      NMF_CU(persist_launch(pp, L, s));
+      if (stats || pa.max_outer > 0)
+        NMF_CU(stats_launch(stats, pa.max_outer > 0 ? w.pg2G : nullptr, w.ctasG, pa.max_outer > 0 ? w.pg2F : nullptr,
+                            w.ctasF, ctrl, pa.max_outer, s));
+      return NMF_OK;
+    }
+  }
 
   NMF_CU(cudaMemsetAsync(ctrl, 0, sizeof(Control), s));
   NMF_CU(cudaMemsetAsync(w.ctr, 0, sizeof(unsigned int) * w.nctr, s));

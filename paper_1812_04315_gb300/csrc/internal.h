@@ -123,7 +123,7 @@ enum BSource { B_FROM_ROWS = 0, B_FROM_COLS = 1, B_FROM_PARTIALS = 2 };
 enum Epilogue { EPI_NONE = 0, EPI_W_ROWS = 1, EPI_W_COLS = 2, EPI_GRAM = 3 };
 constexpr int kSolveThreads = 128;
 constexpr int kSolveWarps = kSolveThreads / 32;
-constexpr int kStopSlots = 16;   // shared-memory slots of the stop test (> kLag)
+constexpr int kStopSlots = 36;   // shared-memory slots of the stop test (> 2 x the largest decision lag)
 constexpr int kMaxInnerIters = 4096;  // largest max_inner accepted
 
 constexpr int kMaxReduceFloats = 16384;  // per-CTA shared-memory budget for reducing the predecessor's partials
@@ -186,6 +186,39 @@ cudaError_t beta_launch(float* beta, int K, cudaStream_t s);
 // CTAs of the solve kernel that fit on the device at once (the stop test
 // needs every CTA of a launch resident).
 int solve_max_coresident(int p, int nu, int epi, int groups_in);
+// Persistent compressed solve (all outer iterations in one cooperative
+// launch; persist.cu). ok: the problem fits (every CTA resident at once,
+// the shares small enough for every CTA to read them all).
+struct PersistPlan {
+  bool ok;
+  int ctas, PM;
+  size_t smem;
+  bool keep_shared;  // pending stop-test iterates in shared memory (else in the workspace)
+};
+struct PersistLaunch {
+  int n, m, p, nu;
+  const float *L, *R, *XL, *XR;
+  float *G, *F;
+  int max_outer, max_inner, min_inner, restart;
+  const float* beta;
+  float *partG, *partF;
+  double *pg2G, *pg2F, *initG, *initF;
+  unsigned long long* slots;  // [kMaxInnerIters][ctas]
+  unsigned int* bar;          // zero
+  float* keep;                // persist_keep_floats(plan) floats
+  float *record_G, *record_F;
+  unsigned long long* times;
+  double tol;
+  int tol_mode;
+  nenmf_stats_t* stats;
+  Control* ctrl;
+};
+PersistPlan persist_plan(int n, int m, int p, int nu, bool test, bool restart);
+// Workspace floats for the pending iterates when they do not fit in shared
+// memory (0 when they do, or when the problem is not run persistently).
+size_t persist_keep_floats(int n, int m, int p, int nu);
+cudaError_t persist_launch(const PersistPlan& pl, const PersistLaunch& L, cudaStream_t s);
+
 // Sums final per-CTA partials into the stats struct (one thread).
 cudaError_t stats_launch(nenmf_stats_t* stats, const double* pg2_final_G, int ctasG,
                          const double* pg2_final_F, int ctasF, Control* ctrl, int outer, cudaStream_t s);
@@ -219,6 +252,11 @@ bool device_is_sm103();
 
 // Host-side count of kernel launches enqueued by the library (all threads).
 void count_launches(int k);
+
+// Failure-path testing (nmf_inject_fault): the fault the next launches carry
+// and the limit of every bounded device wait (2 s unless a test lowers it).
+int injected_fault();
+unsigned long long wait_limit_ns();
 
 // Raises a kernel's dynamic shared-memory limit to `bytes` once per device
 // (cached: the attribute call is not repeated on the launch path).

@@ -35,170 +35,18 @@
 
 #include "internal.h"
 #include "nnls_device.cuh"
+#include "stop_test.cuh"
 
 namespace nmf {
 namespace {
-
-constexpr int T = kSolveThreads;
-constexpr int kLag = 4;
-constexpr int kKeep = kLag + 2;  // a test's iterate is kept until its decision is read (posted one iteration late)
-constexpr int kPackedMax = 12;   // largest padded rank whose H the loop keeps in registers
-static_assert(kStopSlots >= 2 * kLag + 1, "stop-test slots are reused after kStopSlots tests");
-constexpr int kFs = T + 4;                  // column-vector rows: 16-byte aligned, rows 4 banks apart
-constexpr int kWs = NMF_MAX_SKETCH + 1;     // rows of W: consecutive rows in different banks
-constexpr unsigned long long kWaitNs = 2000000000ull;
 
 struct KParams {
   SolveArgs a;
   const float* beta;  // [max_inner] extrapolation weights
   int mode;
+  unsigned long long wait_ns;  // limit of every bounded wait
+  int withhold;                // failure-path testing: CTA 0 never posts its stop-test words
 };
-
-// Sum over the block (every warp, including the collector, which adds 0), in
-// float-float arithmetic (float64 is slow on this part); the result is valid
-// in thread 0.
-__device__ __forceinline__ double block_sum_df(float v, float2* red) {
-  DF s{v, 0.f};
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float h = __shfl_xor_sync(0xffffffffu, s.hi, o), l = __shfl_xor_sync(0xffffffffu, s.lo, o);
-    DF a = (lane & o) ? DF{h, l} : s;
-    const DF b = (lane & o) ? s : DF{h, l};
-    df_add(a, b.hi, b.lo);
-    s = a;
-  }
-  const int w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[w] = make_float2(s.hi, s.lo);
-  __syncthreads();
-  DF t{0.f, 0.f};
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) df_add(t, red[i].x, red[i].y);
-  return (double)t.hi + (double)t.lo;
-}
-
-// Stop test. Compute warps post their ||P grad||^2 partial of test j in
-// shared memory; a dedicated collector warp (warp kWarps of the CTA) sums
-// them and publishes the CTA's partial as one 64-bit word (tag << 32 | float
-// bits) in global memory. If the CTA's own partial already exceeds eps^2 the
-// test fails everywhere (partials are nonnegative), and the collector posts
-// "go on" at once; otherwise it waits until every CTA's word for test j
-// carries the tag, sums them in float-float in one fixed order (identical in
-// every CTA) and posts the decision in shared memory. Compute warps read the decision of
-// test j at iteration j + kLag, so they never wait on global memory. A single
-// relaxed 64-bit store publishes value and tag together, so no fence or
-// counter is needed; tags carry the launch epoch, so words left by earlier
-// launches of the same call never match. Every test has its own row of words
-// (no reuse within a launch): a CTA that decides locally may run ahead of a
-// CTA that still polls.
-constexpr int kWarps = T / 32;          // compute warps
-constexpr int kThreadsAll = T + 32;     // plus the collector warp
-
-__device__ __forceinline__ uint32_t stop_tag(int epoch, int j) { return ((uint32_t)epoch << 16) | (uint32_t)(j + 1); }
-
-// Shared words: (test + 1) << 32 | payload, one 64-bit store each, so a
-// reader that sees the tag sees the payload with it (no fence); zeroed at
-// kernel start, so nothing a previous launch left in this shared memory
-// matches a tag.
-struct StopShared {
-  unsigned long long part[kStopSlots][kWarps];  // payload: float bits of the warp's partial
-  unsigned long long dec[kStopSlots];           // payload: 1 = stop, 0 = go on
-  double dec_tot[kStopSlots];                   // the total, written before dec (collector fences)
-};
-__device__ __forceinline__ unsigned long long stop_word(int j, uint32_t payload) {
-  return ((unsigned long long)(uint32_t)(j + 1) << 32) | payload;
-}
-
-// Collector warp: processes tests 0 .. ntests-1 in order until one passes.
-// Returns false on timeout or abort.
-__device__ bool collector_loop(StopShared& S, unsigned long long* slots, int ntests, int epoch, double eps2,
-                               Control* c) {
-  const int lane = threadIdx.x & 31;
-  const int ctas = gridDim.x;
-  const unsigned long long t0 = global_ns();
-  for (int j = 0; j < ntests; ++j) {
-    const int sl = j % kStopSlots;
-    // 1. the CTA's partial: lane w waits for warp w's word of test j
-    int ok = 1;
-    float pv = 0.f;
-    if (lane < kWarps) {
-      unsigned long long w = *((volatile unsigned long long*)&S.part[sl][lane]);
-      while ((uint32_t)(w >> 32) != (uint32_t)(j + 1)) {
-        if (*((volatile int*)&c->abort) || global_ns() - t0 > kWaitNs) { ok = 0; break; }
-        w = *((volatile unsigned long long*)&S.part[sl][lane]);
-      }
-      pv = __uint_as_float((uint32_t)w);
-    }
-    if (!__all_sync(0xffffffffu, ok)) return false;
-    float own = 0.f;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) own += __shfl_sync(0xffffffffu, pv, w);  // same order in every lane
-    if (lane == 0) {
-      const unsigned long long word =
-          ((unsigned long long)stop_tag(epoch, j) << 32) | (unsigned long long)__float_as_uint(own);
-      cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(slots[(size_t)j * ctas + blockIdx.x]);
-      r.store(word, cuda::memory_order_relaxed);
-    }
-    // Partials are nonnegative and every sum below is monotone, so the total
-    // is at least this CTA's partial: when that already exceeds eps^2 the
-    // test fails in every CTA, and the decision needs no other CTA's word.
-    if ((double)own > eps2) {
-      if (lane == 0) {
-        S.dec_tot[sl] = (double)own;
-        __threadfence_block();
-        *((volatile unsigned long long*)&S.dec[sl]) = stop_word(j, 0u);
-      }
-      continue;
-    }
-    // 2. every CTA's partial, summed in float-float in a fixed order
-    const uint32_t tag = stop_tag(epoch, j);
-    DF acc{0.f, 0.f};
-    for (int i = lane; i < ctas && ok; i += 32) {
-      cuda::atomic_ref<const unsigned long long, cuda::thread_scope_device> r(slots[(size_t)j * ctas + i]);
-      unsigned long long w = r.load(cuda::memory_order_relaxed);
-      while ((uint32_t)(w >> 32) != tag) {
-        if (*((volatile int*)&c->abort) || global_ns() - t0 > kWaitNs) { ok = 0; break; }
-        w = r.load(cuda::memory_order_relaxed);
-      }
-      df_add(acc, __uint_as_float((uint32_t)w), 0.f);
-    }
-    if (!__all_sync(0xffffffffu, ok)) return false;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
-      const float lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
-      DF a = (lane & o) ? DF{hi, lo} : acc;  // lower lane's value first in both lanes
-      const DF b = (lane & o) ? acc : DF{hi, lo};
-      df_add(a, b.hi, b.lo);
-      acc = a;
-    }
-    const double total = (double)acc.hi + (double)acc.lo;
-    const int stop = total <= eps2;
-    if (lane == 0) {
-      S.dec_tot[sl] = total;
-      __threadfence_block();
-      *((volatile unsigned long long*)&S.dec[sl]) = stop_word(j, (uint32_t)stop);
-    }
-    if (stop) return true;
-  }
-  return true;
-}
-
-// Compute warp: waits for the collector's decision on test j (1 = stop, 0 =
-// go on, -1 = timeout or abort).
-__device__ __forceinline__ int wait_decision(StopShared& S, int j, Control* c) {
-  const int sl = j % kStopSlots;
-  unsigned long long w = *((volatile unsigned long long*)&S.dec[sl]);
-  if ((uint32_t)(w >> 32) != (uint32_t)(j + 1)) {
-    const unsigned long long t0 = global_ns();
-    do {
-      if (*((volatile int*)&c->abort) || global_ns() - t0 > kWaitNs) return -1;
-      w = *((volatile unsigned long long*)&S.dec[sl]);
-    } while ((uint32_t)(w >> 32) != (uint32_t)(j + 1));
-  }
-  return (int)(w & 1ull);
-}
 
 // Bulk copy global -> shared (async proxy), completion counted on an mbarrier.
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -222,11 +70,11 @@ __device__ __forceinline__ bool mbar_done(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for phase `parity`; false after kWaitNs or on abort.
-__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, Control* c) {
+// Bounded wait for phase `parity`; false after wait_ns or on abort.
+__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, Control* c, unsigned long long wait_ns) {
   const unsigned long long t0 = global_ns();
   while (!mbar_done(bar, parity)) {
-    if (*((volatile int*)&c->abort) || global_ns() - t0 > kWaitNs) return false;
+    if (*((volatile int*)&c->abort) || global_ns() - t0 > wait_ns) return false;
   }
   return true;
 }
@@ -330,14 +178,14 @@ __global__ void __launch_bounds__(kThreadsAll, PM <= 16 ? 2 : 1) solve_kernel(KP
     float* Rw = Ps + G * P4;      // [P4]: the reduced W (or H)
     float* Red = Rw + P4;         // [slices][P4]
     if (tid == 0) bulk_load(Ps, a.part_in, (uint32_t)(G * P4) * 4u, &pbar);
-    const bool got = mbar_wait_bounded(&pbar, 0u, ctrl);
+    const bool got = mbar_wait_bounded(&pbar, 0u, ctrl, kp.wait_ns);
     if (__syncthreads_or(!got)) {
       if (tid == 0) {
         set_status(ctrl, NMF_ERR_DEVICE_TIMEOUT);
         *((volatile int*)&ctrl->abort) = 1;
         // the copy is in flight: wait for it (bounded) before leaving
         const unsigned long long t0 = global_ns();
-        while (!mbar_done(&pbar, 0u) && global_ns() - t0 < kWaitNs) {
+        while (!mbar_done(&pbar, 0u) && global_ns() - t0 < kp.wait_ns) {
         }
       }
       __syncthreads();
@@ -412,6 +260,14 @@ __global__ void __launch_bounds__(kThreadsAll, PM <= 16 ? 2 : 1) solve_kernel(KP
         }
       }
     }
+    if (active) {
+      // non-finite data or a non-finite current factor: max(0, .) would turn
+      // a NaN step into 0 silently, so report it (the call's later kernels stop)
+      bool bad = false;
+#pragma unroll
+      for (int c = 0; c < PM; ++c) bad |= !isfinite(b[c]) || !isfinite(y[c]);
+      if (bad) set_status(ctrl, NMF_ERR_NONFINITE);
+    }
     // L_c by the whole block (the slice sums are consumed: eigenvalue scratch)
     if (kp.mode == MODE_SOLVE) lambda_max_cta<PM>(Hs, Red, lam_dg, &lam_s, p);
     __syncthreads();
@@ -455,13 +311,15 @@ __global__ void __launch_bounds__(kThreadsAll, PM <= 16 ? 2 : 1) solve_kernel(KP
     constexpr bool test = TEST;
     const double eps2 = ctrl->eps2;
     int tests = 0, stop_j = -1;  // tests: posted so far
+    int checked = 0;             // decisions read so far
     int made = 0;                // tests computed (made - tests: the one whose warp sum is deferred)
     float pend = 0.f;            // this column's ||P grad||^2 term of that test
     bool aborted = false;
     if (!colthr) {
       // collector warp
       const int ntests = test ? max(0, a.max_inner - a.min_inner + 1) : 0;
-      if (!collector_loop(stop_s, a.stop_slots, ntests, a.epoch, eps2, ctrl)) {
+      if (!collector_loop(stop_s, a.stop_slots, ntests, a.epoch, eps2, ctrl, kp.wait_ns, kp.withhold != 0,
+                          ctas)) {
         aborted = true;
         if ((tid & 31) == 0) {
           set_status(ctrl, NMF_ERR_DEVICE_TIMEOUT);
@@ -510,9 +368,13 @@ __global__ void __launch_bounds__(kThreadsAll, PM <= 16 ? 2 : 1) solve_kernel(KP
                 stop_word(tests, __float_as_uint(ws));
           ++tests;
           if (tests > kLag) {
-            const int j = tests - 1 - kLag;
-            const int d = wait_decision(stop_s, j, ctrl);
-            if (d < 0) { aborted = true; break; }
+            const int j = checked++;  // decisions are read in order, kLag tests behind
+            const int d = wait_decision(stop_s, j, ctrl, kp.wait_ns);
+            if (d < 0) {
+              give_up(ctrl);
+              aborted = true;
+              break;
+            }
             if (d) {
               stop_j = j;
               break;
@@ -538,9 +400,13 @@ __global__ void __launch_bounds__(kThreadsAll, PM <= 16 ? 2 : 1) solve_kernel(KP
       }
       if (test && stop_j < 0 && !aborted) {
         // tests still pending when the loop ended, in order
-        for (int j = tests > kLag ? tests - kLag : 0; j < tests; ++j) {
-          const int d = wait_decision(stop_s, j, ctrl);
-          if (d < 0) { aborted = true; break; }
+        for (int j = checked; j < tests; ++j) {
+          const int d = wait_decision(stop_s, j, ctrl, kp.wait_ns);
+          if (d < 0) {
+              give_up(ctrl);
+              aborted = true;
+              break;
+            }
           if (d) {
             stop_j = j;
             break;
@@ -773,7 +639,7 @@ int occupancy_pm(size_t smem) {
 int solve_ctas(int N) { return ceil_div(N, T); }
 
 cudaError_t solve_launch_mode(const SolveArgs& a, const float* beta, int mode, cudaStream_t s) {
-  KParams kp{a, beta, mode};
+  KParams kp{a, beta, mode, wait_limit_ns(), injected_fault() == NMF_FAULT_STOP_TEST ? 1 : 0};
   switch (pad_rank(a.p)) {
     case 4: return launch_pm<4>(kp, s);
     case 8: return launch_pm<8>(kp, s);

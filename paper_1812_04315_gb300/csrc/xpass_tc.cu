@@ -42,7 +42,6 @@ constexpr int kThreads = 192;
 constexpr size_t kSmemBudget = 220 * 1024;
 constexpr int kXStageBytes = kTM * kTK * 2;  // 32 KB
 constexpr uint32_t kMaxTmemCols = 512;
-constexpr long long kWaitLimit = 1ll << 31;  // clock cycles (~1 s)
 constexpr int kStg = 36;                     // floats per staged row (16-byte rows, 4 banks apart)
 constexpr int kStageArea = 4 * 32 * kStg * 4;  // epilogue staging: 4 warps x 32 rows
 
@@ -55,6 +54,8 @@ struct TcParams {
   float* partT;
   Control* ctrl;
   uint32_t tmem_cols;
+  unsigned long long wait_ns;  // limit of every bounded wait
+  int withhold;                // failure-path testing: CTA 0 arms its first stage and issues no copy
 };
 
 __host__ __device__ __forceinline__ int split_point(int total, int parts, int i) {
@@ -87,16 +88,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 // Bounded wait: false when the deadline passed or the CTA is aborting.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  const long long t0 = clock64();
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long wait_ns) {
+  const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitLimit) {
+    if (global_ns() - t0 > wait_ns) {
       *abort_flag = 1;
       return false;
     }
   }
   return true;
+}
+// Bounded wait that ignores the abort flag (draining work already in flight).
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, unsigned long long wait_ns) {
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity) && global_ns() - t0 < wait_ns) {
+  }
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -231,9 +239,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int ct = ct0; ct < ct1; ++ct, ++it) {
           const int s = it % kStages;
           const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, P.wait_ns)) break;
           uint8_t* st = smem + (size_t)s * stageBytes;
           mbar_arrive_expect_tx(&full[s], bytes);
+          if (P.withhold && blockIdx.x == 0 && it == 0) continue;  // failure-path testing: the stage never fills
           bulk_load(st, P.Xt + ((size_t)rt * P.tiles_c + ct) * kXStageBytes, (uint32_t)kXStageBytes, &full[s]);
           if (P.doN) {
             tma_load_2d(st + kXStageBytes, &mapA, &full[s], ct * kTK, 0);
@@ -248,11 +257,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (*abort_flag) {
         // let the copies already issued land before the CTA exits
         const int issued = it;
-        for (int j = issued - kStages < 0 ? 0 : issued - kStages; j < issued; ++j) {
-          const long long t0 = clock64();
-          while (!mbar_try_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u) && clock64() - t0 < kWaitLimit) {
-          }
-        }
+        for (int j = issued - kStages < 0 ? 0 : issued - kStages; j < issued; ++j)
+          mbar_drain(&full[j % kStages], (uint32_t)(j / kStages) & 1u, P.wait_ns);
       }
     }
   } else if (warp == 1) {
@@ -266,13 +272,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int buf = ri & 1;
         const uint32_t dN = tmem + (uint32_t)(buf * NV);
         if (P.doN) {
-          if (!mbar_wait(&tempty[buf], ((uint32_t)(ri >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&tempty[buf], ((uint32_t)(ri >> 1) & 1u) ^ 1u, abort_flag, P.wait_ns)) { ok = false; break; }
           tc_fence_after();
         }
         for (int ci = 0; ci < nct; ++ci, ++it) {
           const int s = it % kStages;
           const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-          if (!mbar_wait(&full[s], ph, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&full[s], ph, abort_flag, P.wait_ns)) { ok = false; break; }
           tc_fence_after();
           const uint32_t st = smem_u32(smem + (size_t)s * stageBytes);
           const uint32_t xa = st, opa = st + kXStageBytes, opb = st + kXStageBytes + 2 * opBox;
@@ -310,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (P.doN) {
       for (int ri = 0; ri < nrt; ++ri) {
         const int buf = ri & 1;
-        if (!mbar_wait(&tfull[buf], (uint32_t)(ri >> 1) & 1u, abort_flag)) break;
+        if (!mbar_wait(&tfull[buf], (uint32_t)(ri >> 1) & 1u, abort_flag, P.wait_ns)) break;
         tc_fence_after();
 #pragma unroll
         for (int c = 0; c < NV; c += 8) tmem_ld8(tmem + lane_off + (uint32_t)(buf * NV + c), v + c);
@@ -322,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         store_block<NV>(v, stg, P.partN + ((size_t)cg * P.n + row0) * NV, P.n - row0, lane);
       }
     }
-    if (P.doT && mbar_wait(&tdone, 0u, abort_flag)) {
+    if (P.doT && mbar_wait(&tdone, 0u, abort_flag, P.wait_ns)) {
       tc_fence_after();
       for (int ci = 0; ci < nct; ++ci) {
 #pragma unroll
@@ -332,11 +338,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         store_block<NV>(v, stg, P.partT + ((size_t)rg * P.m + col0) * NV, P.m - col0, lane);
       }
     } else if (!P.doT) {
-      mbar_wait(&tdone, 0u, abort_flag);
+      mbar_wait(&tdone, 0u, abort_flag, P.wait_ns);
     }
   }
   // The MMA issuer's last commit (tdone) completes only when every MMA has
-  // finished reading shared memory and writing TMEM.
+  // finished reading shared memory and writing TMEM; after an abort nobody
+  // else waited for it, so the issuer drains it before the TMEM is freed.
+  if (warp == 1 && lane == 0 && *abort_flag) mbar_drain(&tdone, 0u, P.wait_ns);
   tc_fence_before();
   __syncthreads();
   if (*abort_flag && threadIdx.x == 0) set_status(P.ctrl, NMF_ERR_DEVICE_TIMEOUT);
@@ -517,6 +525,8 @@ cudaError_t xpass_tc_launch(const XPassPlan& pl, const XPassArgs& a, cudaStream_
   P.partT = a.partT;
   P.ctrl = a.ctrl;
   P.tmem_cols = tmem_cols_for(pl.NV, ceil_div(pl.tiles_c, pl.S_c));
+  P.wait_ns = wait_limit_ns();
+  P.withhold = injected_fault() == NMF_FAULT_XPASS_COPY ? 1 : 0;
   switch (pl.NV) {
     case 16: return launch_nv<16>(mA, mB, P, pl.ctas, s);
     case 32: return launch_nv<32>(mA, mB, P, pl.ctas, s);

@@ -54,6 +54,11 @@ def test_workspace_queries(L):
     assert L.nmf_compress_workspace_size(0, 800, 20, 1) == 0
     assert L.nmf_compress_workspace_size(10, 10, 65, 0) == 0
     assert L.nmf_rre_workspace_size(100, 100, 5) > 0
+    # one partial (two doubles) per block; the grid's y extent stops at 65535
+    # row blocks of 64 rows, beyond which blocks walk several row blocks
+    assert L.nmf_rre_workspace_size(64 * 65535, 256, 4) == 65535 * 16 + 16
+    assert L.nmf_rre_workspace_size(64 * 65535 + 1, 256, 4) == 65535 * 16 + 16
+    assert L.nmf_rre_workspace_size(64 * 70000, 512, 4) == 2 * 65535 * 16 + 32
     import paper_1812_04315_gb300 as pkg
     pr = pkg._problem(pkg.COMPRESSED, 100, 90, 4, 8, 0)
     pr.L = pr.R = pr.XL = pr.XR = 256

@@ -3,10 +3,17 @@
 Both sides get the same Gaussian sketches (host-drawn, or the library's own
 Philox draw reproduced by the oracle). What is compared:
 * orthonormality of L (rows) and R (columns);
-* the leading p basis vectors entrywise (they depend only on well-conditioned
-  leading columns of the sketch products), and the whole subspace through the
-  largest principal angle to the oracle's;
-* X_L = L X and X_R = X R against float64 products of the library's own L, R;
+* the leading p basis vectors entrywise, and the whole subspace through the
+  largest principal angle to the oracle's. Only the leading p of the nu
+  vectors are compared entry by entry: on data of rank p plus noise, the
+  trailing nu - p columns of each sketch product span noise directions
+  whose singular values are nearly equal, so those basis vectors are
+  ill-conditioned (any rotation among them is an equally valid basis of the
+  same span and rounding picks one); their span is what the method uses,
+  and the principal angle checks it;
+* X_L = L X and X_R = X R entry by entry against float64 products of the
+  library's own L, R (for the bfloat16 path: of the bfloat16-rounded L, R
+  and X, the operands the tensor cores multiply);
 * exact recovery on exactly low-rank X (nu >= rank X): X = L^T L X = X R R^T.
 Tolerances: float32 path 2^-24-scale errors amplified by the conditioning of
 the sketch products (kept below 1e2 here); the bfloat16 path rounds X and the
@@ -16,6 +23,7 @@ bases to 8 significant bits (relative 2^-9), so its subspace agrees to ~1e-2.
 import numpy as np
 import pytest
 
+from _parity import bf16_round
 import synth
 from oracle import philox, subspace
 
@@ -71,9 +79,10 @@ def test_compress_matches_oracle(nmf, n, m, p, nu, q, snr, prec):
         np.testing.assert_allclose(XL, L @ Xd, atol=4 * np.sqrt(m) * 2**-24 * (np.abs(L) @ np.abs(Xd)).max())
         np.testing.assert_allclose(XR, Xd @ R, atol=4 * np.sqrt(m) * 2**-24 * (np.abs(Xd) @ np.abs(R)).max())
     else:
-        Xb = X.astype(np.float64)
-        rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
-        assert rel(XL, L @ Xb) < 1e-2 and rel(XR, Xb @ R) < 1e-2
+        # the final pass multiplies bfloat16 X by the bfloat16-rounded bases, accumulating in float32
+        Lb, Rb, Xb = bf16_round(L), bf16_round(R), bf16_round(X)
+        assert np.all(np.abs(XL - Lb @ Xb) <= 4 * np.sqrt(n) * 2**-24 * (np.abs(Lb) @ np.abs(Xb)) + 1e-30)
+        assert np.all(np.abs(XR - Xb @ Rb) <= 4 * np.sqrt(m) * 2**-24 * (np.abs(Xb) @ np.abs(Rb)) + 1e-30)
     # captured energy agrees with the oracle's
     e_gpu = np.linalg.norm(XL) / np.linalg.norm(Xd)
     e_ora = np.linalg.norm(XLo) / np.linalg.norm(Xd)

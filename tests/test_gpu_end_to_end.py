@@ -101,3 +101,24 @@ def test_largest_configuration(nmf):
     G2, F2 = G0.clone(), F0.clone()
     nmf.solve_batched([prob], [G2], [F2], 5, 10, cluster=8)
     assert abs(nmf.rre(X, G1, F1) - nmf.rre(X, G2, F2)) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,tol_rre", [(1, 1e-3), (0, 1e-5)])
+def test_largest_configuration_shape_against_oracle(nmf, prec, tol_rre):
+    # The largest configuration's regime at a size the oracle finishes in
+    # seconds: p = 32 (the widest register tile of the solve kernel),
+    # nu = 42 (the 48-wide MMA of the tensor-core pass), q = 4, 40 dB noise,
+    # 10 % of G0's entries zero (sparse sources); n x m = 5000 x 2000 keeps
+    # the 5 : 2 aspect. GPU compression + solve against the oracle's Alg. 2 +
+    # Alg. 1 on the same sketches, RRE at every outer iteration.
+    n, m, p, nu, q, T, inner, tol = 5000, 2000, 32, 42, 4, 100, 10, 1e-6
+    X, _, _ = synth.lowrank_data(n, m, p, seed=5, snr_db=40.0, dtype=np.float32, zero_frac=0.1)
+    G0, F0 = (a.astype(np.float32) for a in synth.initial_factors(n, m, p, seed=7))
+    OmL, OmR = (a.astype(np.float32) for a in synth.gaussian_sketches(n, m, nu, seed=6))
+    r_gpu, st = _run(nmf, X, G0, F0, p, nu, q, T, inner, tol, prec, OmL, OmR)
+    Xd = X.astype(np.float64)
+    L, R, XL, XR = subspace.compress(Xd, nu, q, OmL.astype(np.float64), OmR.astype(np.float64))
+    _, _, info = nenmf.nenmf_compressed(L, R, XL, XR, G0, F0, T, inner, tol=tol, record=True)
+    r_ora = metrics.rre_history(Xd, info["history"])
+    print("max |RRE gpu - RRE oracle|", np.abs(r_gpu - r_ora).max(), "final", r_gpu[-1], r_ora[-1])
+    assert np.max(np.abs(r_gpu - r_ora)) <= tol_rre, np.abs(r_gpu - r_ora).max()

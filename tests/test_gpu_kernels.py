@@ -107,3 +107,19 @@ def test_rre_kernel(nmf, n, m, p):
     # per-entry residual error <= p * 2^-24 * sum|G F| + rounding of x: relative 1e-5 on the sums
     assert abs(terms[0] - ref_e) <= 1e-5 * ref_e + 1e-9
     assert abs(terms[1] - ref_x) <= 1e-7 * ref_x
+
+
+def test_rre_kernel_beyond_the_grid_row_limit(nmf):
+    # 64 x 65535 rows fill the grid's y extent; with 100 rows more, the last
+    # block walks a second row block (the same fixed summation order per block).
+    n, m, p = 64 * 65535 + 100, 3, 2
+    rng = np.random.default_rng(17)
+    X = rng.random((n, m)).astype(np.float32)
+    G = rng.random((n, p)).astype(np.float32)
+    F = rng.random((p, m)).astype(np.float32) / p
+    terms = _np(nmf.rre_terms(_t(X), _t(G), _t(F)))
+    Xd, Gd, Fd = X.astype(np.float64), G.astype(np.float64), F.astype(np.float64)
+    ref_e = np.sum((Xd - Gd @ Fd) ** 2)
+    ref_x = np.sum(Xd ** 2)
+    assert abs(terms[0] - ref_e) <= 1e-5 * ref_e
+    assert abs(terms[1] - ref_x) <= 1e-7 * ref_x

@@ -3,13 +3,24 @@
 Inputs are float32 on both sides (the oracle computes in float64 on the same
 float32 values). Compared per outer iteration: the RRE of eq. (4), bound
 |RRE_gpu - RRE_oracle| <= 1e-5 for the float32 paths (the target tolerance);
-after one outer iteration the factors themselves (float32 rounding of O(p)
-term dot products through <= 10 Nesterov steps: relative 1e-4).
+after one outer iteration the factors themselves, entry by entry.
+
+Per-entry bound on the factors after one outer iteration: each inner step
+forms an O(p)-term gradient H y - b in float32, so an entry's error is a few
+units of 2^-24 times the scale of its column's terms, carried through <= 10
+non-expansive projected steps (the extrapolation adds at most a factor 2 per
+step to a difference, and the contraction of the step removes most of it):
+    |gpu - oracle| <= ftol * (|oracle| + s),
+s the root-mean-square of the oracle's factor (an entry held at 0 by the
+projection on one side and at a rounding-level positive value on the other
+differs by rounding of that scale), ftol = 1e-4 for the float32 paths and
+2e-2 where the X products take bfloat16 inputs (relative 2^-9 per input).
 """
 
 import numpy as np
 import pytest
 
+from _parity import assert_entrywise
 import synth
 from oracle import metrics, nenmf, subspace
 
@@ -68,8 +79,8 @@ def test_plain_solve_matches_oracle(nmf, n, m, p, T, inner, tol, prec):
     # after the first outer iteration the factors agree closely
     G1, F1 = info["history"][0]
     ftol = 1e-4 if prec == 0 else 2e-2
-    assert np.linalg.norm(_np(rec.G[0]) - G1) <= ftol * np.linalg.norm(G1)
-    assert np.linalg.norm(_np(rec.F[0]) - F1) <= ftol * np.linalg.norm(F1)
+    assert_entrywise(_np(rec.G[0]), G1, ftol, "G after one outer iteration")
+    assert_entrywise(_np(rec.F[0]), F1, ftol, "F after one outer iteration")
     np.testing.assert_array_equal(_np(G), _np(rec.G[T - 1]))
     np.testing.assert_array_equal(_np(F), _np(rec.F[T - 1]))
     assert (_np(G) >= 0).all() and (_np(F) >= 0).all()
@@ -98,8 +109,8 @@ def test_compressed_solve_matches_oracle(nmf, n, m, p, nu, q, T, inner, tol):
     r_ora = metrics.rre_history(Xd, info["history"])
     assert np.max(np.abs(r_gpu - r_ora)) <= 1e-5, (r_gpu - r_ora)
     G1, F1 = info["history"][0]
-    assert np.linalg.norm(_np(rec.G[0]) - G1) <= 1e-4 * np.linalg.norm(G1)
-    assert np.linalg.norm(_np(rec.F[0]) - F1) <= 1e-4 * np.linalg.norm(F1)
+    assert_entrywise(_np(rec.G[0]), G1, 1e-4, "G after one outer iteration")
+    assert_entrywise(_np(rec.F[0]), F1, 1e-4, "F after one outer iteration")
     assert st.total_inner[0] + st.total_inner[1] == pytest.approx(sum(a + b for a, b in info["inner"]), abs=2)
 
 

@@ -19,6 +19,7 @@ products; bfloat16 path: X and the bases rounded to 8 significant bits).
 import numpy as np
 import pytest
 
+from _parity import assert_product, bf16_round
 import synth
 from oracle import subspace
 
@@ -32,6 +33,17 @@ def _t(a):
 
 def _np(t):
     return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _final_pass(XL, XR, L, R, X, prec):
+    """X_L = L X and X_R = X R entry by entry against float64 products of the
+    operands the last pass multiplied (bfloat16-rounded for prec 1)."""
+    if prec == 1:
+        Ld, Rd, Xd = bf16_round(L), bf16_round(R), bf16_round(X)
+    else:
+        Ld, Rd, Xd = (np.asarray(a, dtype=np.float64) for a in (L, R, X))
+    assert_product(XL, Ld, Xd, "X_L")
+    assert_product(XR, Xd, Rd, "X_R")
 
 
 def _max_angle(Q1, Q2):
@@ -62,9 +74,7 @@ def test_orthonormalising_variants(nmf, variant, n, m, p, nu, q, prec):
     np.testing.assert_allclose(L[:p], Lo[:p], atol=lead * np.abs(Lo[:p]).max())
     np.testing.assert_allclose(R[:, :p], Ro[:, :p], atol=lead * np.abs(Ro[:, :p]).max())
     Xd = X.astype(np.float64)
-    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
-    assert rel(XL, L @ Xd) < (1e-5 if prec == 0 else 1e-2)
-    assert rel(XR, Xd @ R) < (1e-5 if prec == 0 else 1e-2)
+    _final_pass(XL, XR, L, R, X, prec)
     e_gpu = np.linalg.norm(XL) / np.linalg.norm(Xd)
     e_ora = np.linalg.norm(XLo) / np.linalg.norm(Xd)
     assert abs(e_gpu - e_ora) < (1e-5 if prec == 0 else 1e-3)
@@ -116,10 +126,7 @@ def test_gaussian_projection(nmf, prec):
     (L, R, XL, XR), (Lo, Ro, _, _) = _run(nmf, X, nu, 0, prec, "gaussian")
     np.testing.assert_allclose(L, Lo, rtol=1e-6, atol=1e-7)
     np.testing.assert_allclose(R, Ro, rtol=1e-6, atol=1e-7)
-    Xd = X.astype(np.float64)
-    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
-    assert rel(XL, L @ Xd) < (1e-5 if prec == 0 else 1e-2)
-    assert rel(XR, Xd @ R) < (1e-5 if prec == 0 else 1e-2)
+    _final_pass(XL, XR, L, R, X, prec)
 
 
 def test_library_sketch_variants_match_default_draw(nmf):

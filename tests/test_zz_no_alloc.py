@@ -47,5 +47,7 @@ def test_rre_static_rejects_sizes_beyond_its_scratch(nmf):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     dummy = torch.empty(4, dtype=torch.float64, device="cuda")
     ptr = dummy.data_ptr()
-    # ceil(m / 256) * ceil(n / 64) blocks > 65536: refused before any launch (NMF_ERR_WORKSPACE).
-    assert fn(stream, 64 * 65537, 256, 4, ptr, ptr, ptr, ptr) == 2
+    # ceil(m / 256) * min(ceil(n / 64), 65535) blocks > 65536: refused before
+    # any launch (NMF_ERR_WORKSPACE); the pointers are never dereferenced.
+    assert fn(stream, 64 * 65537, 512, 4, ptr, ptr, ptr, ptr) == 2
+    assert fn(stream, 64, 256 * 65537, 4, ptr, ptr, ptr, ptr) == 2
