@@ -664,7 +664,8 @@ bool too_many_ctas(const nenmf_problem_t& pr) {
   const int gG = partial_group_size(ctasG, P), gF = partial_group_size(ctasF, P);
   const int inG = gF > 1 ? group_count(ctasF, gF) : ctasF;
   const int inF = gG > 1 ? group_count(ctasG, gG) : ctasG;
-  return ctasG > solve_max_coresident(pr.p, nu, epiG, inG) || ctasF > solve_max_coresident(pr.p, nu, epiF, inF);
+  return ctasG > kMaxStopCtas || ctasF > kMaxStopCtas || ctasG > solve_max_coresident(pr.p, nu, epiG, inG) ||
+         ctasF > solve_max_coresident(pr.p, nu, epiF, inF);
 }
 
 constexpr int kLargeCluster = 8;
@@ -704,7 +705,7 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
   const int epiF = plain ? EPI_GRAM : EPI_W_ROWS;
   const int groupsInG = w.groupF > 1 ? group_count(w.ctasF, w.groupF) : w.ctasF;  // read by the G update
   const int groupsInF = w.groupG > 1 ? group_count(w.ctasG, w.groupG) : w.ctasG;  // read by the F update
-  if (test && (w.ctasG > solve_max_coresident(p, nu, epiG, groupsInG) ||
+  if (test && (w.ctasG > kMaxStopCtas || w.ctasF > kMaxStopCtas || w.ctasG > solve_max_coresident(p, nu, epiG, groupsInG) ||
                w.ctasF > solve_max_coresident(p, nu, epiF, groupsInF))) {
     // more vectors than one co-resident grid: compressed problems go to the
     // batched kernel (snapshots are single-kernel only)

@@ -123,7 +123,7 @@ enum BSource { B_FROM_ROWS = 0, B_FROM_COLS = 1, B_FROM_PARTIALS = 2 };
 enum Epilogue { EPI_NONE = 0, EPI_W_ROWS = 1, EPI_W_COLS = 2, EPI_GRAM = 3 };
 constexpr int kSolveThreads = 128;
 constexpr int kSolveWarps = kSolveThreads / 32;
-constexpr int kStopSlots = 36;   // shared-memory slots of the stop test (> 2 x the largest decision lag)
+constexpr int kMaxStopCtas = 320;  // CTAs one stop test spans at most
 constexpr int kMaxInnerIters = 4096;  // largest max_inner accepted
 
 constexpr int kMaxReduceFloats = 16384;  // per-CTA shared-memory budget for reducing the predecessor's partials

@@ -20,13 +20,13 @@
 //           extrapolated y' follows by linearity,
 //           grad(y') = grad(f) + beta_k (grad(f) - grad(f_prev)).
 //           For p <= 12 the loop reads H from registers (packed upper
-//           triangle). Optional stop test ||P grad(f_k)||_F <= eps: every CTA
-//           publishes its partial as one tagged 64-bit word and every CTA sums
-//           all partials in the same fixed order; a test's warp sums run in
-//           the next iteration, beside its independent product, so the
-//           shuffles hide behind the FMAs; the result of test k is read kLag
-//           tests after it was posted, so the wait overlaps compute, and f_k
-//           is kept until then (bounded waits);
+//           triangle). Optional stop test ||P grad(f_k)||_F <= eps
+//           (stop_test.cuh), taken in blocks of kBlockU tests: each
+//           iteration records its test, the block's tests are then decided
+//           in order (locally when a partial already exceeds eps^2, else
+//           from every CTA's tagged partial, summed in one fixed order),
+//           and the first one that passed returns its kept iterate (bounded
+//           waits);
 // epilogue  the returned iterate is stored (and copied for the next X pass,
 //           the snapshot, the stats); the next phase's W (f times rows of R or
 //           columns of L) or Gram matrix f f^T is summed per CTA; for large
@@ -39,6 +39,8 @@
 
 namespace nmf {
 namespace {
+
+constexpr int kBlockU = 6;  // stop tests per block (their iterates are kept in shared memory)
 
 struct KParams {
   SolveArgs a;
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(kThreadsAll, PM <= 16 ? 2 : 1) solve_kernel(KP
   const int p = a.p, nu = a.nu, N = a.N;
   const int tid = threadIdx.x;
   const int NT = blockDim.x;          // all threads, for cooperative loads
-  const bool colthr = tid < T;        // threads 0..T-1 own a column each; warp kWarps collects
+  const bool colthr = tid < T;        // every thread owns a column
   const int cta = blockIdx.x;
   const int ctas = gridDim.x;
   const int col = cta * T + tid;
@@ -118,10 +120,6 @@ __global__ void __launch_bounds__(kThreadsAll, PM <= 16 ? 2 : 1) solve_kernel(KP
   float* scratch = Ds + (stageD ? vecF : 0);         // partial sums, pending iterates, epilogue
 
   // ---- independent of the previous kernel ----
-  for (int i = tid; i < kStopSlots * (kWarps + 1); i += NT) {
-    if (i < kStopSlots * kWarps) stop_s.part[i / kWarps][i % kWarps] = 0ull;
-    else stop_s.dec[i - kStopSlots * kWarps] = 0ull;
-  }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&pbar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -306,127 +304,71 @@ __global__ void __launch_bounds__(kThreadsAll, PM <= 16 ? 2 : 1) solve_kernel(KP
     float beta_next = __ldg(kp.beta);
     int rs = 0;            // restart: iterations since this vector's last restart
     float obj_prev = 0.f;  // restart: this vector's previous objective
-    float* keep = scratch;  // [kKeep][PM][T]: iterates whose stop test is pending (per thread)
+    float* keep = scratch;  // [kBlockU][PM][T]: iterates of the block's tests (per thread)
     const float inv_Lc = 1.f / Lc;
     constexpr bool test = TEST;
     const double eps2 = ctrl->eps2;
-    int tests = 0, stop_j = -1;  // tests: posted so far
-    int checked = 0;             // decisions read so far
-    int made = 0;                // tests computed (made - tests: the one whose warp sum is deferred)
-    float pend = 0.f;            // this column's ||P grad||^2 term of that test
+    const float eps2_f = eps2 < 0.0 ? 0.f : __double2float_rd(eps2);  // eps^2 rounded down to float
+    int stop_j = -1, nrec = 0, base = 0;  // tests: recorded in this block, decided before it
     bool aborted = false;
-    if (!colthr) {
-      // collector warp
-      const int ntests = test ? max(0, a.max_inner - a.min_inner + 1) : 0;
-      if (!collector_loop(stop_s, a.stop_slots, ntests, a.epoch, eps2, ctrl, kp.wait_ns, kp.withhold != 0,
-                          ctas)) {
-        aborted = true;
-        if ((tid & 31) == 0) {
-          set_status(ctrl, NMF_ERR_DEVICE_TIMEOUT);
-          *((volatile int*)&ctrl->abort) = 1;
-        }
-      }
-    } else {
-      for (int k = 0; k < a.max_inner; ++k) {
+    for (int k = 0; k < a.max_inner; ++k) {
 #pragma unroll
-        for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
-        float beta = beta_next;
-        if (k + 1 < a.max_inner) beta_next = __ldg(kp.beta + k + 1);  // in flight during the product
-        // the deferred test's warp sum, independent of this product
-        const float ws = test ? warp_sum(pend) : 0.f;
-        float gf[PM];
-        if constexpr (packed) hmatvec_packed<PM>(Hp, f, b, gf);
-        else hmatvec<PM>(Hs, f, b, gf);
-        if (RESTART) {
-          // adaptive restart: this vector's objective 1/2 f^T H f - b^T f = 1/2 f^T (gf - b);
-          // when it rises the vector drops its momentum (beta_0 = 0 now, beta_1 next)
-          // a rise counts beyond kRestartTol of the terms' scale (float32 rounding stays below it)
-          float obj = 0.f, sc = 0.f;
-#pragma unroll
-          for (int c = 0; c < PM; ++c) {
-            obj = fmaf(f[c], gf[c] - b[c], obj);
-            sc = fmaf(fabsf(f[c]), fabsf(gf[c]) + fabsf(b[c]), sc);
-          }
-          obj *= 0.5f;
-          if (k >= 1 && obj - obj_prev > kRestartTol * sc) rs = 0;
-          obj_prev = obj;
-          beta = __ldg(kp.beta + rs);
-          ++rs;
-        }
+      for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
+      float beta = beta_next;
+      if (k + 1 < a.max_inner) beta_next = __ldg(kp.beta + k + 1);  // in flight during the product
+      float gf[PM];
+      if constexpr (packed) hmatvec_packed<PM>(Hp, f, b, gf);
+      else hmatvec<PM>(Hs, f, b, gf);
+      if (RESTART) {
+        // adaptive restart: this vector's objective 1/2 f^T H f - b^T f = 1/2 f^T (gf - b);
+        // when it rises the vector drops its momentum (beta_0 = 0 now, beta_1 next)
+        // a rise counts beyond kRestartTol of the terms' scale (float32 rounding stays below it)
+        float obj = 0.f, sc = 0.f;
 #pragma unroll
         for (int c = 0; c < PM; ++c) {
-          y[c] = fmaf(beta, f[c] - fp[c], f[c]);
-          g[c] = fmaf(beta, gf[c] - gp[c], gf[c]);
-          fp[c] = f[c];
-          gp[c] = gf[c];
+          obj = fmaf(f[c], gf[c] - b[c], obj);
+          sc = fmaf(fabsf(f[c]), fabsf(gf[c]) + fabsf(b[c]), sc);
         }
-        iters = k + 1;
-        if (test && made > tests) {
-          // post the deferred test, then read the decision kLag tests back
-          if ((tid & 31) == 0)
-            *((volatile unsigned long long*)&stop_s.part[tests % kStopSlots][tid >> 5]) =
-                stop_word(tests, __float_as_uint(ws));
-          ++tests;
-          if (tests > kLag) {
-            const int j = checked++;  // decisions are read in order, kLag tests behind
-            const int d = wait_decision(stop_s, j, ctrl, kp.wait_ns);
-            if (d < 0) {
-              give_up(ctrl);
-              aborted = true;
-              break;
-            }
-            if (d) {
-              stop_j = j;
-              break;
-            }
-          }
-        }
-        if (test && k + 1 >= a.min_inner) {
-          // this iterate's test: its term now, its warp sum next iteration
-          pend = active ? pg_sq<PM>(f, gf) : 0.f;
-          float* slot = keep + (size_t)(made % kKeep) * PM * T;
+        obj *= 0.5f;
+        if (k >= 1 && obj - obj_prev > kRestartTol * sc) rs = 0;
+        obj_prev = obj;
+        beta = __ldg(kp.beta + rs);
+        ++rs;
+      }
 #pragma unroll
-          for (int c = 0; c < PM; ++c) slot[c * T + tid] = f[c];
-          ++made;
-        }
+      for (int c = 0; c < PM; ++c) {
+        y[c] = fmaf(beta, f[c] - fp[c], f[c]);
+        g[c] = fmaf(beta, gf[c] - gp[c], gf[c]);
+        fp[c] = f[c];
+        gp[c] = gf[c];
       }
-      if (test && stop_j < 0 && !aborted && made > tests) {
-        // the last test's warp sum
-        const float ws = warp_sum(pend);
-        if ((tid & 31) == 0)
-          *((volatile unsigned long long*)&stop_s.part[tests % kStopSlots][tid >> 5]) =
-              stop_word(tests, __float_as_uint(ws));
-        ++tests;
-      }
-      if (test && stop_j < 0 && !aborted) {
-        // tests still pending when the loop ended, in order
-        for (int j = checked; j < tests; ++j) {
-          const int d = wait_decision(stop_s, j, ctrl, kp.wait_ns);
-          if (d < 0) {
-              give_up(ctrl);
-              aborted = true;
-              break;
-            }
-          if (d) {
-            stop_j = j;
+      iters = k + 1;
+      if (test && k + 1 >= a.min_inner) {
+        stop_record<PM>(stop_s, nrec, active ? pg_sq<PM>(f, gf) : 0.f, f, keep, eps2_f);
+        if (++nrec == kBlockU || k + 1 == a.max_inner) {
+          const int r = stop_decide(stop_s, nrec, base, a.stop_slots, a.epoch, eps2, eps2_f, ctas,
+                                    kp.withhold != 0, ctrl, kp.wait_ns);
+          if (r == -2) {
+            aborted = true;
             break;
           }
+          if (r >= 0) {
+            // the first test that passed: its iterate, as the sequential rule returns it
+            const float* slot = keep + (size_t)r * PM * T;
+#pragma unroll
+            for (int c = 0; c < PM; ++c) f[c] = slot[c * T + tid];
+            stop_j = base + r;
+            break;
+          }
+          base += nrec;
+          nrec = 0;
         }
       }
     }
-    if (__syncthreads_or(aborted)) return;
-    if (colthr && stop_j >= 0) {
-      const float* slot = keep + (size_t)(stop_j % kKeep) * PM * T;
-#pragma unroll
-      for (int c = 0; c < PM; ++c) f[c] = slot[c * T + tid];
-      iters = a.min_inner + stop_j;
-    }
-    // every compute thread reached the same decision; broadcast it to the collector
-    if (tid == 0) flag_s = stop_j;
-    __syncthreads();
-    stop_j = flag_s;
+    if (aborted) return;  // every thread saw the same outcome
+    if (stop_j >= 0) iters = a.min_inner + stop_j;
     if (stop_j >= 0) {
-      pg2_final = cta == 0 ? stop_s.dec_tot[stop_j % kStopSlots] : 0.0;  // the total is global: CTA 0 carries it
+      pg2_final = cta == 0 ? stop_s.total : 0.0;  // the total is global: CTA 0 carries it
     } else {
       pg2_final = block_sum_df(active ? pg_sq<PM>(fp, gp) : 0.f, red);  // thread 0
     }
@@ -541,7 +483,7 @@ size_t dyn_smem(const SolveArgs& a, int mode) {
     // partials, their sum, and the slice sums (reused as the eigenvalue scratch)
     scratch = (size_t)a.groups_in * P4 + P4 + std::max({(size_t)4 * kThreadsAll, P4, (size_t)2 * PM * lam_stride<PM>()});
   }
-  if (mode == MODE_SOLVE && a.stop_test) scratch = std::max(scratch, (size_t)kKeep * PM * T);
+  if (mode == MODE_SOLVE && a.stop_test) scratch = std::max(scratch, (size_t)kBlockU * PM * T);
   if (a.epi != EPI_NONE) scratch = std::max(scratch, (size_t)PM * kFs);
   const size_t vecF = round_up_sz((size_t)a.nu * kFs, 4);
   return ((epiW ? vecF : 0) + (stageD ? vecF : 0) + scratch) * sizeof(float);

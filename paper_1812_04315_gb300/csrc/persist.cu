@@ -17,10 +17,8 @@
 //              bit for bit): G side W = F R (p x nu), F side W = (L G)^T;
 //     prepare  H = W W^T, L_c = lambda_max(H), b_j = W d_j per column;
 //     solve    the inner loop of Sec. 2 on the CTA's columns, with the
-//              projected-gradient stop test across CTAs (stop_test.cuh): the
-//              decisions are read as they arrive and waited for only when
-//              kLagP tests are pending, so the global round trip of a test
-//              overlaps up to kLagP iterations;
+//              projected-gradient stop test across CTAs (stop_test.cuh),
+//              taken in blocks of kBlockP tests;
 //     share    this CTA's part of the other side's W (G side: sum_j g_j l_j^T;
 //              F side: sum_j f_j r_j^T), then its arrival at the barrier.
 //
@@ -57,7 +55,7 @@ struct PArgs {
   double* initF;      // [ctasF]
   unsigned long long* slots;  // [max_inner][C] stop-test words (zeroed per call)
   unsigned int* bar;          // barrier arrivals (zeroed per call)
-  float* keep;                // [C][kKeepP][PM][T] pending iterates, or null: in shared memory
+  float* keep;                // [C][kBlockP][PM][T] kept iterates, or null: in shared memory
   float* record_G;            // optional [max_outer][n][p]
   float* record_F;            // optional [max_outer][p][m]
   unsigned long long* times;  // optional [max_outer + 1]
@@ -70,9 +68,7 @@ struct PArgs {
   int ctasG, ctasF;
 };
 
-constexpr int kLagP = 16;            // stop-test decisions pending before a compute warp waits
-constexpr int kKeepP = kLagP + 2;    // iterates kept until their decision is read
-static_assert(kStopSlots >= 2 * kLagP + 1, "stop-test slots are reused after kStopSlots tests");
+constexpr int kBlockP = kMaxStopBlock;  // stop tests per block (their iterates are kept)
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
@@ -222,7 +218,6 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
   Control* ctrl = a.ctrl;
   const int p = a.p, nu = a.nu;
   const int tid = threadIdx.x, NT = blockDim.x;
-  const bool colthr = tid < T;
   const int cta = blockIdx.x, C = gridDim.x;
   const int c0 = cta * T;
   const int P4 = partial_stride(p * nu);
@@ -230,7 +225,7 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
   __shared__ __align__(16) float Hs[PM * PM];
   __shared__ float Ws[PM * kWs];
   __shared__ float2 red[kThreadsAll / 32];
-  __shared__ int flag_s, ok_s;
+  __shared__ int ok_s;
   __shared__ StopShared stop_s;
   __shared__ double lam_s, eps2_s;
   __shared__ __align__(16) float lam_dg[2 * PM];
@@ -243,7 +238,7 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
   float* const EG = DF + vecF;             // columns of L (basis vectors of the G side's share)
   float* const EF = EG + vecF;             // rows of R
   float* const scratch = EF + vecF;        // reductions, eigenvalue scratch, pending iterates
-  float* keep = a.keep ? a.keep + (size_t)cta * kKeepP * PM * T : scratch;
+  float* keep = a.keep ? a.keep + (size_t)cta * kBlockP * PM * T : scratch;
 
   if (call_failed(ctrl)) return;
   // ---- resident data: factors, data and basis vectors of the CTA's columns ----
@@ -265,10 +260,6 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
     EG[k * kFs + t] = g ? __ldg(a.L + (size_t)k * a.n + c0 + t) : 0.f;
     DF[k * kFs + t] = f ? __ldg(a.XL + (size_t)k * a.m + c0 + t) : 0.f;
   }
-  for (int i = tid; i < kStopSlots * (kWarps + 1); i += NT) {
-    if (i < kStopSlots * kWarps) stop_s.part[i / kWarps][i % kWarps] = 0ull;
-    else stop_s.dec[i - kStopSlots * kWarps] = 0ull;
-  }
   __syncthreads();
 
   unsigned int rounds = 0;  // barrier arrivals so far (the same count in every CTA)
@@ -288,7 +279,7 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
       stage_shares(s == 0 ? a.partF : a.partG, G, P4, scratch);
       sum_shares(scratch, G, P4, Rw, Red);
       form_h<PM>(Rw, p, nu, Ws, Hs);
-      const bool active = colthr && c0 + tid < (s == 0 ? a.n : a.m);
+      const bool active = c0 + tid < (s == 0 ? a.n : a.m);
       const float* Y = s == 0 ? YG : YF;
       float y[PM], b[PM], g[PM];
       float pg = 0.f;
@@ -339,7 +330,7 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
       const int col = c0 + tid;
       const int ctas_s = s == 0 ? a.ctasG : a.ctasF;
       const bool mine = cta < ctas_s;  // this CTA has columns on this side
-      const bool active = colthr && col < (s == 0 ? a.n : a.m);
+      const bool active = col < (s == 0 ? a.n : a.m);
       const int epoch = 2 * t + 1 + s;
       float* const Y = s == 0 ? YG : YF;
       float* Rw = scratch + (size_t)C * P4;
@@ -390,126 +381,66 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
         int rs = 0;
         float obj_prev = 0.f;
         const float inv_Lc = 1.f / Lc;
-        int tests = 0, stop_j = -1, made = 0, checked = 0;
-        float pend = 0.f;
+        const float eps2_f = eps2 < 0.0 ? 0.f : __double2float_rd(eps2);  // eps^2 rounded down to float
+        int stop_j = -1, nrec = 0, base = 0;  // tests: recorded in this block, decided before it
         bool aborted = false;
-        if (!colthr) {
-          const int ntests = TEST ? max(0, a.max_inner - a.min_inner + 1) : 0;
-          if (!collector_loop(stop_s, a.slots, ntests, epoch, eps2, ctrl, a.wait_ns, a.withhold != 0, ctas_s)) {
-            aborted = true;
-            if ((tid & 31) == 0) {
-              set_status(ctrl, NMF_ERR_DEVICE_TIMEOUT);
-              *((volatile int*)&ctrl->abort) = 1;
-            }
-          }
-        } else {
-          for (int k = 0; k < a.max_inner; ++k) {
+        for (int k = 0; k < a.max_inner; ++k) {
 #pragma unroll
-            for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
-            float beta = beta_next;
-            if (k + 1 < a.max_inner) beta_next = __ldg(a.beta + k + 1);
-            const float ws = TEST ? warp_sum(pend) : 0.f;
-            float gf[PM];
-            if constexpr (packed) hmatvec_packed<PM>(Hp, f, b, gf);
-            else hmatvec<PM>(Hs, f, b, gf);
-            if (RESTART) {
-              float obj = 0.f, sc = 0.f;
-#pragma unroll
-              for (int c = 0; c < PM; ++c) {
-                obj = fmaf(f[c], gf[c] - b[c], obj);
-                sc = fmaf(fabsf(f[c]), fabsf(gf[c]) + fabsf(b[c]), sc);
-              }
-              obj *= 0.5f;
-              if (k >= 1 && obj - obj_prev > kRestartTol * sc) rs = 0;
-              obj_prev = obj;
-              beta = __ldg(a.beta + rs);
-              ++rs;
-            }
+          for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
+          float beta = beta_next;
+          if (k + 1 < a.max_inner) beta_next = __ldg(a.beta + k + 1);
+          float gf[PM];
+          if constexpr (packed) hmatvec_packed<PM>(Hp, f, b, gf);
+          else hmatvec<PM>(Hs, f, b, gf);
+          if (RESTART) {
+            float obj = 0.f, sc = 0.f;
 #pragma unroll
             for (int c = 0; c < PM; ++c) {
-              y[c] = fmaf(beta, f[c] - fp[c], f[c]);
-              g[c] = fmaf(beta, gf[c] - gp[c], gf[c]);
-              fp[c] = f[c];
-              gp[c] = gf[c];
+              obj = fmaf(f[c], gf[c] - b[c], obj);
+              sc = fmaf(fabsf(f[c]), fabsf(gf[c]) + fabsf(b[c]), sc);
             }
-            iters = k + 1;
-            if (TEST && made > tests) {
-              if ((tid & 31) == 0)
-                *((volatile unsigned long long*)&stop_s.part[tests % kStopSlots][tid >> 5]) =
-                    stop_word(tests, __float_as_uint(ws));
-              ++tests;
-              // read every decision already posted, in order; wait only when
-              // kLagP tests are pending (their iterates fill the kept slots)
-              while (checked < tests) {
-                int d = poll_decision(stop_s, checked);
-                if (d == -2) {
-                  if (tests - checked <= kLagP) break;
-                  d = wait_decision(stop_s, checked, ctrl, a.wait_ns);
-                  if (d < 0) {
-                    give_up(ctrl);
-                    aborted = true;
-                    break;
-                  }
-                }
-                if (d) {
-                  stop_j = checked;
-                  break;
-                }
-                ++checked;
-              }
-              if (aborted || stop_j >= 0) break;
-            }
-            if (TEST && k + 1 >= a.min_inner) {
-              pend = active ? pg_sq<PM>(f, gf) : 0.f;
-              float* slot = keep + (size_t)(made % kKeepP) * PM * T;
+            obj *= 0.5f;
+            if (k >= 1 && obj - obj_prev > kRestartTol * sc) rs = 0;
+            obj_prev = obj;
+            beta = __ldg(a.beta + rs);
+            ++rs;
+          }
 #pragma unroll
-              for (int c = 0; c < PM; ++c) slot[c * T + tid] = f[c];
-              ++made;
-            }
+          for (int c = 0; c < PM; ++c) {
+            y[c] = fmaf(beta, f[c] - fp[c], f[c]);
+            g[c] = fmaf(beta, gf[c] - gp[c], gf[c]);
+            fp[c] = f[c];
+            gp[c] = gf[c];
           }
-          if (TEST && stop_j < 0 && !aborted && made > tests) {
-            const float ws = warp_sum(pend);
-            if ((tid & 31) == 0)
-              *((volatile unsigned long long*)&stop_s.part[tests % kStopSlots][tid >> 5]) =
-                  stop_word(tests, __float_as_uint(ws));
-            ++tests;
-          }
-          if (TEST && stop_j < 0 && !aborted) {
-            for (int j = checked; j < tests; ++j) {
-              const int d = wait_decision(stop_s, j, ctrl, a.wait_ns);
-              if (d < 0) {
-                give_up(ctrl);
+          iters = k + 1;
+          if (TEST && k + 1 >= a.min_inner) {
+            stop_record<PM>(stop_s, nrec, active ? pg_sq<PM>(f, gf) : 0.f, f, keep, eps2_f);
+            if (++nrec == kBlockP || k + 1 == a.max_inner) {
+              const int r = stop_decide(stop_s, nrec, base, a.slots, epoch, eps2, eps2_f, ctas_s, a.withhold != 0,
+                                        ctrl, a.wait_ns);
+              if (r == -2) {
                 aborted = true;
                 break;
               }
-              if (d) {
-                stop_j = j;
+              if (r >= 0) {
+                // the first test that passed: its iterate, as the sequential rule returns it
+                const float* slot = keep + (size_t)r * PM * T;
+#pragma unroll
+                for (int c = 0; c < PM; ++c) f[c] = slot[c * T + tid];
+                stop_j = base + r;
                 break;
               }
+              base += nrec;
+              nrec = 0;
             }
           }
         }
-        if (__syncthreads_or(aborted)) return;
-        if (colthr && stop_j >= 0) {
-          const float* slot = keep + (size_t)(stop_j % kKeepP) * PM * T;
-#pragma unroll
-          for (int c = 0; c < PM; ++c) f[c] = slot[c * T + tid];
-          iters = a.min_inner + stop_j;
-        }
-        if (tid == 0) flag_s = stop_j;
-        __syncthreads();
-        stop_j = flag_s;
+        if (aborted) return;  // every thread saw the same outcome
+        if (stop_j >= 0) iters = a.min_inner + stop_j;
         // ||P grad||^2 of the returned iterate: only the last update's
         // reaches the statistics
-        if (stop_j >= 0) pg2_final = cta == 0 ? stop_s.dec_tot[stop_j % kStopSlots] : 0.0;
+        if (stop_j >= 0) pg2_final = cta == 0 ? stop_s.total : 0.0;
         else if (t == a.max_outer - 1) pg2_final = block_sum_df(active ? pg_sq<PM>(fp, gp) : 0.f, red);
-        // the stop-test words of this CTA's shared slots are tagged by test
-        // index only: clear them for the next phase (every warp is past them)
-        __syncthreads();
-        for (int i = tid; i < kStopSlots * (kWarps + 1); i += NT) {
-          if (i < kStopSlots * kWarps) stop_s.part[i / kWarps][i % kWarps] = 0ull;
-          else stop_s.dec[i - kStopSlots * kWarps] = 0ull;
-        }
       }
       // ---- outputs of the phase ----
       if (active) {
@@ -571,7 +502,7 @@ size_t persist_smem(int nu, int p, int ctas, bool keep_shared) {
   const size_t P4 = partial_stride(p * nu);
   // staged shares, their sum, and the slice sums (reused as the eigenvalue scratch)
   size_t scratch = (size_t)ctas * P4 + P4 + std::max({(size_t)4 * kThreadsAll, P4, (size_t)2 * PM * lam_stride<PM>()});
-  if (keep_shared) scratch = std::max(scratch, (size_t)kKeepP * PM * T);
+  if (keep_shared) scratch = std::max(scratch, (size_t)kBlockP * PM * T);
   return ((size_t)2 * PM * kFs + 4 * vecF + scratch) * sizeof(float);
 }
 
@@ -621,6 +552,7 @@ PersistPlan persist_plan(int n, int m, int p, int nu, bool test, bool restart) {
   pl.ctas = C;
   pl.PM = pad_rank_p(p);
   if ((long)C * P4 > kMaxReduceFloats) return pl;  // every CTA reads every share: keep that small
+  if (C > kMaxStopCtas) return pl;
   int dev = 0, max_smem = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return pl;
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -642,7 +574,7 @@ PersistPlan persist_plan(int n, int m, int p, int nu, bool test, bool restart) {
 
 size_t persist_keep_floats(int n, int m, int p, int nu) {
   const PersistPlan pl = persist_plan(n, m, p, nu, true, false);
-  return pl.ok && !pl.keep_shared ? (size_t)pl.ctas * kKeepP * pl.PM * T : 0;
+  return pl.ok && !pl.keep_shared ? (size_t)pl.ctas * kBlockP * pl.PM * T : 0;
 }
 
 cudaError_t persist_launch(const PersistPlan& pl, const PersistLaunch& L, cudaStream_t s) {
