@@ -93,6 +93,11 @@ namespace {
 // The second CholeskyQR pass is skipped when the first pass's basis has a
 // Gram matrix within this of I (every entry, float-float value).
 constexpr float kSecondPassSkip = 1e-6f;
+// One CholeskyQR pass is taken when the first factorisation did not shift and
+// its pivots span less than this ratio: kappa(Y)^2 of about that size, so the
+// float-float Gram leaves Q orthonormal to ~3e7 x 2^-48 ~ 1e-7, below the
+// 1e-6 at which the second pass would keep Q anyway.
+constexpr float kSinglePassPivotRatio = 3e7f;
 
 // ----------------------------------------------------------------------------
 // nmf_compress workspace
@@ -161,7 +166,7 @@ nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16
                             float* XLout, cudaStream_t s) {
   Control* ctrl = w.ctrl;
   const int NV = w.plan.NV;
-  NMF_CU(cudaMemsetAsync(ctrl->flags, 0, 2 * sizeof(int), s));
+  NMF_CU(cudaMemsetAsync(ctrl->flags, 0, 4 * sizeof(int), s));  // shift flags, single-pass flags
   RowJob r1[2] = {}, r2[2] = {}, r3[2] = {}, r4[2] = {};
   int k = 0;
   for (int t = 0; t < 2; ++t) {
@@ -193,6 +198,12 @@ nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16
     // about float32 rounding unless Y is ill conditioned: then the second
     // pass would change Q1 by as little, and is skipped
     c.skip_tol = kSecondPassSkip;
+    // apply 1 may find one pass enough: it then writes apply 2's outputs and
+    // apply 2 (and the third pass, whose shift flag stays down) do nothing
+    b.single_ratio = kSinglePassPivotRatio;
+    b.single_flag = &ctrl->flags[2 + t];
+    b.Y_final = c.Y; b.Yt_final = c.Yt; b.op_final = c.op; b.ldop = c.ldop; b.op_bf16 = c.op_bf16;
+    c.skip_flag = &ctrl->flags[2 + t];
     // apply 3, in place, only where a shift was taken
     RowJob& d = r4[k];
     d = c;

@@ -109,8 +109,18 @@ struct RowJob {
   int gram_on_shift;    // form gram_part when *shift_flag (as read) or this factorisation shifted
   int* shift_flag;      // apply step: raised (by CTA 0) when the factorisation needed the shift
   const int* run_flag;  // optional: skip the job unless *run_flag != 0
+  const int* skip_flag; // optional: skip the job when *skip_flag != 0
   int diag_only;        // apply step: R = diag(sqrt(S_cc)) (columns rescaled to unit norm, span kept)
   float skip_tol;       // apply step: keep src as it is when its Gram is within this of I (0: never)
+  // apply step, one pass enough: when the factorisation did not shift and the
+  // ratio of its largest to smallest pivot is below single_ratio, the rows
+  // go to the final outputs below (not Y, Yt, op, no Gram partial) and
+  // *single_flag is raised (so the next pass can skip); 0: never
+  float single_ratio;
+  int* single_flag;
+  float* Y_final;
+  float* Yt_final;
+  void* op_final;
 };
 
 cudaError_t rows_launch(const RowJob* jobs, int njobs, Control* ctrl, cudaStream_t s);

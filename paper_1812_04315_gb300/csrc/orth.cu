@@ -91,10 +91,11 @@ __device__ __forceinline__ void tri_index(int e, int nu, int& a, int& b) {
 // Sum of the Gram partials (fixed order), float-float Cholesky S = R^T R and
 // the float-float inverse R^{-1}, redundantly in every CTA. Leaves R^{-1}
 // (upper, stride kAs) in (Ihi, Ilo). Returns 0 (ok), 1 (ok, shifted), 2 (S
-// within skip_tol of I: R = I, nothing left in Ihi, Ilo) or -1 (failure:
+// within skip_tol of I: R = I, nothing left in Ihi, Ilo), 3 (ok, not
+// shifted, largest / smallest pivot below single_ratio) or -1 (failure:
 // status set).
 __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, float* Ahi, float* Alo, float* Ihi,
-                           float* Ilo, Control* ctrl, bool diag_only, float skip_tol) {
+                           float* Ilo, Control* ctrl, bool diag_only, float skip_tol, float single_ratio) {
   __shared__ float maxdiag_s, trace_s;
   __shared__ float Sdiag[NMF_MAX_SKETCH], Sdiag_lo[NMF_MAX_SKETCH];
   __shared__ float Dinv_hi[NMF_MAX_SKETCH], Dinv_lo[NMF_MAX_SKETCH];
@@ -267,6 +268,20 @@ __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, 
     if (tid == 0) set_status(ctrl, NMF_ERR_NOT_SPD);
     return -1;
   }
+  // One pass suffices when S is well conditioned: the pivots of S = U^T D U
+  // bound kappa(Y)^2 from below by max d / min d, and a float-float Gram and
+  // factor leave Q orthonormal to about kappa(Y)^2 2^-48 beside the float32
+  // rounding of its entries. Every thread reads the same pivots.
+  bool single = false;
+  if (!shifted && single_ratio > 0.f) {
+    float dmax = 0.f, dmin = 3.4e38f;
+    for (int j = 0; j < nu; ++j) {
+      const float d = Ahi[j * kAs + j];
+      dmax = fmaxf(dmax, d);
+      dmin = fminf(dmin, d);
+    }
+    single = dmax < single_ratio * dmin;
+  }
   // R = D^{1/2} U, so R^{-1} = U^{-1} D^{-1/2}. U_jk = S'_jk / d_j (strict
   // upper part), and X = U^{-1} starts as the identity.
   for (int e = tid; e < E; e += blockDim.x) {
@@ -310,7 +325,7 @@ __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, 
     Ilo[i * kAs + c] = v.lo;
   }
   __syncthreads();
-  return shifted;
+  return single ? 3 : shifted;
 }
 
 __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control* ctrl) {
@@ -319,6 +334,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
   while (jj + 1 < jobs.njobs && (int)blockIdx.x >= jobs.start[jj + 1]) ++jj;
   const RowJob& J = jobs.j[jj];
   if (J.run_flag && *((volatile const int*)J.run_flag) == 0) return;
+  if (J.skip_flag && *((volatile const int*)J.skip_flag) != 0) return;
   const int cta = blockIdx.x - jobs.start[jj];
   const int r0 = cta * kOrthRows;
   const int rows = min(kOrthRows, J.N - r0);
@@ -334,6 +350,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
   __shared__ int shifted_s;
 
   bool extra_gram = false;
+  bool single = false;  // one pass was enough: the rows go to the final outputs
   if (J.part) {
     // Y = sum over the S partials: four accumulators (partial k feeds
     // accumulator k mod 4, in increasing k), float4 over four columns. A
@@ -407,10 +424,12 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
     // the skip is only taken while no factorisation of this basis has shifted
     const int shifted_before = J.shift_flag ? *((volatile const int*)J.shift_flag) : 0;
     const int sh = factor_gram(J.gram_in, J.gram_parts, nu, Ys, Ahi, Alo, Ihi, Ilo, ctrl, J.diag_only != 0,
-                               shifted_before ? 0.f : J.skip_tol);
+                               shifted_before ? 0.f : J.skip_tol, shifted_before ? 0.f : J.single_ratio);
     if (sh < 0) return;
     const bool keep_rows = sh == 2;
-    if (tid == 0) shifted_s = keep_rows ? 0 : sh;
+    single = sh == 3;
+    if (single && cta == 0 && tid == 0) *J.single_flag = 1;  // every CTA decided alike
+    if (tid == 0) shifted_s = (keep_rows || single) ? 0 : sh;
     __syncthreads();
     if (J.shift_flag) {
       // pass 1 records its shift; later passes add theirs; a shift anywhere
@@ -475,29 +494,32 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
   __syncthreads();
 
   bool bad = false;
-  if (J.Y)
+  float* const outY = single ? J.Y_final : J.Y;
+  float* const outYt = single ? J.Yt_final : J.Yt;
+  void* const outOp = single ? J.op_final : J.op;
+  if (outY)
     for (int i = tid; i < rows * nu; i += kRowThreads) {
       const int r = i / nu, c = i % nu;
       const float v = Ys[r * kYsStride + c];
       bad |= !isfinite(v);
-      J.Y[(size_t)(r0 + r) * nu + c] = v;
+      outY[(size_t)(r0 + r) * nu + c] = v;
     }
-  if (J.Yt)
+  if (outYt)
     for (int i = tid; i < rows * nu; i += kRowThreads) {
       const int c = i / rows, r = i % rows;
-      J.Yt[(size_t)c * J.N + r0 + r] = Ys[r * kYsStride + c];
+      outYt[(size_t)c * J.N + r0 + r] = Ys[r * kYsStride + c];
     }
-  if (J.op)
+  if (outOp)
     for (int i = tid; i < rows * nu; i += kRowThreads) {
       const int c = i / rows, r = i % rows;
       const float v = Ys[r * kYsStride + c];
       if (J.op_bf16)
-        static_cast<__nv_bfloat16*>(J.op)[(size_t)c * J.ldop + r0 + r] = __float2bfloat16_rn(v);
+        static_cast<__nv_bfloat16*>(outOp)[(size_t)c * J.ldop + r0 + r] = __float2bfloat16_rn(v);
       else
-        static_cast<float*>(J.op)[(size_t)c * J.ldop + r0 + r] = v;
+        static_cast<float*>(outOp)[(size_t)c * J.ldop + r0 + r] = v;
     }
   if (bad) set_status(ctrl, NMF_ERR_NONFINITE);
-  if (J.gram_part && (J.gram_always || extra_gram)) {
+  if (J.gram_part && !single && (J.gram_always || extra_gram)) {
     const int E = nu * (nu + 1) / 2;
     const int E2 = gram_stride(nu);
     for (int e = tid; e < E2; e += kRowThreads) {
