@@ -593,10 +593,14 @@ def run_ours(args):
     h2d = X.nbytes + G0.nbytes + F0.nbytes
     d2h = G0.nbytes + F0.nbytes
 
-    # ---- roofline of the dominant kernel: the fused inner solve ----
-    # nenmf_solve = a few set-up launches + 2T solve launches; the per-launch
-    # time is the live-timed solve call divided by its 2T solve launches.
-    solve_launch_ms = ms_solve / (2 * T)
+    # ---- roofline of the dominant kernel: the persistent compressed solve ----
+    # nenmf_solve = a few set-up kernels + one persistent launch that runs all
+    # T outer iterations (2T factor updates); the launch time is taken as the
+    # live-timed solve call. Algorithmic bytes: every update's operands (the
+    # factor columns read and written, the compressed data and basis vectors),
+    # as the per-update kernels stream them; the persistent kernel loads them
+    # once and keeps them in shared memory, so its DRAM traffic is far lower.
+    launches_per_solve = 1
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -604,13 +608,16 @@ def run_ours(args):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    sbytes = solve_kernel_bytes(n, m, p, nu)
-    achieved = sbytes / (solve_launch_ms / 1e3) / 1e9
-    roofline = {"kernel": "solve_kernel (fused Nesterov inner loop, Sec. 2 / Alg. 1)", "bound": "hbm",
-                "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 5), "traffic": profile_traffic("solve_kernel"),
-                "algorithmic_bytes_per_launch": sbytes, "launch_ms": round(solve_launch_ms, 5),
-                "peak_source": peak_src}
+    sbytes = 2 * T * solve_kernel_bytes(n, m, p, nu)
+    launch_ms = ms_solve / launches_per_solve
+    achieved = sbytes / (launch_ms / 1e3) / 1e9
+    roofline = {"kernel": "persist_kernel (Alg. 1: all outer iterations, fused Nesterov inner loop of Sec. 2)",
+                "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 5), "traffic": profile_traffic("persist_kernel"),
+                "algorithmic_bytes_per_launch": sbytes, "launch_ms": round(launch_ms, 5),
+                "updates_per_launch": 2 * T, "peak_source": peak_src,
+                "note": "latency bound: operands stay in shared memory after one load, so DRAM traffic is "
+                        "far below the algorithmic bytes"}
 
     result = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
