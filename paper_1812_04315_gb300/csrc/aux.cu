@@ -68,7 +68,8 @@ __global__ void to_bf16_kernel(const float* X, int n, int m, __nv_bfloat16* Xb, 
   }
 }
 
-__global__ void transpose_kernel(const float* in, int R, int C, void* out, int ldo, int out_bf16, Control* ctrl) {
+__global__ void transpose_kernel(const float* in, int R, int C, void* out, int ldo, int fmt, size_t part_stride,
+                                 Control* ctrl) {
   if (ctrl && call_failed(ctrl)) return;
   __shared__ float tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -80,22 +81,19 @@ __global__ void transpose_kernel(const float* in, int R, int C, void* out, int l
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int c = c0 + i, r = r0 + threadIdx.x;
     if (c < C && r < R) {
-      const float v = tile[threadIdx.x][i];
-      if (out_bf16) static_cast<__nv_bfloat16*>(out)[(size_t)c * ldo + r] = __float2bfloat16_rn(v);
-      else static_cast<float*>(out)[(size_t)c * ldo + r] = v;
+      store_op(out, (size_t)c * ldo + r, fmt, part_stride, tile[threadIdx.x][i]);
     }
   }
 }
 
-__global__ void copy_rows_kernel(const float* in, int rows, int cols, void* out, int ldo, int out_bf16,
-                                 Control* ctrl) {
+__global__ void copy_rows_kernel(const float* in, int rows, int cols, void* out, int ldo, int fmt,
+                                 size_t part_stride, Control* ctrl) {
   if (ctrl && call_failed(ctrl)) return;
   const long long total = (long long)rows * cols;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(i / cols), c = (int)(i % cols);
-    if (out_bf16) static_cast<__nv_bfloat16*>(out)[(size_t)r * ldo + c] = __float2bfloat16_rn(in[i]);
-    else static_cast<float*>(out)[(size_t)r * ldo + c] = in[i];
+    store_op(out, (size_t)r * ldo + c, fmt, part_stride, in[i]);
   }
 }
 
@@ -216,18 +214,19 @@ cudaError_t to_bf16_launch(const float* X, int n, int m, __nv_bfloat16* Xb, int 
   return cudaGetLastError();
 }
 
-cudaError_t transpose_launch(const float* in, int R, int C, void* out, int ldo, int out_bf16, Control* ctrl,
-                             cudaStream_t s) {
+cudaError_t transpose_launch(const float* in, int R, int C, void* out, int ldo, int fmt, Control* ctrl,
+                             cudaStream_t s, size_t part_stride) {
   dim3 grid(ceil_div(C, 32), ceil_div(R, 32));
   count_launches(1);
-  transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(in, R, C, out, ldo, out_bf16, ctrl);
+  transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(in, R, C, out, ldo, fmt, part_stride, ctrl);
   return cudaGetLastError();
 }
 
-cudaError_t copy_rows_launch(const float* in, int rows, int cols, void* out, int ldo, int out_bf16, Control* ctrl,
-                             cudaStream_t s) {
+cudaError_t copy_rows_launch(const float* in, int rows, int cols, void* out, int ldo, int fmt, Control* ctrl,
+                             cudaStream_t s, size_t part_stride) {
   count_launches(1);
-  copy_rows_kernel<<<grid_for((long long)rows * cols, 256), 256, 0, s>>>(in, rows, cols, out, ldo, out_bf16, ctrl);
+  copy_rows_kernel<<<grid_for((long long)rows * cols, 256), 256, 0, s>>>(in, rows, cols, out, ldo, fmt, part_stride,
+                                                                          ctrl);
   return cudaGetLastError();
 }
 

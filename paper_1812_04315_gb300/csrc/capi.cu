@@ -31,6 +31,10 @@ bool ws_ok(const void* ws, size_t bytes, size_t need) {
 }
 
 bool use_tc(nmf_prec_t prec) { return prec == NMF_PREC_BF16 && !g_force_simt && xpass_tc_available(); }
+// float32 passes as three bfloat16 parts on the tensor cores (widths up to kSplitMaxNV)
+bool use_split(nmf_prec_t prec, int nu) {
+  return prec == NMF_PREC_FP32 && !g_force_simt && round_up(nu, 16) <= nmf::kSplitMaxNV && xpass_tc_available();
+}
 
 }  // namespace
 
@@ -66,18 +70,20 @@ cudaError_t allow_dynamic_smem(const void* kernel, int bytes) {
 
 int device_sm_count() { return sm_count(); }
 
-XPassPlan xpass_plan(int n, int m, int nu, nmf_prec_t prec, int num_sms) {
-  if (use_tc(prec)) return xpass_tc_plan(n, m, nu, num_sms);
+XPassPlan xpass_plan(int n, int m, int nu, nmf_prec_t prec, int num_sms, bool split_ok) {
+  if (use_tc(prec)) return xpass_tc_plan(n, m, nu, num_sms, 1);
+  if (split_ok && use_split(prec, nu)) return xpass_tc_plan(n, m, nu, num_sms, 3);
   return xpass_simt_plan(n, m, nu, num_sms);
 }
 
 cudaError_t xpass_launch(const XPassPlan& plan, const XPassArgs& a, nmf_prec_t prec, cudaStream_t s) {
-  if (use_tc(prec)) return xpass_tc_launch(plan, a, s);
+  if (plan.tiled) return xpass_tc_launch(plan, a, s);
   return xpass_simt_launch(plan, a, prec == NMF_PREC_BF16, s);
 }
 
 size_t xb_elems(const XPassPlan& plan, int n, int ldxb) {
-  return plan.tiled ? (size_t)plan.tiles_r * plan.tiles_c * plan.tile_r * plan.tile_c : (size_t)n * ldxb;
+  return plan.tiled ? (size_t)plan.tiles_r * plan.tiles_c * plan.tile_r * plan.tile_c * plan.parts
+                    : (size_t)n * ldxb;
 }
 
 cudaError_t xb_convert(const XPassPlan& plan, const float* X, int n, int m, __nv_bfloat16* Xb, int ldxb,
@@ -126,16 +132,15 @@ CompressWs carve_compress(void* base, int n, int m, int nu, nmf_prec_t prec) {
   Carver cv(base);
   w.plan = xpass_plan(n, m, nu, prec, sm_count());
   const int NV = w.plan.NV;
-  const size_t es = prec == NMF_PREC_BF16 ? 2 : 4;
   w.ctrl = cv.take<Control>(1);
-  if (prec == NMF_PREC_BF16) {
+  if (x_converted(w.plan, prec)) {
     w.ldxb = round_up(m, 64);
     w.Xb = cv.take<__nv_bfloat16>(xb_elems(w.plan, n, w.ldxb));
   }
   w.lda = round_up(m, 128);
   w.ldb = round_up(n, 128);
-  w.opA = cv.take<char>((size_t)NV * w.lda * es);
-  w.opB = cv.take<char>((size_t)NV * w.ldb * es);
+  w.opA = cv.take<char>(op_bytes(w.plan, prec, w.lda));
+  w.opB = cv.take<char>(op_bytes(w.plan, prec, w.ldb));
   w.partN = cv.take<float>((size_t)w.plan.S_c * n * NV);
   w.partT = cv.take<float>((size_t)w.plan.S_r * m * NV);
   for (int i = 0; i < 2; ++i) {
@@ -162,7 +167,7 @@ struct Jobs {
 // pass. Outputs: the next operands (N job -> opB, T job -> opA); with Lout
 // and Rout set, L = Q_N^T and R = Q_T; with XLout set, the T product itself
 // (before orthonormalisation) transposed into XLout.
-nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16, Jobs jb, float* Lout, float* Rout,
+nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, int ofmt, Jobs jb, float* Lout, float* Rout,
                             float* XLout, cudaStream_t s) {
   Control* ctrl = w.ctrl;
   const int NV = w.plan.NV;
@@ -191,7 +196,8 @@ nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16
     float* Q = isN ? Y0 : (Rout ? Rout : Y0);
     RowJob& c = r3[k];
     c.src = Y1; c.gram_in = g1; c.gram_parts = rows_ctas(N); c.N = N; c.nu = nu;
-    c.Y = Q; c.op = isN ? w.opB : w.opA; c.ldop = isN ? w.ldb : w.lda; c.op_bf16 = bf16;
+    c.Y = Q; c.op = isN ? w.opB : w.opA; c.ldop = isN ? w.ldb : w.lda; c.op_fmt = ofmt;
+    c.op_part = (size_t)NV * c.ldop;
     if (isN) c.Yt = Lout;
     c.gram_part = g0; c.gram_on_shift = 1; c.shift_flag = flag;
     // the first pass's float-float Gram and factor leave Q1 orthonormal to
@@ -202,7 +208,8 @@ nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16
     // apply 2 (and the third pass, whose shift flag stays down) do nothing
     b.single_ratio = kSinglePassPivotRatio;
     b.single_flag = &ctrl->flags[2 + t];
-    b.Y_final = c.Y; b.Yt_final = c.Yt; b.op_final = c.op; b.ldop = c.ldop; b.op_bf16 = c.op_bf16;
+    b.Y_final = c.Y; b.Yt_final = c.Yt; b.op_final = c.op; b.ldop = c.ldop; b.op_fmt = c.op_fmt;
+    b.op_part = c.op_part;
     c.skip_flag = &ctrl->flags[2 + t];
     // apply 3, in place, only where a shift was taken
     RowJob& d = r4[k];
@@ -220,7 +227,7 @@ nmf_status_t orthonormalize(const CompressWs& w, int n, int m, int nu, bool bf16
 // The power-iteration variant's step between products: every column of the
 // present products rescaled to unit norm (span unchanged, no
 // orthonormalisation), written as the next operands.
-nmf_status_t normalize_columns(const CompressWs& w, int n, int m, int nu, bool bf16, Jobs jb, cudaStream_t s) {
+nmf_status_t normalize_columns(const CompressWs& w, int n, int m, int nu, int ofmt, Jobs jb, cudaStream_t s) {
   Control* ctrl = w.ctrl;
   const int NV = w.plan.NV;
   RowJob r1[2] = {}, r2[2] = {};
@@ -236,7 +243,7 @@ nmf_status_t normalize_columns(const CompressWs& w, int n, int m, int nu, bool b
     a.Y = Y0; a.gram_part = g0; a.gram_always = 1;
     RowJob& b = r2[k];
     b.src = Y0; b.gram_in = g0; b.gram_parts = rows_ctas(N); b.N = N; b.nu = nu; b.diag_only = 1;
-    b.op = isN ? w.opB : w.opA; b.ldop = isN ? w.ldb : w.lda; b.op_bf16 = bf16;
+    b.op = isN ? w.opB : w.opA; b.ldop = isN ? w.ldb : w.lda; b.op_fmt = ofmt; b.op_part = (size_t)NV * b.ldop;
     ++k;
   }
   NMF_CU(rows_launch(r1, k, ctrl, s));
@@ -315,7 +322,9 @@ SolveWs carve_solve(void* base, const nenmf_problem_t& pr) {
   if (!plain) w.keep = cv.take<float>(persist_keep_floats(n, m, p, nu));
   if (plain) {
     const nmf_prec_t prec = (nmf_prec_t)pr.prec;
-    w.plan = xpass_plan(n, m, p, prec, sm_count());
+    // plain NeNMF's float32 passes stay on CUDA cores: the solve kernels write
+    // their operands as float32 or one bfloat16 part
+    w.plan = xpass_plan(n, m, p, prec, sm_count(), false);
     const size_t es = prec == NMF_PREC_BF16 ? 2 : 4;
     if (prec == NMF_PREC_BF16) {
       w.ldxb = round_up(m, 64);
@@ -366,16 +375,15 @@ DualWs carve_dual(void* base, int n, int m, int k, nmf_prec_t prec) {
   DualWs w{};
   Carver cv(base);
   w.plan = xpass_plan(n, m, k, prec, sm_count());
-  const size_t es = prec == NMF_PREC_BF16 ? 2 : 4;
   w.ctrl = cv.take<Control>(1);
-  if (prec == NMF_PREC_BF16) {
+  if (x_converted(w.plan, prec)) {
     w.ldxb = round_up(m, 64);
     w.Xb = cv.take<__nv_bfloat16>(xb_elems(w.plan, n, w.ldxb));
   }
   w.lda = round_up(m, 128);
   w.ldb = round_up(n, 128);
-  w.opA = cv.take<char>((size_t)w.plan.NV * w.lda * es);
-  w.opB = cv.take<char>((size_t)w.plan.NV * w.ldb * es);
+  w.opA = cv.take<char>(op_bytes(w.plan, prec, w.lda));
+  w.opB = cv.take<char>(op_bytes(w.plan, prec, w.ldb));
   w.partN = cv.take<float>((size_t)w.plan.S_c * n * w.plan.NV);
   w.partT = cv.take<float>((size_t)w.plan.S_r * m * w.plan.NV);
   w.bytes = cv.size();
@@ -453,20 +461,21 @@ nmf_status_t nmf_compress_variant(nmf_stream_t stream, int n, int m, int nu, int
   const CompressWs w = carve_compress(workspace, n, m, nu, prec);
   if (!ws_ok(workspace, workspace_bytes, w.bytes)) return NMF_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
-  const bool bf16 = prec == NMF_PREC_BF16;
-  const size_t es = bf16 ? 2 : 4;
+  const bool xconv = x_converted(w.plan, prec);
+  const int ofmt = op_format(w.plan, prec);
   const int NV = w.plan.NV;
+  const size_t partA = (size_t)NV * w.lda, partB = (size_t)NV * w.ldb;  // OP_BF16X3 part strides
 
   NMF_CU(cudaMemsetAsync(w.ctrl, 0, sizeof(Control), s));
-  NMF_CU(cudaMemsetAsync(w.opA, 0, (size_t)NV * w.lda * es, s));
-  NMF_CU(cudaMemsetAsync(w.opB, 0, (size_t)NV * w.ldb * es, s));
-  if (bf16) NMF_CU(xb_convert(w.plan, X, n, m, w.Xb, w.ldxb, w.ctrl, s));
+  NMF_CU(cudaMemsetAsync(w.opA, 0, op_bytes(w.plan, prec, w.lda), s));
+  NMF_CU(cudaMemsetAsync(w.opB, 0, op_bytes(w.plan, prec, w.ldb), s));
+  if (xconv) NMF_CU(xb_convert(w.plan, X, n, m, w.Xb, w.ldxb, w.ctrl, s));
 
   XPassArgs xa{};
   xa.n = n;
   xa.m = m;
-  xa.X = bf16 ? (const void*)w.Xb : (const void*)X;
-  xa.ldx = bf16 ? w.ldxb : m;
+  xa.X = xconv ? (const void*)w.Xb : (const void*)X;
+  xa.ldx = xconv ? w.ldxb : m;
   xa.opA = w.opA;
   xa.lda = w.lda;
   xa.opB = w.opB;
@@ -507,8 +516,8 @@ nmf_status_t nmf_compress_variant(nmf_stream_t stream, int n, int m, int nu, int
       NMF_CU(sketch_launch(nu, n, seed, 1u, L, s));
       NMF_CU(scale_launch(L, L, (long long)nu * n, sc, s));
     }
-    NMF_CU(transpose_launch(R, m, nu, w.opA, w.lda, bf16, w.ctrl, s));
-    NMF_CU(copy_rows_launch(L, nu, n, w.opB, w.ldb, bf16, w.ctrl, s));
+    NMF_CU(transpose_launch(R, m, nu, w.opA, w.lda, ofmt, w.ctrl, s, partA));
+    NMF_CU(copy_rows_launch(L, nu, n, w.opB, w.ldb, ofmt, w.ctrl, s, partB));
     return closing(both);
   }
 
@@ -518,29 +527,29 @@ nmf_status_t nmf_compress_variant(nmf_stream_t stream, int n, int m, int nu, int
     NMF_CU(sketch_launch(m, nu, seed, 0u, w.omega, s));
     oL = w.omega;
   }
-  NMF_CU(transpose_launch(oL, m, nu, w.opA, w.lda, bf16, w.ctrl, s));
+  NMF_CU(transpose_launch(oL, m, nu, w.opA, w.lda, ofmt, w.ctrl, s, partA));
   const float* oR = omega_R;
   if (!oR) {
     NMF_CU(sketch_launch(nu, n, seed, 1u, w.omega, s));
     oR = w.omega;
   }
-  NMF_CU(copy_rows_launch(oR, nu, n, w.opB, w.ldb, bf16, w.ctrl, s));
+  NMF_CU(copy_rows_launch(oR, nu, n, w.opB, w.ldb, ofmt, w.ctrl, s, partB));
 
   nmf_status_t st = NMF_OK;
   if (variant == NMF_VARIANT_SINGLE_CHAIN) {
     // one chain: Q_L^(0) = orth(X Omega_L); Q~ = orth(X^T Q_L), Q_L = orth(X Q~) q times;
     // L = Q_L^(q)^T; X_L^T = X^T Q_L^(q) and R = orth(X^T Q_L^(q)); X_R = X R
     NMF_CU(xpass_launch(w.plan, xN, prec, s));
-    if ((st = orthonormalize(w, n, m, nu, bf16, onlyN, q == 0 ? L : nullptr, nullptr, nullptr, s)) != NMF_OK) return st;
+    if ((st = orthonormalize(w, n, m, nu, ofmt, onlyN, q == 0 ? L : nullptr, nullptr, nullptr, s)) != NMF_OK) return st;
     for (int k = 1; k <= q; ++k) {
       NMF_CU(xpass_launch(w.plan, xT, prec, s));
-      if ((st = orthonormalize(w, n, m, nu, bf16, onlyT, nullptr, nullptr, nullptr, s)) != NMF_OK) return st;
+      if ((st = orthonormalize(w, n, m, nu, ofmt, onlyT, nullptr, nullptr, nullptr, s)) != NMF_OK) return st;
       NMF_CU(xpass_launch(w.plan, xN, prec, s));
-      if ((st = orthonormalize(w, n, m, nu, bf16, onlyN, k == q ? L : nullptr, nullptr, nullptr, s)) != NMF_OK)
+      if ((st = orthonormalize(w, n, m, nu, ofmt, onlyN, k == q ? L : nullptr, nullptr, nullptr, s)) != NMF_OK)
         return st;
     }
     NMF_CU(xpass_launch(w.plan, xT, prec, s));
-    if ((st = orthonormalize(w, n, m, nu, bf16, onlyT, nullptr, R, XL, s)) != NMF_OK) return st;
+    if ((st = orthonormalize(w, n, m, nu, ofmt, onlyT, nullptr, R, XL, s)) != NMF_OK) return st;
     return closing(onlyN);
   }
 
@@ -553,8 +562,8 @@ nmf_status_t nmf_compress_variant(nmf_stream_t stream, int n, int m, int nu, int
   for (int pass = 0; pass < steps; ++pass) {
     NMF_CU(xpass_launch(w.plan, xa, prec, s));
     const bool last = pass == steps - 1;
-    if (variant == NMF_VARIANT_POWER && !last) st = normalize_columns(w, n, m, nu, bf16, both, s);
-    else st = orthonormalize(w, n, m, nu, bf16, both, last ? L : nullptr, last ? R : nullptr, nullptr, s);
+    if (variant == NMF_VARIANT_POWER && !last) st = normalize_columns(w, n, m, nu, ofmt, both, s);
+    else st = orthonormalize(w, n, m, nu, ofmt, both, last ? L : nullptr, last ? R : nullptr, nullptr, s);
     if (st != NMF_OK) return st;
   }
   return closing(both);
@@ -904,18 +913,18 @@ nmf_status_t nmf_dual_product(nmf_stream_t stream, int n, int m, int k, nmf_prec
   const DualWs w = carve_dual(workspace, n, m, k, prec);
   if (!ws_ok(workspace, workspace_bytes, w.bytes)) return NMF_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
-  const bool bf16 = prec == NMF_PREC_BF16;
-  const size_t es = bf16 ? 2 : 4;
+  const bool xconv = x_converted(w.plan, prec);
+  const int ofmt = op_format(w.plan, prec);
   NMF_CU(cudaMemsetAsync(w.ctrl, 0, sizeof(Control), s));
-  NMF_CU(cudaMemsetAsync(w.opA, 0, (size_t)w.plan.NV * w.lda * es, s));
-  NMF_CU(cudaMemsetAsync(w.opB, 0, (size_t)w.plan.NV * w.ldb * es, s));
-  if (bf16) NMF_CU(xb_convert(w.plan, X, n, m, w.Xb, w.ldxb, w.ctrl, s));
-  if (A) NMF_CU(transpose_launch(A, m, k, w.opA, w.lda, bf16, w.ctrl, s));
-  if (B) NMF_CU(transpose_launch(B, n, k, w.opB, w.ldb, bf16, w.ctrl, s));
+  NMF_CU(cudaMemsetAsync(w.opA, 0, op_bytes(w.plan, prec, w.lda), s));
+  NMF_CU(cudaMemsetAsync(w.opB, 0, op_bytes(w.plan, prec, w.ldb), s));
+  if (xconv) NMF_CU(xb_convert(w.plan, X, n, m, w.Xb, w.ldxb, w.ctrl, s));
+  if (A) NMF_CU(transpose_launch(A, m, k, w.opA, w.lda, ofmt, w.ctrl, s, (size_t)w.plan.NV * w.lda));
+  if (B) NMF_CU(transpose_launch(B, n, k, w.opB, w.ldb, ofmt, w.ctrl, s, (size_t)w.plan.NV * w.ldb));
   XPassArgs xa{};
   xa.n = n; xa.m = m;
-  xa.X = bf16 ? (const void*)w.Xb : (const void*)X;
-  xa.ldx = bf16 ? w.ldxb : m;
+  xa.X = xconv ? (const void*)w.Xb : (const void*)X;
+  xa.ldx = xconv ? w.ldxb : m;
   xa.opA = w.opA; xa.lda = w.lda; xa.opB = w.opB; xa.ldb = w.ldb;
   xa.partN = w.partN; xa.partT = w.partT; xa.nu = k;
   xa.doN = A != nullptr; xa.doT = B != nullptr;
@@ -948,20 +957,20 @@ nmf_status_t nmf_project(nmf_stream_t stream, int n, int m, int nu, nmf_prec_t p
   const DualWs w = carve_dual(workspace, n, m, nu, prec);
   if (!ws_ok(workspace, workspace_bytes, w.bytes)) return NMF_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
-  const bool bf16 = prec == NMF_PREC_BF16;
-  const size_t es = bf16 ? 2 : 4;
+  const bool xconv = x_converted(w.plan, prec);
+  const int ofmt = op_format(w.plan, prec);
   NMF_CU(cudaMemsetAsync(w.ctrl, 0, sizeof(Control), s));
-  NMF_CU(cudaMemsetAsync(w.opA, 0, (size_t)w.plan.NV * w.lda * es, s));
-  NMF_CU(cudaMemsetAsync(w.opB, 0, (size_t)w.plan.NV * w.ldb * es, s));
-  if (bf16) NMF_CU(xb_convert(w.plan, X, n, m, w.Xb, w.ldxb, w.ctrl, s));
+  NMF_CU(cudaMemsetAsync(w.opA, 0, op_bytes(w.plan, prec, w.lda), s));
+  NMF_CU(cudaMemsetAsync(w.opB, 0, op_bytes(w.plan, prec, w.ldb), s));
+  if (xconv) NMF_CU(xb_convert(w.plan, X, n, m, w.Xb, w.ldxb, w.ctrl, s));
   // X_R = X R: R is the N-product operand (stored transposed); X_L^T = X^T L^T:
   // the T-product operand is (L^T)^T = L itself, copied row by row
-  NMF_CU(transpose_launch(R, m, nu, w.opA, w.lda, bf16, w.ctrl, s));
-  NMF_CU(copy_rows_launch(L, nu, n, w.opB, w.ldb, bf16, w.ctrl, s));
+  NMF_CU(transpose_launch(R, m, nu, w.opA, w.lda, ofmt, w.ctrl, s, (size_t)w.plan.NV * w.lda));
+  NMF_CU(copy_rows_launch(L, nu, n, w.opB, w.ldb, ofmt, w.ctrl, s, (size_t)w.plan.NV * w.ldb));
   XPassArgs xa{};
   xa.n = n; xa.m = m;
-  xa.X = bf16 ? (const void*)w.Xb : (const void*)X;
-  xa.ldx = bf16 ? w.ldxb : m;
+  xa.X = xconv ? (const void*)w.Xb : (const void*)X;
+  xa.ldx = xconv ? w.ldxb : m;
   xa.opA = w.opA; xa.lda = w.lda; xa.opB = w.opB; xa.ldb = w.ldb;
   xa.partN = w.partN; xa.partT = w.partT; xa.nu = nu;
   xa.doN = true; xa.doT = true;

@@ -128,6 +128,35 @@ __device__ __forceinline__ void df_norm(DF& s) {
   s.hi = t;
 }
 
+// Operand formats of an X pass. OP_BF16X3 holds a float32 value v as three
+// bfloat16 parts p0 + p1 + p2 (p0 = bf16(v), p1 = bf16(v - p0), p2 =
+// bf16(v - p0 - p1), each difference exact in float32), so |v - p0 - p1 - p2|
+// <= 2^-27 |v|; part k of element i sits at i + k * part_stride.
+enum OpFormat { OP_F32 = 0, OP_BF16 = 1, OP_BF16X3 = 3 };
+
+__device__ __forceinline__ void split_bf16x3(float v, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
+  p0 = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(p0);
+  p1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(p1);
+  p2 = __float2bfloat16_rn(r2);
+}
+
+__device__ __forceinline__ void store_op(void* out, size_t i, int fmt, size_t part_stride, float v) {
+  if (fmt == OP_F32) {
+    static_cast<float*>(out)[i] = v;
+  } else if (fmt == OP_BF16) {
+    static_cast<__nv_bfloat16*>(out)[i] = __float2bfloat16_rn(v);
+  } else {
+    __nv_bfloat16 p0, p1, p2;
+    split_bf16x3(v, p0, p1, p2);
+    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out);
+    o[i] = p0;
+    o[i + part_stride] = p1;
+    o[i + 2 * part_stride] = p2;
+  }
+}
+
 __host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int round_up(int a, int b) { return ceil_div(a, b) * b; }
 __host__ __device__ __forceinline__ size_t round_up_sz(size_t a, size_t b) { return (a + b - 1) / b * b; }

@@ -48,6 +48,8 @@ struct XPassPlan {
   int NV;               // padded operand / partial width
   int ctas;
   int tiled;            // bfloat16 X held tile by tile (the tensor-core path's layout)
+  int parts;            // tiled: 1 (bfloat16 X, bfloat16 operands) or 3 (float32 X and
+                        // operands as three bfloat16 parts each, OP_BF16X3)
 };
 
 struct XPassArgs {
@@ -65,8 +67,21 @@ struct XPassArgs {
   Control* ctrl;
 };
 
-// Plans (tile sizes, region grid) for a pass at the given width.
-XPassPlan xpass_plan(int n, int m, int nu, nmf_prec_t prec, int num_sms);
+// Plans (tile sizes, region grid) for a pass at the given width. A float32
+// pass runs on the tensor cores as three bfloat16 parts when split_ok and the
+// width allows it (NV <= kSplitMaxNV), else on CUDA cores.
+constexpr int kSplitMaxNV = 32;
+XPassPlan xpass_plan(int n, int m, int nu, nmf_prec_t prec, int num_sms, bool split_ok = true);
+// Operand format and bytes of one operand buffer (NV rows of ld elements per part).
+inline int op_format(const XPassPlan& pl, nmf_prec_t prec) {
+  return pl.tiled && pl.parts == 3 ? OP_BF16X3 : prec == NMF_PREC_BF16 ? OP_BF16 : OP_F32;
+}
+inline size_t op_bytes(const XPassPlan& pl, nmf_prec_t prec, int ld) {
+  const int f = op_format(pl, prec);
+  return (size_t)pl.NV * ld * (f == OP_F32 ? 4 : f == OP_BF16 ? 2 : 6);
+}
+// Whether the pass reads a converted copy of X (bfloat16 rows, or tiles).
+inline bool x_converted(const XPassPlan& pl, nmf_prec_t prec) { return pl.tiled || prec == NMF_PREC_BF16; }
 cudaError_t xpass_launch(const XPassPlan& plan, const XPassArgs& a, nmf_prec_t prec, cudaStream_t s);
 // bfloat16 copy of a float32 X in the layout the plan's kernel reads:
 // row-major with ldxb columns, or (plan.tiled) tile by tile.
@@ -80,7 +95,7 @@ cudaError_t xpass_tc_convert(const XPassPlan& plan, const float* X, int n, int m
 cudaError_t xpass_simt_launch(const XPassPlan& plan, const XPassArgs& a, bool bf16, cudaStream_t s);
 XPassPlan xpass_simt_plan(int n, int m, int nu, int num_sms);
 // Tensor-core (tcgen05) path for bfloat16 X.
-XPassPlan xpass_tc_plan(int n, int m, int nu, int num_sms);
+XPassPlan xpass_tc_plan(int n, int m, int nu, int num_sms, int parts);
 cudaError_t xpass_tc_launch(const XPassPlan& plan, const XPassArgs& a, cudaStream_t s);
 bool xpass_tc_available();
 
@@ -102,8 +117,9 @@ struct RowJob {
   // outputs (each optional)
   float* Y;             // N x nu row-major (may alias src: rows are read before written)
   float* Yt;            // nu x N row-major (transpose)
-  void* op;             // NV x ldop transposed operand (float or bf16)
-  int ldop, op_bf16;
+  void* op;             // NV x ldop transposed operand (OpFormat op_fmt; OP_BF16X3: parts NV * ldop apart)
+  int ldop, op_fmt;
+  size_t op_part;       // elements between the parts of an OP_BF16X3 operand
   float2* gram_part;    // [ctas][nu*(nu+1)/2] float-float partial Gram of the output rows
   int gram_always;      // form gram_part unconditionally
   int gram_on_shift;    // form gram_part when *shift_flag (as read) or this factorisation shifted
@@ -244,12 +260,13 @@ cudaError_t sketch_launch(int rows, int cols, uint64_t seed, uint32_t stream_id,
 cudaError_t to_bf16_launch(const float* X, int n, int m, __nv_bfloat16* Xb, int ldb, Control* ctrl,
                            cudaStream_t s);
 // out[c][r] = in[r][c] for an R x C float matrix; `out` has leading dim ldo and
-// element type float or bf16. Padding (rows >= C, cols >= R) is untouched.
-cudaError_t transpose_launch(const float* in, int R, int C, void* out, int ldo, int out_bf16, Control* ctrl,
-                             cudaStream_t s);
-// Copies a rows x cols float matrix into a float or bf16 matrix with leading dim ldo.
-cudaError_t copy_rows_launch(const float* in, int rows, int cols, void* out, int ldo, int out_bf16,
-                             Control* ctrl, cudaStream_t s);
+// OpFormat fmt (OP_BF16X3: parts part_stride elements apart). Padding (rows
+// >= C, cols >= R) is untouched.
+cudaError_t transpose_launch(const float* in, int R, int C, void* out, int ldo, int fmt, Control* ctrl,
+                             cudaStream_t s, size_t part_stride = 0);
+// Copies a rows x cols float matrix into an operand (OpFormat fmt) with leading dim ldo.
+cudaError_t copy_rows_launch(const float* in, int rows, int cols, void* out, int ldo, int fmt,
+                             Control* ctrl, cudaStream_t s, size_t part_stride = 0);
 cudaError_t timestamp_launch(unsigned long long* t, cudaStream_t s);
 // out[i] = alpha * in[i] (may alias)
 cudaError_t scale_launch(const float* in, float* out, long long count, float alpha, cudaStream_t s);

@@ -512,11 +512,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
   if (outOp)
     for (int i = tid; i < rows * nu; i += kRowThreads) {
       const int c = i / rows, r = i % rows;
-      const float v = Ys[r * kYsStride + c];
-      if (J.op_bf16)
-        static_cast<__nv_bfloat16*>(outOp)[(size_t)c * J.ldop + r0 + r] = __float2bfloat16_rn(v);
-      else
-        static_cast<float*>(outOp)[(size_t)c * J.ldop + r0 + r] = v;
+      store_op(outOp, (size_t)c * J.ldop + r0 + r, J.op_fmt, J.op_part, Ys[r * kYsStride + c]);
     }
   if (bad) set_status(ctrl, NMF_ERR_NONFINITE);
   if (J.gram_part && !single && (J.gram_always || extra_gram)) {

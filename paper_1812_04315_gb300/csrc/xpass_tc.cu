@@ -187,6 +187,79 @@ __device__ __forceinline__ void store_block(const float* v, float* stg, float* d
   }
 }
 
+// Epilogue warps 2..5 (TMEM lane quarter = warp % 4): D_N of every row of
+// tiles as it completes (double buffered: tfull / tempty), then every D_T
+// once the MMA issuer's last commit (tdone) has landed. stage_area: 4 x 32
+// staged rows of kStg floats.
+//
+// ACC accumulators per output (TMEM columns): ACC = 1: D_N buffer b at b NV,
+// D_T[ci] at (2 + ci) NV. ACC = 2 (leading term and small terms, summed
+// here): D_N buffer b at 2 b NV (+ NV), D_T[ci] at (4 + 2 ci) NV (+ NV).
+template <int NV, int ACC>
+__device__ __forceinline__ void load_acc(uint32_t taddr, float* v) {
+#pragma unroll
+  for (int c = 0; c < NV; c += 8) tmem_ld8(taddr + (uint32_t)c, v + c);
+  if constexpr (ACC == 2) {
+    float w[NV];
+#pragma unroll
+    for (int c = 0; c < NV; c += 8) tmem_ld8(taddr + (uint32_t)(NV + c), w + c);
+    tmem_ld_wait();
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] += w[c];
+  } else {
+    tmem_ld_wait();
+  }
+}
+
+template <int NV, int ACC>
+__device__ __forceinline__ void epilogue(const TcParams& P, uint32_t tmem, float* stage_area, uint64_t* tfull,
+                                         uint64_t* tempty, uint64_t* tdone, volatile int* abort_flag, int rt0, int ct0,
+                                         int nrt, int nct, int rg, int cg) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3;
+  const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+  float* stg = stage_area + (warp - 2) * 32 * kStg;
+  float v[NV];
+  if (P.doN) {
+    for (int ri = 0; ri < nrt; ++ri) {
+      const int buf = ri & 1;
+      if (!mbar_wait(&tfull[buf], (uint32_t)(ri >> 1) & 1u, abort_flag, P.wait_ns)) break;
+      tc_fence_after();
+      load_acc<NV, ACC>(tmem + lane_off + (uint32_t)(buf * ACC * NV), v);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+      const int row0 = (rt0 + ri) * kTM + q * 32;
+      store_block<NV>(v, stg, P.partN + ((size_t)cg * P.n + row0) * NV, P.n - row0, lane);
+    }
+  }
+  if (P.doT && mbar_wait(tdone, 0u, abort_flag, P.wait_ns)) {
+    tc_fence_after();
+    for (int ci = 0; ci < nct; ++ci) {
+      load_acc<NV, ACC>(tmem + lane_off + (uint32_t)((2 + ci) * ACC * NV), v);
+      const int col0 = (ct0 + ci) * kTK + q * 32;
+      store_block<NV>(v, stg, P.partT + ((size_t)rg * P.m + col0) * NV, P.m - col0, lane);
+    }
+  } else if (!P.doT) {
+    mbar_wait(tdone, 0u, abort_flag, P.wait_ns);
+  }
+}
+
+// The MMA issuer's last commit (tdone) completes only when every MMA has
+// finished reading shared memory and writing TMEM; after an abort nobody
+// else waited for it, so the issuer drains it before the TMEM is freed.
+__device__ __forceinline__ void teardown(const TcParams& P, uint32_t tmem, uint64_t* tdone, volatile int* abort_flag) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 1 && lane == 0 && *abort_flag) mbar_drain(tdone, 0u, P.wait_ns);
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) set_status(P.ctrl, NMF_ERR_DEVICE_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols));
+  }
+}
+
 template <int NV>
 __global__ void __launch_bounds__(kThreads, 1)
     xpass_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcParams P) {
@@ -308,50 +381,216 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_commit(&tdone);
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    const int q = warp & 3;
-    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    float* stg = reinterpret_cast<float*>(smem + (size_t)kStages * stageBytes) + (warp - 2) * 32 * kStg;
-    float v[NV];
-    if (P.doN) {
-      for (int ri = 0; ri < nrt; ++ri) {
-        const int buf = ri & 1;
-        if (!mbar_wait(&tfull[buf], (uint32_t)(ri >> 1) & 1u, abort_flag, P.wait_ns)) break;
-        tc_fence_after();
-#pragma unroll
-        for (int c = 0; c < NV; c += 8) tmem_ld8(tmem + lane_off + (uint32_t)(buf * NV + c), v + c);
-        tmem_ld_wait();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[buf]);
-        const int row0 = (rt0 + ri) * kTM + q * 32;
-        store_block<NV>(v, stg, P.partN + ((size_t)cg * P.n + row0) * NV, P.n - row0, lane);
-      }
-    }
-    if (P.doT && mbar_wait(&tdone, 0u, abort_flag, P.wait_ns)) {
-      tc_fence_after();
-      for (int ci = 0; ci < nct; ++ci) {
-#pragma unroll
-        for (int c = 0; c < NV; c += 8) tmem_ld8(tmem + lane_off + (uint32_t)((2 + ci) * NV + c), v + c);
-        tmem_ld_wait();
-        const int col0 = (ct0 + ci) * kTK + q * 32;
-        store_block<NV>(v, stg, P.partT + ((size_t)rg * P.m + col0) * NV, P.m - col0, lane);
-      }
-    } else if (!P.doT) {
-      mbar_wait(&tdone, 0u, abort_flag, P.wait_ns);
-    }
+    epilogue<NV, 1>(P, tmem, reinterpret_cast<float*>(smem + (size_t)kStages * stageBytes), tfull, tempty, &tdone,
+                    abort_flag, rt0, ct0, nrt, nct, rg, cg);
   }
-  // The MMA issuer's last commit (tdone) completes only when every MMA has
-  // finished reading shared memory and writing TMEM; after an abort nobody
-  // else waited for it, so the issuer drains it before the TMEM is freed.
-  if (warp == 1 && lane == 0 && *abort_flag) mbar_drain(&tdone, 0u, P.wait_ns);
+  teardown(P, tmem, &tdone, abort_flag);
+}
+
+
+// ---- float32 X as three bfloat16 parts -------------------------------------
+// X = X0 + X1 + X2 and every operand A = A0 + A1 + A2 (OP_BF16X3): each part
+// rounds the float32 residual of the previous ones, so |X - X0 - X1 - X2| <=
+// 2^-27 |X|. The six products X_j A_i with i + j <= 2 leave out terms below
+// 2^-26 |x a|. The leading term X_0 A_0 has a TMEM accumulator of its own and
+// the five others (at most 2^-8 of it) share a second one: tensor-core
+// accumulation rounds the running sum at every MMA, so adding the small
+// terms into the large sum would round it six times as often as a one-part
+// pass does. The epilogue adds the two once. A pass is then as accurate as
+// the one-part pass is on its own inputs, from 6 bytes of X per element
+// instead of 4 (the parts are formed once per call).
+//
+// A tile's three parts arrive as three 32 KB stages of the X ring. The
+// operand slices change less often and have rings of their own: the A slice
+// (3 NV rows x 128 columns, the tile's columns) per tile, the B slice per row
+// of tiles, each double buffered. Part j of a tile feeds the MMAs with
+// operand parts 0 .. 2 - j.
+constexpr int kMaxStages3 = 4;
+__host__ __device__ constexpr int op3_box_bytes(int NV) { return 3 * NV * kBoxK * 2; }  // 3 NV rows x 128 bytes
+__host__ __device__ constexpr int op3_tile_bytes(int NV) { return 2 * op3_box_bytes(NV); }
+
+template <int NV>
+__global__ void __launch_bounds__(kThreads, 1)
+    xpass_tc3_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcParams P) {
+  if (call_failed(P.ctrl)) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int box = op3_box_bytes(NV);
+  constexpr int opTile = op3_tile_bytes(NV);
+  const int kStages = P.stages;
+  uint8_t* xring = smem;
+  uint8_t* aring = xring + (size_t)kStages * kXStageBytes;
+  uint8_t* bring = aring + 2 * opTile;
+  float* stage_area = reinterpret_cast<float*>(bring + 2 * opTile);
+  __shared__ uint64_t xfull[kMaxStages3], xempty[kMaxStages3], afull[2], aempty[2], bfull[2], bempty[2];
+  __shared__ uint64_t tfull[2], tempty[2], tdone;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rg = blockIdx.x / P.S_c, cg = blockIdx.x % P.S_c;
+  const int rt0 = split_point(P.tiles_r, P.S_r, rg), rt1 = split_point(P.tiles_r, P.S_r, rg + 1);
+  const int ct0 = split_point(P.tiles_c, P.S_c, cg), ct1 = split_point(P.tiles_c, P.S_c, cg + 1);
+  const int nrt = rt1 - rt0, nct = ct1 - ct0;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&xfull[st], 1);
+      mbar_init(&xempty[st], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&afull[b], 1);
+      mbar_init(&aempty[b], 1);
+      mbar_init(&bfull[b], 1);
+      mbar_init(&bempty[b], 1);
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(&tdone, 1);
+    abort_s = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(P.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
   tc_fence_before();
   __syncthreads();
-  if (*abort_flag && threadIdx.x == 0) set_status(P.ctrl, NMF_ERR_DEVICE_TIMEOUT);
-  if (warp == 1) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols));
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+  volatile int* abort_flag = &abort_s;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int it = 0, at = 0, bt = 0;
+      for (int rt = rt0; rt < rt1 && !*abort_flag; ++rt) {
+        if (P.doT) {
+          const int b = bt & 1;
+          if (!mbar_wait(&bempty[b], ((uint32_t)(bt >> 1) & 1u) ^ 1u, abort_flag, P.wait_ns)) break;
+          mbar_arrive_expect_tx(&bfull[b], (uint32_t)opTile);
+          tma_load_2d(bring + (size_t)b * opTile, &mapB, &bfull[b], rt * kTM, 0);
+          tma_load_2d(bring + (size_t)b * opTile + box, &mapB, &bfull[b], rt * kTM + kBoxK, 0);
+          ++bt;
+        }
+        bool ok = true;
+        for (int ct = ct0; ct < ct1 && ok; ++ct) {
+          if (P.doN) {
+            const int a = at & 1;
+            if (!mbar_wait(&aempty[a], ((uint32_t)(at >> 1) & 1u) ^ 1u, abort_flag, P.wait_ns)) { ok = false; break; }
+            mbar_arrive_expect_tx(&afull[a], (uint32_t)opTile);
+            tma_load_2d(aring + (size_t)a * opTile, &mapA, &afull[a], ct * kTK, 0);
+            tma_load_2d(aring + (size_t)a * opTile + box, &mapA, &afull[a], ct * kTK + kBoxK, 0);
+            ++at;
+          }
+          for (int j = 0; j < 3; ++j, ++it) {
+            const int st = it % kStages;
+            if (!mbar_wait(&xempty[st], ((uint32_t)(it / kStages) & 1u) ^ 1u, abort_flag, P.wait_ns)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&xfull[st], (uint32_t)kXStageBytes);
+            if (P.withhold && blockIdx.x == 0 && it == 0) continue;  // failure-path testing: the stage never fills
+            bulk_load(xring + (size_t)st * kXStageBytes, P.Xt + (((size_t)rt * P.tiles_c + ct) * 3 + j) * kXStageBytes,
+                      (uint32_t)kXStageBytes, &xfull[st]);
+          }
+        }
+        if (!ok) break;
+      }
+      if (*abort_flag) {
+        // let the copies already issued land before the CTA exits
+        for (int k = it - kStages < 0 ? 0 : it - kStages; k < it; ++k)
+          mbar_drain(&xfull[k % kStages], (uint32_t)(k / kStages) & 1u, P.wait_ns);
+        for (int k = at - 2 < 0 ? 0 : at - 2; k < at; ++k) mbar_drain(&afull[k & 1], (uint32_t)(k >> 1) & 1u, P.wait_ns);
+        for (int k = bt - 2 < 0 ? 0 : bt - 2; k < bt; ++k) mbar_drain(&bfull[k & 1], (uint32_t)(k >> 1) & 1u, P.wait_ns);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idN = instr_desc(kTM, NV, 0);
+      const uint32_t idT = instr_desc(kTK, NV, 1);
+      int it = 0, at = 0, bt = 0;
+      bool ok = true;
+      for (int ri = 0; ri < nrt && ok; ++ri) {
+        const int buf = ri & 1;
+        const uint32_t dN = tmem + (uint32_t)(buf * 2 * NV);  // leading term; small terms at + NV
+        int b = 0;
+        if (P.doN) {
+          if (!mbar_wait(&tempty[buf], ((uint32_t)(ri >> 1) & 1u) ^ 1u, abort_flag, P.wait_ns)) { ok = false; break; }
+          tc_fence_after();
+        }
+        if (P.doT) {
+          b = bt & 1;
+          if (!mbar_wait(&bfull[b], (uint32_t)(bt >> 1) & 1u, abort_flag, P.wait_ns)) { ok = false; break; }
+          tc_fence_after();
+        }
+        const uint32_t opb = smem_u32(bring + (size_t)b * opTile);
+        for (int ci = 0; ci < nct && ok; ++ci) {
+          int a = 0;
+          if (P.doN) {
+            a = at & 1;
+            if (!mbar_wait(&afull[a], (uint32_t)(at >> 1) & 1u, abort_flag, P.wait_ns)) { ok = false; break; }
+            tc_fence_after();
+          }
+          const uint32_t opa = smem_u32(aring + (size_t)a * opTile);
+          for (int j = 0; j < 3; ++j, ++it) {
+            const int st = it % kStages;
+            if (!mbar_wait(&xfull[st], (uint32_t)(it / kStages) & 1u, abort_flag, P.wait_ns)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t xa = smem_u32(xring + (size_t)st * kXStageBytes);
+            // term (j, i) goes to the leading accumulator when j = i = 0, else to
+            // the small-term one, whose first term of a row (N) or of the
+            // CTA's rows (T) is (0, 1)
+            if (P.doN) {
+              for (int i = 0; i + j < 3; ++i) {
+                const bool lead = i + j == 0;
+                const uint32_t d = dN + (lead ? 0u : (uint32_t)NV);
+                const bool first = ci == 0 && (lead || (j == 0 && i == 1));
+#pragma unroll
+                for (int kk = 0; kk < kTK / 16; ++kk) {
+                  const uint32_t off = (uint32_t)((kk >> 2) * (kXStageBytes / 2) + (kk & 3) * 32);
+                  const uint32_t boff = (uint32_t)((kk >> 2) * box + i * NV * 128 + (kk & 3) * 32);
+                  tc_mma(d, smem_desc(xa + off, 16, 1024), smem_desc(opa + boff, 16, 1024), idN,
+                         (first && kk == 0) ? 0u : 1u);
+                }
+              }
+            }
+            if (P.doT) {
+              const uint32_t dT = tmem + (uint32_t)((4 + 2 * ci) * NV);
+              for (int i = 0; i + j < 3; ++i) {
+                const bool lead = i + j == 0;
+                const uint32_t d = dT + (lead ? 0u : (uint32_t)NV);
+                const bool first = ri == 0 && (lead || (j == 0 && i == 1));
+#pragma unroll
+                for (int kk = 0; kk < kTM / 16; ++kk) {
+                  const uint32_t aoff = (uint32_t)(kk * 2048);
+                  const uint32_t boff = (uint32_t)((kk >> 2) * box + i * NV * 128 + (kk & 3) * 32);
+                  tc_mma(d, smem_desc(xa + aoff, kXStageBytes / 2, 1024), smem_desc(opb + boff, 16, 1024), idT,
+                         (first && kk == 0) ? 0u : 1u);
+                }
+              }
+            }
+            tc_commit(&xempty[st]);
+          }
+          if (ok && P.doN) {
+            tc_commit(&aempty[a]);
+            ++at;
+          }
+        }
+        if (ok && P.doT) {
+          tc_commit(&bempty[b]);
+          ++bt;
+        }
+        if (ok && P.doN) tc_commit(&tfull[buf]);
+      }
+      tc_commit(&tdone);
+    }
+  } else {
+    epilogue<NV, 2>(P, tmem, stage_area, tfull, tempty, &tdone, abort_flag, rt0, ct0, nrt, nct, rg, cg);
   }
+  teardown(P, tmem, &tdone, abort_flag);
 }
 
 // ---- host side -------------------------------------------------------------
@@ -381,14 +620,14 @@ bool make_map(CUtensorMap* map, const void* base, int ld, int rows, int box_cols
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-uint32_t tmem_cols_for(int NV, int maxct) {
-  const uint32_t need = (uint32_t)((2 + maxct) * NV);
+uint32_t tmem_cols_for(int NV, int maxct, int acc) {
+  const uint32_t need = (uint32_t)((2 + maxct) * acc * NV);
   uint32_t c = 32;
   while (c < need) c <<= 1;
   return c;
 }
 
-int max_col_tiles(int NV) { return (int)(kMaxTmemCols / NV) - 2; }
+int max_col_tiles(int NV, int acc) { return (int)(kMaxTmemCols / (acc * NV)) - 2; }
 
 size_t tc_stage_bytes(int NV) { return (size_t)(kXStageBytes + 4 * NV * kBoxK * 2); }
 int tc_stages(int NV) {
@@ -404,6 +643,11 @@ size_t tc_smem_bytes(int NV) { return (size_t)tc_stages(NV) * tc_stage_bytes(NV)
 // j ^ (r mod 8) (the 128-byte swizzle). Entries outside X are zero. One
 // thread per 8 consecutive elements of a row: the reads of a warp are
 // contiguous, and every 8 threads fill one 128-byte row of a box.
+//
+// parts = 3: every element is stored as its three bfloat16 parts
+// (split_bf16x3), part j of tile (rt, ct) at byte ((rt * tiles_c + ct) * 3 +
+// j) * 32 KB, in the same layout.
+template <int PARTS>
 __global__ void to_tiles_kernel(const float* __restrict__ X, int n, int m, int tiles_r, int tiles_c,
                                 uint4* __restrict__ Xt, Control* ctrl) {
   if (call_failed(ctrl)) return;
@@ -424,17 +668,26 @@ __global__ void to_tiles_kernel(const float* __restrict__ X, int n, int m, int t
 #pragma unroll
       for (int k = 0; k < 8; ++k) v[k] = (r < n && c0 + k < m) ? X[(size_t)r * m + c0 + k] : 0.f;
     }
-    uint4 out;
-    uint32_t* o = reinterpret_cast<uint32_t*>(&out);
+    uint4 out[PARTS];
+    if constexpr (PARTS == 1) {
+      uint32_t* o = reinterpret_cast<uint32_t*>(&out[0]);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-      o[k] = *reinterpret_cast<const uint32_t*>(&h);
+      for (int k = 0; k < 4; ++k) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+        o[k] = *reinterpret_cast<const uint32_t*>(&h);
+      }
+    } else {
+      __nv_bfloat16* o0 = reinterpret_cast<__nv_bfloat16*>(&out[0]);
+      __nv_bfloat16* o1 = reinterpret_cast<__nv_bfloat16*>(&out[1]);
+      __nv_bfloat16* o2 = reinterpret_cast<__nv_bfloat16*>(&out[2]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) split_bf16x3(v[k], o0[k], o1[k], o2[k]);
     }
     const int rt = r / kTM, rr = r % kTM, ct = cj / (kTK / 8), h = (cj / 8) & 1, j = cj & 7;
-    const size_t byte = ((size_t)rt * tiles_c + ct) * kXStageBytes + (size_t)h * (kTM * 128) + (size_t)rr * 128 +
-                        (size_t)((j ^ (rr & 7)) * 16);
-    Xt[byte / 16] = out;
+    const size_t byte = ((size_t)rt * tiles_c + ct) * PARTS * kXStageBytes + (size_t)h * (kTM * 128) +
+                        (size_t)rr * 128 + (size_t)((j ^ (rr & 7)) * 16);
+#pragma unroll
+    for (int q = 0; q < PARTS; ++q) Xt[(byte + (size_t)q * kXStageBytes) / 16] = out[q];
   }
 }
 
@@ -445,6 +698,27 @@ cudaError_t launch_nv(const CUtensorMap& mA, const CUtensorMap& mB, const TcPara
   if (e != cudaSuccess) return e;
   count_launches(1);
   xpass_tc_kernel<NV><<<ctas, kThreads, smem, s>>>(mA, mB, P);
+  return cudaGetLastError();
+}
+
+// Three-part kernel: X ring stages that fit beside the two operand rings
+// (double buffered) and the epilogue staging.
+int tc3_stages(int NV) {
+  const long room = (long)kSmemBudget - 1024 - kStageArea - 4l * op3_tile_bytes(NV);
+  const long st = room / kXStageBytes;
+  return (int)(st > kMaxStages3 ? kMaxStages3 : st);
+}
+size_t tc3_smem_bytes(int NV) {
+  return (size_t)tc3_stages(NV) * kXStageBytes + 4 * (size_t)op3_tile_bytes(NV) + kStageArea + 1024;
+}
+
+template <int NV>
+cudaError_t launch3_nv(const CUtensorMap& mA, const CUtensorMap& mB, const TcParams& P, int ctas, cudaStream_t s) {
+  const size_t smem = tc3_smem_bytes(NV);
+  cudaError_t e = allow_dynamic_smem((const void*)xpass_tc3_kernel<NV>, (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  xpass_tc3_kernel<NV><<<ctas, kThreads, smem, s>>>(mA, mB, P);
   return cudaGetLastError();
 }
 
@@ -466,14 +740,15 @@ bool xpass_tc_available() {
 // Region grid: the S_r x S_c split of the tile grid with at most `num_sms`
 // CTAs that minimises the largest region (tiles per CTA), subject to the
 // TMEM budget on column tiles per region.
-XPassPlan xpass_tc_plan(int n, int m, int nu, int num_sms) {
+XPassPlan xpass_tc_plan(int n, int m, int nu, int num_sms, int parts) {
   XPassPlan pl{};
+  pl.parts = parts;
   pl.tile_r = kTM;
   pl.tile_c = kTK;
   pl.tiles_r = ceil_div(n, kTM);
   pl.tiles_c = ceil_div(m, kTK);
   pl.NV = round_up(nu, 16);
-  const int maxct = max_col_tiles(pl.NV);
+  const int maxct = max_col_tiles(pl.NV, parts == 3 ? 2 : 1);
   long best = -1;
   int bestr = 1, bestc = pl.tiles_c;
   for (int S_c = 1; S_c <= pl.tiles_c; ++S_c) {
@@ -500,21 +775,26 @@ cudaError_t xpass_tc_convert(const XPassPlan& pl, const float* X, int n, int m, 
   const long long chunks = (long long)pl.tiles_r * kTM * pl.tiles_c * (kTK / 8);
   const long long ctas = std::min<long long>((chunks + 255) / 256, 8ll * device_sm_count());
   count_launches(1);
-  to_tiles_kernel<<<(int)ctas, 256, 0, s>>>(X, n, m, pl.tiles_r, pl.tiles_c, static_cast<uint4*>(Xt),
-                                                        ctrl);
+  if (pl.parts == 3)
+    to_tiles_kernel<3><<<(int)ctas, 256, 0, s>>>(X, n, m, pl.tiles_r, pl.tiles_c, static_cast<uint4*>(Xt), ctrl);
+  else
+    to_tiles_kernel<1><<<(int)ctas, 256, 0, s>>>(X, n, m, pl.tiles_r, pl.tiles_c, static_cast<uint4*>(Xt), ctrl);
   return cudaGetLastError();
 }
 
 cudaError_t xpass_tc_launch(const XPassPlan& pl, const XPassArgs& a, cudaStream_t s) {
   CUtensorMap mA, mB;
   if (!pl.tiled || (reinterpret_cast<uintptr_t>(a.X) & 15u)) return cudaErrorInvalidValue;
-  if (!make_map(&mA, a.opA, a.lda, pl.NV, kBoxK, pl.NV)) return cudaErrorInvalidValue;
-  if (!make_map(&mB, a.opB, a.ldb, pl.NV, kBoxK, pl.NV)) return cudaErrorInvalidValue;
+  if (pl.parts != 1 && (pl.parts != 3 || pl.NV > kSplitMaxNV)) return cudaErrorInvalidValue;
+  // operands: parts x NV rows (part k at rows k NV .. k NV + NV - 1), one box holds them all
+  const int oprows = pl.parts * pl.NV;
+  if (!make_map(&mA, a.opA, a.lda, oprows, kBoxK, oprows)) return cudaErrorInvalidValue;
+  if (!make_map(&mB, a.opB, a.ldb, oprows, kBoxK, oprows)) return cudaErrorInvalidValue;
   TcParams P{};
   P.Xt = static_cast<const uint8_t*>(a.X);
   P.n = a.n;
   P.m = a.m;
-  P.stages = tc_stages(pl.NV);
+  P.stages = pl.parts == 3 ? tc3_stages(pl.NV) : tc_stages(pl.NV);
   P.tiles_r = pl.tiles_r;
   P.tiles_c = pl.tiles_c;
   P.S_r = pl.S_r;
@@ -524,9 +804,16 @@ cudaError_t xpass_tc_launch(const XPassPlan& pl, const XPassArgs& a, cudaStream_
   P.partN = a.partN;
   P.partT = a.partT;
   P.ctrl = a.ctrl;
-  P.tmem_cols = tmem_cols_for(pl.NV, ceil_div(pl.tiles_c, pl.S_c));
+  P.tmem_cols = tmem_cols_for(pl.NV, ceil_div(pl.tiles_c, pl.S_c), pl.parts == 3 ? 2 : 1);
   P.wait_ns = wait_limit_ns();
   P.withhold = injected_fault() == NMF_FAULT_XPASS_COPY ? 1 : 0;
+  if (pl.parts == 3) {
+    switch (pl.NV) {
+      case 16: return launch3_nv<16>(mA, mB, P, pl.ctas, s);
+      case 32: return launch3_nv<32>(mA, mB, P, pl.ctas, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (pl.NV) {
     case 16: return launch_nv<16>(mA, mB, P, pl.ctas, s);
     case 32: return launch_nv<32>(mA, mB, P, pl.ctas, s);

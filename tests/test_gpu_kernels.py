@@ -2,8 +2,10 @@
 
 * Gaussian sketch: element-by-element against the oracle's Philox/Box-Muller;
 * one pass, two products (nmf_dual_product): float32 path against float64
-  products; bfloat16 path against float64 products of the bfloat16-rounded
-  inputs (only the float32 accumulation differs);
+  products (tensor cores on three bfloat16 parts up to 32 columns, CUDA
+  cores beyond, and the two against each other); bfloat16 path against
+  float64 products of the bfloat16-rounded inputs (only the float32
+  accumulation differs);
 * RRE (eq. 4) against float64.
 
 Tolerances. A float32 dot product of length K has error below
@@ -84,14 +86,57 @@ def test_tensor_core_path_matches_cuda_core_path(nmf, n, m, k):
         assert np.max(np.abs(a - b)) <= 8 * np.sqrt(K) * 2.0 ** -24 * np.sqrt(K) * scale
 
 
+@pytest.mark.parametrize("n,m,k", [(2000, 3000, 20), (129, 1000, 10), (5, 7, 3), (300, 517, 32), (640, 384, 16)])
+def test_float32_tensor_core_path_matches_cuda_cores(nmf, n, m, k):
+    # Float32 X and operands: the tensor cores take three bfloat16 parts of
+    # each (up to 32 columns), the CUDA-core kernel plain float32. Both sit
+    # inside the float32 bound of test_dual_product; their difference is the
+    # two summation orders, bounded by twice that bound.
+    rng = np.random.default_rng(n + 7 * m + k)
+    X = rng.random((n, m)).astype(np.float32)
+    A = rng.standard_normal((m, k)).astype(np.float32)
+    B = rng.standard_normal((n, k)).astype(np.float32)
+    tcN, tcT = nmf.dual_product(_t(X), _t(A), _t(B), prec=0)
+    nmf.set_kernel_path(True)
+    try:
+        scN, scT = nmf.dual_product(_t(X), _t(A), _t(B), prec=0)
+    finally:
+        nmf.set_kernel_path(False)
+    Xd, Ad, Bd = X.astype(np.float64), A.astype(np.float64), B.astype(np.float64)
+    for got, alt, ref, absprod, K in ((tcN, scN, Xd @ Ad, np.abs(Xd) @ np.abs(Ad), m),
+                                      (tcT, scT, Xd.T @ Bd, np.abs(Xd).T @ np.abs(Bd), n)):
+        bound = 4 * np.sqrt(K) * 2.0 ** -24 * absprod + 1e-30
+        got, alt = _np(got), _np(alt)
+        assert np.all(np.abs(got - ref) <= bound)
+        assert np.all(np.abs(alt - ref) <= bound)
+        assert np.all(np.abs(got - alt) <= 2 * bound)
+        # the three-part products are far closer than bfloat16 inputs would be
+        assert np.max(np.abs(got - ref) / (absprod + 1e-30)) < 2.0 ** -20
+
+
+def test_float32_tensor_core_path_keeps_small_residuals(nmf):
+    # X = 1 + d with |d| ~ 2^-12: bfloat16 keeps only 1, the three parts keep
+    # d to 2^-27; X A - 1 A isolates the residual part of the product.
+    n, m, k = 256, 384, 8
+    rng = np.random.default_rng(3)
+    d = (rng.random((n, m)) * 2.0 ** -12).astype(np.float32)
+    X = (np.float32(1.0) + d).astype(np.float32)
+    A = rng.standard_normal((m, k)).astype(np.float32)
+    YN, _ = nmf.dual_product(_t(X), _t(A), None, prec=0)
+    Xd, Ad = X.astype(np.float64), A.astype(np.float64)
+    ref = Xd @ Ad
+    assert np.all(np.abs(_np(YN) - ref) <= 4 * np.sqrt(m) * 2.0 ** -24 * (np.abs(Xd) @ np.abs(Ad)))
+
+
 def test_dual_product_is_deterministic(nmf):
     rng = np.random.default_rng(1)
     X = _t(rng.random((777, 555)))
     A = _t(rng.standard_normal((555, 24)))
     B = _t(rng.standard_normal((777, 24)))
-    a1, b1 = nmf.dual_product(X, A, B, prec=1)
-    a2, b2 = nmf.dual_product(X, A, B, prec=1)
-    assert bool((a1 == a2).all()) and bool((b1 == b2).all())
+    for prec in (1, 0):
+        a1, b1 = nmf.dual_product(X, A, B, prec=prec)
+        a2, b2 = nmf.dual_product(X, A, B, prec=prec)
+        assert bool((a1 == a2).all()) and bool((b1 == b2).all())
 
 
 @pytest.mark.parametrize("n,m,p", [(300, 200, 5), (1, 1, 1), (513, 257, 32)])
