@@ -192,20 +192,24 @@ __device__ __forceinline__ void store_block(const float* v, float* stg, float* d
 // once the MMA issuer's last commit (tdone) has landed. stage_area: 4 x 32
 // staged rows of kStg floats.
 //
-// ACC accumulators per output (TMEM columns): ACC = 1: D_N buffer b at b NV,
-// D_T[ci] at (2 + ci) NV. ACC = 2 (leading term and small terms, summed
-// here): D_N buffer b at 2 b NV (+ NV), D_T[ci] at (4 + 2 ci) NV (+ NV).
+// ACC accumulators per output, ACC NV TMEM columns: ACC = 1: D_N buffer b at
+// b NV, D_T[ci] at (2 + ci) NV. ACC = 3 (L, S_a, S_b of the three-part pass,
+// summed here as L + (S_a + S_b)): D_N buffer b at 3 b NV, D_T[ci] at
+// (6 + 3 ci) NV.
 template <int NV, int ACC>
 __device__ __forceinline__ void load_acc(uint32_t taddr, float* v) {
 #pragma unroll
   for (int c = 0; c < NV; c += 8) tmem_ld8(taddr + (uint32_t)c, v + c);
-  if constexpr (ACC == 2) {
-    float w[NV];
+  if constexpr (ACC == 3) {
+    float a[NV], b[NV];
 #pragma unroll
-    for (int c = 0; c < NV; c += 8) tmem_ld8(taddr + (uint32_t)(NV + c), w + c);
+    for (int c = 0; c < NV; c += 8) {
+      tmem_ld8(taddr + (uint32_t)(NV + c), a + c);
+      tmem_ld8(taddr + (uint32_t)(2 * NV + c), b + c);
+    }
     tmem_ld_wait();
 #pragma unroll
-    for (int c = 0; c < NV; ++c) v[c] += w[c];
+    for (int c = 0; c < NV; ++c) v[c] += a[c] + b[c];
   } else {
     tmem_ld_wait();
   }
@@ -355,24 +359,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t st = smem_u32(smem + (size_t)s * stageBytes);
           const uint32_t xa = st, opa = st + kXStageBytes, opb = st + kXStageBytes + 2 * opBox;
-          if (P.doN) {
+          // N and T steps alternate: an MMA into the accumulator the previous
+          // MMA wrote waits for it, so consecutive MMAs go to different ones
+          const uint32_t dT = tmem + (uint32_t)((2 + ci) * NV);
 #pragma unroll
-            for (int kk = 0; kk < kTK / 16; ++kk) {
+          for (int kk = 0; kk < kTK / 16; ++kk) {
+            const uint32_t boff = (uint32_t)((kk >> 2) * opBox + (kk & 3) * 32);
+            if (P.doN) {
               const uint32_t off = (uint32_t)((kk >> 2) * (kXStageBytes / 2) + (kk & 3) * 32);
-              const uint32_t boff = (uint32_t)((kk >> 2) * opBox + (kk & 3) * 32);
               tc_mma(dN, smem_desc(xa + off, 16, 1024), smem_desc(opa + boff, 16, 1024), idN,
                      (ci > 0 || kk > 0) ? 1u : 0u);
             }
-          }
-          if (P.doT) {
-            const uint32_t dT = tmem + (uint32_t)((2 + ci) * NV);
-#pragma unroll
-            for (int kk = 0; kk < kTM / 16; ++kk) {
-              const uint32_t aoff = (uint32_t)(kk * 2048);
-              const uint32_t boff = (uint32_t)((kk >> 2) * opBox + (kk & 3) * 32);
-              tc_mma(dT, smem_desc(xa + aoff, kXStageBytes / 2, 1024), smem_desc(opb + boff, 16, 1024), idT,
-                     (ri > 0 || kk > 0) ? 1u : 0u);
-            }
+            if (P.doT)
+              tc_mma(dT, smem_desc(xa + (uint32_t)(kk * 2048), kXStageBytes / 2, 1024), smem_desc(opb + boff, 16, 1024),
+                     idT, (ri > 0 || kk > 0) ? 1u : 0u);
           }
           tc_commit(&empty[s]);
         }
@@ -392,13 +392,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 // X = X0 + X1 + X2 and every operand A = A0 + A1 + A2 (OP_BF16X3): each part
 // rounds the float32 residual of the previous ones, so |X - X0 - X1 - X2| <=
 // 2^-27 |X|. The six products X_j A_i with i + j <= 2 leave out terms below
-// 2^-26 |x a|. The leading term X_0 A_0 has a TMEM accumulator of its own and
-// the five others (at most 2^-8 of it) share a second one: tensor-core
-// accumulation rounds the running sum at every MMA, so adding the small
-// terms into the large sum would round it six times as often as a one-part
-// pass does. The epilogue adds the two once. A pass is then as accurate as
-// the one-part pass is on its own inputs, from 6 bytes of X per element
-// instead of 4 (the parts are formed once per call).
+// 2^-26 |x a|. The leading term X_0 A_0 has a TMEM accumulator L of its own
+// and the five others (at most 2^-8 of it) go to two more, S_a and S_b:
+// tensor-core accumulation rounds the running sum at every MMA, so adding
+// the small terms into the large sum would round it six times as often as a
+// one-part pass does. With the operand parts stacked (A_0; A_1; A_2), the
+// small terms take two MMAs of width 2 NV and one of width NV per step:
+//   X_0 [A_1 | A_2] -> [S_a | S_b],  X_1 [A_0 | A_1] -> [S_a | S_b],  X_2 A_0 -> S_a.
+// The epilogue forms L + (S_a + S_b). A pass is then as accurate as the
+// one-part pass is on its own inputs, from 6 bytes of X per element instead
+// of 4 (the parts are formed once per call).
 //
 // A tile's three parts arrive as three 32 KB stages of the X ring. The
 // operand slices change less often and have rings of their own: the A slice
@@ -509,13 +512,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idN = instr_desc(kTM, NV, 0);
-      const uint32_t idT = instr_desc(kTK, NV, 1);
+      const uint32_t idN1 = instr_desc(kTM, NV, 0), idN2 = instr_desc(kTM, 2 * NV, 0);
+      const uint32_t idT1 = instr_desc(kTK, NV, 1), idT2 = instr_desc(kTK, 2 * NV, 1);
       int it = 0, at = 0, bt = 0;
       bool ok = true;
       for (int ri = 0; ri < nrt && ok; ++ri) {
         const int buf = ri & 1;
-        const uint32_t dN = tmem + (uint32_t)(buf * 2 * NV);  // leading term; small terms at + NV
+        const uint32_t dN = tmem + (uint32_t)(buf * 3 * NV);  // L, then S_a, S_b
         int b = 0;
         if (P.doN) {
           if (!mbar_wait(&tempty[buf], ((uint32_t)(ri >> 1) & 1u) ^ 1u, abort_flag, P.wait_ns)) { ok = false; break; }
@@ -540,37 +543,34 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!mbar_wait(&xfull[st], (uint32_t)(it / kStages) & 1u, abort_flag, P.wait_ns)) { ok = false; break; }
             tc_fence_after();
             const uint32_t xa = smem_u32(xring + (size_t)st * kXStageBytes);
-            // term (j, i) goes to the leading accumulator when j = i = 0, else to
-            // the small-term one, whose first term of a row (N) or of the
-            // CTA's rows (T) is (0, 1)
-            if (P.doN) {
-              for (int i = 0; i + j < 3; ++i) {
-                const bool lead = i + j == 0;
-                const uint32_t d = dN + (lead ? 0u : (uint32_t)NV);
-                const bool first = ci == 0 && (lead || (j == 0 && i == 1));
+            // Per K step: part 0 issues L and [S_a | S_b] MMAs, parts 1 and 2
+            // one [S_a | S_b] or S_a MMA; N and T alternate so that
+            // consecutive MMAs go to different accumulators.
+            const uint32_t dT = tmem + (uint32_t)((6 + 3 * ci) * NV);
+            const bool firstN = ci == 0 && j == 0, firstT = ri == 0 && j == 0;
+            // operand rows of the small-term MMA: A_1 (j = 0) or A_0 (j = 1, 2)
+            const uint32_t srow = (uint32_t)(j == 0 ? NV * 128 : 0);
+            const uint32_t idNs = j == 2 ? idN1 : idN2, idTs = j == 2 ? idT1 : idT2;
 #pragma unroll
-                for (int kk = 0; kk < kTK / 16; ++kk) {
-                  const uint32_t off = (uint32_t)((kk >> 2) * (kXStageBytes / 2) + (kk & 3) * 32);
-                  const uint32_t boff = (uint32_t)((kk >> 2) * box + i * NV * 128 + (kk & 3) * 32);
-                  tc_mma(d, smem_desc(xa + off, 16, 1024), smem_desc(opa + boff, 16, 1024), idN,
-                         (first && kk == 0) ? 0u : 1u);
-                }
+            for (int kk = 0; kk < kTK / 16; ++kk) {
+              const uint32_t xoffN = (uint32_t)((kk >> 2) * (kXStageBytes / 2) + (kk & 3) * 32);
+              const uint32_t xoffT = (uint32_t)(kk * 2048);
+              const uint32_t boff = (uint32_t)((kk >> 2) * box + (kk & 3) * 32);
+              const uint32_t acc = kk > 0 ? 1u : 0u;
+              if (j == 0) {
+                if (P.doN)
+                  tc_mma(dN, smem_desc(xa + xoffN, 16, 1024), smem_desc(opa + boff, 16, 1024), idN1,
+                         firstN ? acc : 1u);
+                if (P.doT)
+                  tc_mma(dT, smem_desc(xa + xoffT, kXStageBytes / 2, 1024), smem_desc(opb + boff, 16, 1024), idT1,
+                         firstT ? acc : 1u);
               }
-            }
-            if (P.doT) {
-              const uint32_t dT = tmem + (uint32_t)((4 + 2 * ci) * NV);
-              for (int i = 0; i + j < 3; ++i) {
-                const bool lead = i + j == 0;
-                const uint32_t d = dT + (lead ? 0u : (uint32_t)NV);
-                const bool first = ri == 0 && (lead || (j == 0 && i == 1));
-#pragma unroll
-                for (int kk = 0; kk < kTM / 16; ++kk) {
-                  const uint32_t aoff = (uint32_t)(kk * 2048);
-                  const uint32_t boff = (uint32_t)((kk >> 2) * box + i * NV * 128 + (kk & 3) * 32);
-                  tc_mma(d, smem_desc(xa + aoff, kXStageBytes / 2, 1024), smem_desc(opb + boff, 16, 1024), idT,
-                         (first && kk == 0) ? 0u : 1u);
-                }
-              }
+              if (P.doN)
+                tc_mma(dN + NV, smem_desc(xa + xoffN, 16, 1024), smem_desc(opa + boff + srow, 16, 1024), idNs,
+                       firstN ? acc : 1u);
+              if (P.doT)
+                tc_mma(dT + NV, smem_desc(xa + xoffT, kXStageBytes / 2, 1024), smem_desc(opb + boff + srow, 16, 1024),
+                       idTs, firstT ? acc : 1u);
             }
             tc_commit(&xempty[st]);
           }
@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_commit(&tdone);
     }
   } else {
-    epilogue<NV, 2>(P, tmem, stage_area, tfull, tempty, &tdone, abort_flag, rt0, ct0, nrt, nct, rg, cg);
+    epilogue<NV, 3>(P, tmem, stage_area, tfull, tempty, &tdone, abort_flag, rt0, ct0, nrt, nct, rg, cg);
   }
   teardown(P, tmem, &tdone, abort_flag);
 }
@@ -748,7 +748,7 @@ XPassPlan xpass_tc_plan(int n, int m, int nu, int num_sms, int parts) {
   pl.tiles_r = ceil_div(n, kTM);
   pl.tiles_c = ceil_div(m, kTK);
   pl.NV = round_up(nu, 16);
-  const int maxct = max_col_tiles(pl.NV, parts == 3 ? 2 : 1);
+  const int maxct = max_col_tiles(pl.NV, parts == 3 ? 3 : 1);
   long best = -1;
   int bestr = 1, bestc = pl.tiles_c;
   for (int S_c = 1; S_c <= pl.tiles_c; ++S_c) {
@@ -804,7 +804,7 @@ cudaError_t xpass_tc_launch(const XPassPlan& pl, const XPassArgs& a, cudaStream_
   P.partN = a.partN;
   P.partT = a.partT;
   P.ctrl = a.ctrl;
-  P.tmem_cols = tmem_cols_for(pl.NV, ceil_div(pl.tiles_c, pl.S_c), pl.parts == 3 ? 2 : 1);
+  P.tmem_cols = tmem_cols_for(pl.NV, ceil_div(pl.tiles_c, pl.S_c), pl.parts == 3 ? 3 : 1);
   P.wait_ns = wait_limit_ns();
   P.withhold = injected_fault() == NMF_FAULT_XPASS_COPY ? 1 : 0;
   if (pl.parts == 3) {
