@@ -57,6 +57,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-rre", action="store_true", help="skip the time-to-RRE runs")
     ap.add_argument("--count", type=int, default=256, help="batched workload: number of problems")
+    ap.add_argument("--peaks", action="store_true",
+                    help="build and run the FP64 / FP32 peak probe (paper_1812_04315_gb300/probes/peaks.cu)")
     ap.add_argument("--workload", choices=["single", "batched", "paper"], default="single",
                     help="single: the headline problem; batched: 256 uneven problems in one batched solve; "
                          "paper: the paper's setting (n = m in 500, 5000, 10000; p = 15, nu = 25, Max_iter 500), "
@@ -870,8 +872,28 @@ def run_reference(args):
                               "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def run_peaks(args):
+    """Builds the FP64 / FP32 peak probe with nvcc for this GPU and prints its JSON line."""
+    import shutil
+    import subprocess
+    import tempfile
+    src = os.path.join(ROOT, "paper_1812_04315_gb300", "probes", "peaks.cu")
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    with tempfile.TemporaryDirectory() as tmp:
+        exe = os.path.join(tmp, "peaks")
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-o", exe, src],
+                       check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.strip()
+    rec = json.loads(out)
+    rec["probe"] = "paper_1812_04315_gb300/probes/peaks.cu"
+    print(json.dumps(rec), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.peaks:
+        run_peaks(args)
+        return
     if args.workload == "batched":
         run_batched(args)
     elif args.workload == "paper":

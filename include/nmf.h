@@ -70,7 +70,7 @@ int nmf_version(void);
 nmf_status_t nmf_workspace_status(nmf_stream_t stream, const void* workspace, int* status);
 
 /* ------------------------------------------------------------------------ */
-/* Gaussian sketches (Alg. 2, first line: "Draw Gaussian random matrices")   */
+/* Gaussian sketches (Alg. 2: the two Gaussian test matrices)                */
 /* ------------------------------------------------------------------------ */
 /*
  * out (rows x cols, device, row-major) <- iid N(0, 1) values, counter-based:
@@ -91,7 +91,7 @@ size_t nmf_compress_workspace_size(int n, int m, int nu, nmf_prec_t prec);
 /*
  * Alg. 2 with q power steps, each orthonormalisation a CholeskyQR2 whose Gram
  * matrix is accumulated, factorised and inverted in extended (float-float)
- * precision; then X_L = L X and X_R = X R (first line of Alg. 1).
+ * precision; then X_L = L X and X_R = X R (the compression step of Alg. 1).
  *
  *  X        n x m input, nonnegative (not checked).
  *  omega_L  m x nu Gaussian sketch, or NULL to draw it from `seed` (stream 0).
@@ -101,10 +101,12 @@ size_t nmf_compress_workspace_size(int n, int m, int nu, nmf_prec_t prec);
  *  R        out, m x nu, orthonormal columns: R = (Q_R^(q))^T.
  *  XL       out, nu x m, X_L = L X.
  *  XR       out, n x nu, X_R = X R.
- * Alg. 2's last line names the half-step bases Q~^(q), which have the wrong
- * shapes; the full-step bases Q^(q) are used. prec selects how the 2q+2
- * passes over X compute (NMF_PREC_BF16: X rounded to bfloat16 once, tensor
- * cores; NMF_PREC_FP32: float32 CUDA cores).
+ * Alg. 2's output step names the half-step bases Q~^(q), which have the
+ * wrong shapes; the full-step bases Q^(q) are used. prec selects how the
+ * 2q+2 passes over X compute: NMF_PREC_BF16: X rounded to bfloat16 once,
+ * tensor cores; NMF_PREC_FP32: float32 accuracy, on the tensor cores with X
+ * and the operands split into three bfloat16 parts each (widths nu <= 32),
+ * else float32 CUDA cores.
  */
 nmf_status_t nmf_compress(nmf_stream_t stream, int n, int m, int nu, int q, nmf_prec_t prec,
                           const float* X, const float* omega_L, const float* omega_R, uint64_t seed,
@@ -115,7 +117,7 @@ nmf_status_t nmf_compress(nmf_stream_t stream, int n, int m, int nu, int q, nmf_
  * Compression variants (the paper's Sec. 3 names the alternatives; Alg. 2 is
  * the one it studies):
  *  NMF_VARIANT_SUBSPACE      Alg. 2 as nmf_compress reads it (the default).
- *  NMF_VARIANT_SWAPPED       Alg. 2's last line with the tildes swapped, the
+ *  NMF_VARIANT_SWAPPED       Alg. 2's output step with the tildes swapped, the
  *                            other dimensionally valid reading: L = Q~_R^(q),
  *                            R = Q~_L^(q), the half-step bases (q >= 1).
  *  NMF_VARIANT_SINGLE_CHAIN  one chain (omega_L only): L = Q_L^(q)^T and R the
@@ -423,7 +425,7 @@ nmf_status_t nmf_dual_product(nmf_stream_t stream, int n, int m, int k, nmf_prec
 size_t nmf_project_workspace_size(int n, int m, int nu, nmf_prec_t prec);
 
 /*
- * The first line of Alg. 1 for given bases: X_L = L X (nu x m) and
+ * The compression step of Alg. 1 for given bases: X_L = L X (nu x m) and
  * X_R = X R (n x nu) from one pass over X (as nmf_compress ends). L is
  * nu x n, R is m x nu (device, row-major); prec as nmf_compress. Used where
  * the bases stay fixed while X changes (the differentiated map of

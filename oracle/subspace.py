@@ -6,15 +6,16 @@ Shapes (Sec. 3): L is nu x n, R is m x nu, X_L = L X is nu x m, X_R = X R is
 n x nu, with p <= nu << min(n, m).
 
 Readings of points the paper leaves open:
-  * "orthonormal basis" / "QR decomposition" = the Q factor of the thin
+  * an orthonormal basis from a QR decomposition = the Q factor of the thin
     Householder QR with the signs fixed so that diag(R) > 0 (unique when the
     input has full column rank). A wide input (nu x m, orthonormal rows
     wanted) is orthonormalised through its transpose.
-  * Alg. 2's last line reads L = Q~_L^(q), R = Q~_R^(q), which has the wrong
+  * Alg. 2's output step reads L = Q~_L^(q), R = Q~_R^(q), which has the wrong
     shapes (Q~_L^(q) is m x nu while L must be nu x n). The oracle takes the
     last full-step bases: L = (Q_L^(q))^T and R = (Q_R^(q))^T, so that
-    L L^T = I and R^T R = I (Sec. 3's "orthonormal columns and rows", with
-    rows and columns swapped to match the shapes).
+    L L^T = I and R^T R = I (Sec. 3 asks for orthonormal columns of one basis
+    and rows of the other; here rows and columns are swapped to match the
+    shapes).
 """
 
 from __future__ import annotations
@@ -57,7 +58,7 @@ def randomized_subspace_iteration(X, nu: int, q: int, Omega_L, Omega_R):
 
 
 def compress(X, nu: int, q: int, Omega_L, Omega_R):
-    """L, R from Alg. 2, then X_L = L X and X_R = X R (first line of Alg. 1)."""
+    """L, R from Alg. 2, then X_L = L X and X_R = X R (the compression step of Alg. 1)."""
     X = np.asarray(X, dtype=np.float64)
     L, R = randomized_subspace_iteration(X, nu, q, Omega_L, Omega_R)
     return L, R, L @ X, X @ R
@@ -86,7 +87,7 @@ def compression_bases(X, nu: int, q: int, Omega_L, Omega_R, variant: str = "subs
     """(L, R) of one compression variant, L nu x n and R m x nu.
 
     subspace  Alg. 2 as read in the module docstring (the default);
-    swapped   Alg. 2's last line with the tildes swapped, the other
+    swapped   Alg. 2's output step with the tildes swapped, the other
               dimensionally valid reading: L = Q~_R^(q) (nu x n, orthonormal
               rows), R = Q~_L^(q) (m x nu, orthonormal columns); needs q >= 1;
     single    one chain (Omega_L only): Q_L^(q) as in Alg. 2 gives L, and the

@@ -238,7 +238,8 @@ VARIANTS = {"subspace": 0, "swapped": 1, "single": 2, "power": 3, "gaussian": 4}
 
 def compress(X, nu: int, q: int, prec: int = PREC_BF16, omega_L=None, omega_R=None, seed: int = 0, ws=None,
              out=None, variant: str = "subspace"):
-    """Alg. 2 (or a named variant) + first line of Alg. 1: returns (L nu x n, R m x nu, X_L nu x m, X_R n x nu)."""
+    """Alg. 2 (or a named variant) + the compression step of Alg. 1: returns (L nu x n, R m x nu, X_L nu x m,
+    X_R n x nu)."""
     torch = _torch()
     n, m = X.shape
     _check_f32("X", X, (n, m))

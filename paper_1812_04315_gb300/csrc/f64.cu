@@ -1,5 +1,5 @@
-// f64.cu -- float64 twins of nmf_compress (Alg. 2 and the first line of
-// Alg. 1) and nenmf_solve (Alg. 1 / plain NeNMF with the inner loop of
+// f64.cu -- float64 twins of nmf_compress (Alg. 2 and the compression step
+// of Alg. 1) and nenmf_solve (Alg. 1 / plain NeNMF with the inner loop of
 // Sec. 2): the same steps in the same order, computed in float64 on the GPU.
 // They exist for parity at tight tolerances on small problems, not for speed
 // (float64 runs at 1/64 of the float32 rate here): every product is a
