@@ -530,6 +530,67 @@ nmf_status_t nmf_rre(nmf_stream_t stream, int n, int m, int p, const float* X, c
 nmf_status_t nmf_rre_static(nmf_stream_t stream, int n, int m, int p, const float* X, const float* G,
                             const float* F, double* out);
 
+/* ------------------------------------------------------------------------ */
+/* Row-sharded runs (X split by row blocks across GPUs)                      */
+/* ------------------------------------------------------------------------ */
+/*
+ * With X split by row blocks, every product X A of a pass is local, every
+ * X^T B is a partial sum to all-reduce, and the orthonormal bases of Alg. 2
+ * (CholeskyQR) need their Gram matrix summed over the row blocks. In the
+ * outer loop of Alg. 1 the rows of G are local (X_R = X R has the rows of X),
+ * G_L = L G is a partial sum, and the stop test of the inner loop (Sec. 2)
+ * sums ||P grad||^2 over all row blocks. The three calls below are the
+ * per-GPU steps between those collectives; the Python module
+ * paper_1812_04315_gb300.sharded drives them.
+ *
+ * nmf_gram: S = Y^T Y (nu x nu, float64, both triangles written) of this
+ * GPU's N x nu rows Y (device, row-major), summed in float-float (products
+ * exact, ~48-bit sums) in a fixed order, so that the partial Grams of all
+ * row blocks can be added by an all-reduce. 1 <= nu <= NMF_MAX_SKETCH.
+ */
+size_t nmf_gram_workspace_size(int N, int nu);
+nmf_status_t nmf_gram(nmf_stream_t stream, int N, int nu, const float* Y, double* S, void* workspace,
+                      size_t workspace_bytes);
+
+/*
+ * nmf_orth_apply: one CholeskyQR pass over this GPU's rows: Q = Y R^{-1}
+ * (N x nu, device, row-major; may alias Y) with R^T R = S the given
+ * (summed) Gram, S factorised in float-float; when a pivot is not safely
+ * positive, S + 1e-10 tr(S) I is factorised instead (shifted CholeskyQR), and
+ * a second pass is then still needed. Every row block applies the same R.
+ * A Gram whose diagonal is not positive sets NMF_ERR_NOT_SPD in the
+ * workspace status.
+ */
+size_t nmf_orth_apply_workspace_size(int N, int nu);
+nmf_status_t nmf_orth_apply(nmf_stream_t stream, int N, int nu, const float* Y, const double* S, float* Q,
+                            void* workspace, size_t workspace_bytes);
+
+/*
+ * nenmf_nnls_block: iterations k0 .. k0 + kb - 1 of the Nesterov inner loop
+ * of Sec. 2 on the N columns of a p x N unknown (this GPU's columns),
+ * min_{F >= 0} 1/2 tr(F^T H F) - tr(B^T F):
+ *   f_k = max(0, y_k - (H y_k - b) / L_c),  y_{k+1} = f_k + beta_k (f_k - f_{k-1}),
+ * L_c = lambda_max(H) (computed here from H; written to *Lc), beta_k from the
+ * alpha recurrence (beta_0 = 0), as nenmf_solve without restart.
+ *  H       p x p, symmetric (device, row-major).
+ *  B       p x N (device, row-major).
+ *  Y       p x N in/out: y_{k0} on entry (y_0 = F^t), y_{k0+kb} on return.
+ *  Fprev   p x N in/out: f_{k0-1} (any value when k0 = 0), f_{k0+kb-1} on return.
+ *  keep    [kb][p][N] out: f_k of every iteration of the block.
+ *  pg2     [max(kb, 1)] out (device, float64): this GPU's share of
+ *          ||P grad(f_k)||_F^2, P grad = grad where f > 0, min(0, grad) where
+ *          f = 0 (summed over its columns in a fixed order).
+ * kb = 0 evaluates pg2[0] at Y (no step); with L_c = 0 no step is taken
+ * either and every pg2 entry holds the value at Y. The caller sums pg2 over
+ * the row blocks and stops at the first k (k + 1 >= min_inner) whose total
+ * is <= eps^2, taking keep[k - k0]. 1 <= p <= NMF_MAX_RANK,
+ * 0 <= k0, k0 + kb <= max_inner.
+ */
+size_t nenmf_nnls_block_workspace_size(int N, int p, int kb, int max_inner);
+nmf_status_t nenmf_nnls_block(nmf_stream_t stream, int N, int p, const float* H, const float* B, float* Y,
+                              float* Fprev, int k0, int kb, int max_inner, float* keep, double* pg2, double* Lc,
+                              void* workspace, size_t workspace_bytes);
+
 #ifdef __cplusplus
 }
 #endif

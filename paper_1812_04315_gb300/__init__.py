@@ -119,6 +119,12 @@ def lib() -> ctypes.CDLL:
                                     vp, sz]),
         "nenmf_backward_workspace_size": (sz, [ctypes.POINTER(Problem), ctypes.POINTER(Params)]),
         "nenmf_backward": (i, [vp, ctypes.POINTER(Problem), ctypes.POINTER(Params)] + [vp] * 11 + [vp, sz]),
+        "nmf_gram_workspace_size": (sz, [i, i]),
+        "nmf_gram": (i, [vp, i, i, vp, vp, vp, sz]),
+        "nmf_orth_apply_workspace_size": (sz, [i, i]),
+        "nmf_orth_apply": (i, [vp, i, i, vp, vp, vp, vp, sz]),
+        "nenmf_nnls_block_workspace_size": (sz, [i, i, i, i]),
+        "nenmf_nnls_block": (i, [vp, i, i, vp, vp, vp, vp, i, i, i, vp, vp, vp, vp, sz]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -139,7 +145,9 @@ def exported_symbols():
             "nmf_compress_batched_workspace_size", "nmf_compress_batched", "nmf_compress_f64_workspace_size",
             "nmf_compress_f64", "nenmf_solve_f64_workspace_size", "nenmf_solve_f64",
             "nenmf_backward_f64_workspace_size", "nenmf_backward_f64", "nmf_project_workspace_size", "nmf_project",
-            "nenmf_batch_autotune_workspace_size", "nenmf_batch_autotune", "nmf_inject_fault"]
+            "nenmf_batch_autotune_workspace_size", "nenmf_batch_autotune", "nmf_inject_fault",
+            "nmf_gram_workspace_size", "nmf_gram", "nmf_orth_apply_workspace_size", "nmf_orth_apply",
+            "nenmf_nnls_block_workspace_size", "nenmf_nnls_block"]
 
 
 # ---------------------------------------------------------------------------
@@ -666,3 +674,56 @@ def backward_f64(problem: ProblemF64, G0, F0, dG_T, dF_T, max_outer: int, max_in
                                  _ptr(dF_T), *[_ptr(t) for t in out], _ptr(dX), _ptr(ws), ws.numel()),
         "nenmf_backward_f64")
     return (*out, dX)
+
+
+# ---------------------------------------------------------------------------
+# row-sharded runs: the per-GPU steps between the collectives
+# ---------------------------------------------------------------------------
+
+def gram(Y, ws=None):
+    """nmf_gram: Y^T Y (float64 device tensor) of the N x nu rows Y."""
+    torch = _torch()
+    N, nu = Y.shape
+    _check_f32("Y", Y, (N, nu))
+    S = torch.empty((nu, nu), dtype=torch.float64, device="cuda")
+    if ws is None:
+        ws = workspace(lib().nmf_gram_workspace_size(N, nu))
+    _ok(lib().nmf_gram(_stream(), N, nu, _ptr(Y), _ptr(S), _ptr(ws), ws.numel()), "nmf_gram")
+    return S
+
+
+def orth_apply(Y, S, out=None, ws=None):
+    """nmf_orth_apply: Y R^{-1} with R^T R = S (one CholeskyQR pass over these rows)."""
+    torch = _torch()
+    N, nu = Y.shape
+    _check_f32("Y", Y, (N, nu))
+    if S.device.type != "cuda" or S.dtype != torch.float64 or tuple(S.shape) != (nu, nu) or not S.is_contiguous():
+        raise ValueError("S must be a contiguous nu x nu float64 CUDA tensor")
+    if out is None:
+        out = torch.empty_like(Y)
+    if ws is None:
+        ws = workspace(lib().nmf_orth_apply_workspace_size(N, nu))
+    _ok(lib().nmf_orth_apply(_stream(), N, nu, _ptr(Y), _ptr(S), _ptr(out), _ptr(ws), ws.numel()),
+        "nmf_orth_apply")
+    return out
+
+
+def nnls_block(H, B, Y, Fprev, k0: int, kb: int, max_inner: int, ws=None):
+    """nenmf_nnls_block: iterations k0 .. k0+kb-1 of the inner loop on these columns.
+
+    Updates Y and Fprev in place; returns (keep [kb, p, N], pg2 [max(kb, 1)] float64, L_c float64),
+    all device tensors."""
+    torch = _torch()
+    p, N = B.shape
+    _check_f32("H", H, (p, p))
+    _check_f32("B", B, (p, N))
+    _check_f32("Y", Y, (p, N))
+    _check_f32("Fprev", Fprev, (p, N))
+    keep = torch.empty((max(kb, 1), p, N), dtype=torch.float32, device="cuda")
+    pg2 = torch.empty(max(kb, 1), dtype=torch.float64, device="cuda")
+    lc = torch.empty(1, dtype=torch.float64, device="cuda")
+    if ws is None:
+        ws = workspace(lib().nenmf_nnls_block_workspace_size(N, p, kb, max_inner))
+    _ok(lib().nenmf_nnls_block(_stream(), N, p, _ptr(H), _ptr(B), _ptr(Y), _ptr(Fprev), k0, kb, max_inner,
+                               _ptr(keep), _ptr(pg2), _ptr(lc), _ptr(ws), ws.numel()), "nenmf_nnls_block")
+    return keep[:kb], pg2, lc

@@ -127,6 +127,7 @@ struct RowJob {
   const int* run_flag;  // optional: skip the job unless *run_flag != 0
   const int* skip_flag; // optional: skip the job when *skip_flag != 0
   int diag_only;        // apply step: R = diag(sqrt(S_cc)) (columns rescaled to unit norm, span kept)
+  int gram_only;        // src given: no factorisation, src's rows kept as they are (Gram partial only)
   float skip_tol;       // apply step: keep src as it is when its Gram is within this of I (0: never)
   // apply step, one pass enough: when the factorisation did not shift and the
   // ratio of its largest to smallest pivot is below single_ratio, the rows

@@ -423,8 +423,10 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
   } else {
     // the skip is only taken while no factorisation of this basis has shifted
     const int shifted_before = J.shift_flag ? *((volatile const int*)J.shift_flag) : 0;
-    const int sh = factor_gram(J.gram_in, J.gram_parts, nu, Ys, Ahi, Alo, Ihi, Ilo, ctrl, J.diag_only != 0,
-                               shifted_before ? 0.f : J.skip_tol, shifted_before ? 0.f : J.single_ratio);
+    const int sh = J.gram_only ? 2
+                               : factor_gram(J.gram_in, J.gram_parts, nu, Ys, Ahi, Alo, Ihi, Ilo, ctrl,
+                                             J.diag_only != 0, shifted_before ? 0.f : J.skip_tol,
+                                             shifted_before ? 0.f : J.single_ratio);
     if (sh < 0) return;
     const bool keep_rows = sh == 2;
     single = sh == 3;

@@ -58,6 +58,13 @@ def test_workspace_queries(L):
     # row blocks of 64 rows, beyond which blocks walk several row blocks
     assert L.nmf_rre_workspace_size(64 * 65535, 256, 4) == 65535 * 16 + 16
     assert L.nmf_rre_workspace_size(64 * 65535 + 1, 256, 4) == 65535 * 16 + 16
+    # the row-sharded steps: sizes out of range are refused with 0
+    assert L.nmf_gram_workspace_size(1000, 20) > 0 and L.nmf_gram_workspace_size(0, 20) == 0
+    assert L.nmf_gram_workspace_size(10, 65) == 0
+    assert L.nmf_orth_apply_workspace_size(10, 64) > 0 and L.nmf_orth_apply_workspace_size(10, 0) == 0
+    assert L.nenmf_nnls_block_workspace_size(100, 32, 16, 40) > 0
+    assert L.nenmf_nnls_block_workspace_size(100, 33, 16, 40) == 0
+    assert L.nenmf_nnls_block_workspace_size(100, 4, -1, 40) == 0
     assert L.nmf_rre_workspace_size(64 * 70000, 512, 4) == 2 * 65535 * 16 + 32
     import paper_1812_04315_gb300 as pkg
     pr = pkg._problem(pkg.COMPRESSED, 100, 90, 4, 8, 0)
