@@ -9,7 +9,7 @@
 //            product over its share of the summed index in shared-memory
 //            chunks; the cluster's partials are summed in rank order through
 //            distributed shared memory, so every CTA holds the same W;
-//   H      = W W^T and L_c = lambda_max(H) (one warp per CTA);
+//   H      = W W^T and L_c = lambda_max(H) (by the whole CTA);
 //   loop   every thread owns whole vectors (rows of G or columns of F) and
 //          runs blocks of kBlockIters Nesterov iterations on each, state in
 //          registers, recording ||P grad||^2 of every iteration; after a
@@ -112,6 +112,7 @@ struct Shared {
   float* Ws;   // [pcap][kBWs]
   float* Hs;   // [pcap * pcap]
   float* Ms;   // eigenvalue scratch
+  float* dg;   // [2][pcap]: diagonal of the squared iterate (lambda_max by the whole CTA)
   float2* pgc; // [2][kBlockIters] this CTA's float-float stop-test partials (read by the cluster)
   float* red;  // [warps][kBlockIters]
   float* pgt;  // [kBlockIters][threads]: each thread's ||P grad||^2 sums per iteration of the block
@@ -302,10 +303,10 @@ __device__ PhaseOut phase(const Side& s, int p, int nu, int mode, double eps2, c
   const int j0 = (int)((long long)s.J * rank / CS), j1 = (int)((long long)s.J * (rank + 1) / CS);
   float invL = 0.f;
   if (mode == 1) {
-    if (tid < 32) {
-      const double lam = lambda_max_warp<PM>(S.Hs, S.Ms, p);
-      if (tid == 0) lam_s = isfinite(lam) ? (float)lam : -1.f;
-    }
+    // L_c by every thread of the CTA (one upper-triangle entry each per squaring)
+    __shared__ double lam_d;
+    const double lam = lambda_max_cta<PM>(S.Hs, S.Ms, S.dg, &lam_d, p);
+    if (tid == 0) lam_s = isfinite(lam) ? (float)lam : -1.f;
     __syncthreads();
     const float Lc = lam_s;
     out.lc = Lc;
@@ -438,8 +439,8 @@ __device__ void solve_problem(const BatchDesc& d, int inst, const BatchArgs& A, 
   const int nev = (A.tol > 0.0 && A.tol_mode == NENMF_TOL_REL) ? 2 : 0;
   double eps2 = (A.tol > 0.0 && nev == 0) ? A.tol * A.tol : -1.0;
   double ev = 0.0;
-  long long tot[2] = {0, 0};
-  PhaseOut last[2] = {};
+  long long totG = 0, totF = 0;  // per side (no runtime-indexed arrays: they would live in local memory)
+  PhaseOut lastG{}, lastF{};
   int bad = 0;
   const int steps = nev + 2 * A.max_outer;
   for (int st = 0; st < steps; ++st) {
@@ -450,8 +451,13 @@ __device__ void solve_problem(const BatchDesc& d, int inst, const BatchArgs& A, 
       ev += o.pg2;
       if (st == nev - 1) eps2 = A.tol * A.tol * ev;
     } else {
-      tot[sd] += o.iters;
-      last[sd] = o;
+      if (sd) {
+        totF += o.iters;
+        lastF = o;
+      } else {
+        totG += o.iters;
+        lastG = o;
+      }
       bad |= o.bad;
     }
   }
@@ -470,17 +476,23 @@ __device__ void solve_problem(const BatchDesc& d, int inst, const BatchArgs& A, 
       st->status = bad ? NMF_ERR_NONFINITE : NMF_OK;
       st->outer_done = A.max_outer;
       st->eps = eps2 > 0.0 ? sqrt(eps2) : 0.0;
-      for (int sd = 0; sd < 2; ++sd) {
-        st->last_inner[sd] = last[sd].iters;
-        st->total_inner[sd] = tot[sd];
-        st->pg_norm[sd] = sqrt(fmax(last[sd].pg2, 0.0));
-        st->lipschitz[sd] = last[sd].lc;
-      }
+      st->last_inner[0] = lastG.iters;
+      st->last_inner[1] = lastF.iters;
+      st->total_inner[0] = totG;
+      st->total_inner[1] = totF;
+      st->pg_norm[0] = sqrt(fmax(lastG.pg2, 0.0));
+      st->pg_norm[1] = sqrt(fmax(lastF.pg2, 0.0));
+      st->lipschitz[0] = lastG.lc;
+      st->lipschitz[1] = lastF.lc;
     }
   }
 }
 
-__global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs A) {
+// PMAX: the largest padded rank of the batch. The kernel instantiates the
+// rank classes up to PMAX only, so a batch of small ranks does not pay the
+// registers of the largest class.
+template <int PMAX>
+__global__ void __launch_bounds__(kBatchThreads, 1) batched_kernel(BatchArgs A) {
   extern __shared__ __align__(16) float dyn[];
   const int TB = blockDim.x;
   const int pc = A.pcap, nc = A.nucap;
@@ -500,6 +512,8 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs A) {
   q += pc * pc;
   S.Ms = q;
   q += 2 * pc * (((pc / 4) & 1) ? pc : pc + 4);
+  S.dg = q;
+  q += 2 * pc;
   S.pgc = reinterpret_cast<float2*>(q);
   q += 4 * kBlockIters;
   S.red = q;
@@ -520,14 +534,13 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs A) {
     const int inst = A.order[ii];
     const BatchDesc d = A.desc[inst];
     // the smallest padded rank that holds p
-    switch (d.p <= 4 ? 4 : d.p <= 8 ? 8 : d.p <= 12 ? 12 : d.p <= 16 ? 16 : d.p <= 24 ? 24 : 32) {
-      case 4: solve_problem<4>(d, inst, A, S, LS, ph); break;
-      case 8: solve_problem<8>(d, inst, A, S, LS, ph); break;
-      case 12: solve_problem<12>(d, inst, A, S, LS, ph); break;
-      case 16: solve_problem<16>(d, inst, A, S, LS, ph); break;
-      case 24: solve_problem<24>(d, inst, A, S, LS, ph); break;
-      default: solve_problem<32>(d, inst, A, S, LS, ph); break;
-    }
+    const int pm = d.p <= 4 ? 4 : d.p <= 8 ? 8 : d.p <= 12 ? 12 : d.p <= 16 ? 16 : d.p <= 24 ? 24 : 32;
+    if (pm == 4) solve_problem<4>(d, inst, A, S, LS, ph);
+    if constexpr (PMAX >= 8) if (pm == 8) solve_problem<8>(d, inst, A, S, LS, ph);
+    if constexpr (PMAX >= 12) if (pm == 12) solve_problem<12>(d, inst, A, S, LS, ph);
+    if constexpr (PMAX >= 16) if (pm == 16) solve_problem<16>(d, inst, A, S, LS, ph);
+    if constexpr (PMAX >= 24) if (pm == 24) solve_problem<24>(d, inst, A, S, LS, ph);
+    if constexpr (PMAX >= 32) if (pm == 32) solve_problem<32>(d, inst, A, S, LS, ph);
   }
   cl_sync();  // no CTA leaves while another may read its shared memory
 }
@@ -553,11 +566,23 @@ __global__ void int_upload_kernel(int* dst, IntChunk c) {
 
 int pad_p(int p) { return p <= 4 ? 4 : p <= 8 ? 8 : p <= 12 ? 12 : p <= 16 ? 16 : p <= 24 ? 24 : 32; }
 
+// The instantiation for a batch whose largest padded rank is pmax.
+const void* batched_fn(int pmax) {
+  switch (pad_p(pmax)) {
+    case 4: return (const void*)batched_kernel<4>;
+    case 8: return (const void*)batched_kernel<8>;
+    case 12: return (const void*)batched_kernel<12>;
+    case 16: return (const void*)batched_kernel<16>;
+    case 24: return (const void*)batched_kernel<24>;
+    default: return (const void*)batched_kernel<32>;
+  }
+}
+
 size_t batched_smem(int pcap, int nucap, int tb) {
   const size_t sv = tb + 4;
   size_t f = pcap * sv + nucap * sv + round_up(2 * pcap * nucap, 4) + round_up(pcap * kBWs, 4) + pcap * pcap;
-  f += 2 * pcap * (((pcap / 4) & 1) ? pcap : pcap + 4) + 4 * kBlockIters + (kBatchThreads / 32) * kBlockIters +
-       kBlockIters * tb;
+  f += 2 * pcap * (((pcap / 4) & 1) ? pcap : pcap + 4) + 2 * pcap + 4 * kBlockIters +
+       (kBatchThreads / 32) * kBlockIters + kBlockIters * tb;
   f = round_up_sz(f, 2);
   return f * sizeof(float) + kBlockIters * sizeof(double);
 }
@@ -580,7 +605,7 @@ int active_clusters(int cs, int pmax, int numax, int tb) {
     for (const auto& e : cache)
       if (e[0] == dev && e[1] == cs * 1000 + tb && e[2] == pmax * 100 + numax) return e[3];
   }
-  const void* fn = (const void*)batched_kernel;
+  const void* fn = batched_fn(pmax);
   const size_t smem = batched_smem(pmax, numax, tb);
   int n = 0;
   if (allow_dynamic_smem(fn, (int)smem) == cudaSuccess) {
@@ -823,7 +848,7 @@ extern "C" nmf_status_t nenmf_solve_batched(nmf_stream_t stream, int count, cons
   a.tol = params->tol;
   a.stats = stats;
   a.ctrl = w.ctrl;
-  const void* fn = (const void*)batched_kernel;
+  const void* fn = batched_fn(pl.pmax);
   const size_t smem = batched_smem(pl.pmax, pl.numax, pl.threads);
   NMF_CU(allow_dynamic_smem(fn, (int)smem));
   cudaLaunchConfig_t cfg{};
