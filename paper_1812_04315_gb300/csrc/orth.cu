@@ -329,6 +329,10 @@ __device__ int factor_gram(const float2* gram, int parts, int nu, float* stage, 
 }
 
 __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control* ctrl) {
+  // launched as a programmatic dependent: wait for the predecessor's writes
+  // (its X pass partials, Gram partials, flags) before reading anything
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   if (call_failed(ctrl)) return;
   int jj = 0;
   while (jj + 1 < jobs.njobs && (int)blockIdx.x >= jobs.start[jj + 1]) ++jj;
@@ -565,9 +569,18 @@ cudaError_t rows_launch(const RowJob* jobs, int njobs, Control* ctrl, cudaStream
   const size_t smem = rows_smem();
   cudaError_t e = allow_dynamic_smem((const void*)rows_kernel, (int)smem);
   if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(total);
+  cfg.blockDim = dim3(kRowThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   count_launches(1);
-  rows_kernel<<<total, kRowThreads, smem, s>>>(rj, ctrl);
-  return cudaGetLastError();
+  return cudaLaunchKernelEx(&cfg, rows_kernel, rj, ctrl);
 }
 
 }  // namespace nmf

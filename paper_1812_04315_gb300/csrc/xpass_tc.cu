@@ -267,6 +267,8 @@ __device__ __forceinline__ void teardown(const TcParams& P, uint32_t tmem, uint6
 template <int NV>
 __global__ void __launch_bounds__(kThreads, 1)
     xpass_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcParams P) {
+  // launched as a programmatic dependent: the operands come from the previous kernel
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (call_failed(P.ctrl)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -415,6 +417,8 @@ __host__ __device__ constexpr int op3_tile_bytes(int NV) { return 2 * op3_box_by
 template <int NV>
 __global__ void __launch_bounds__(kThreads, 1)
     xpass_tc3_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcParams P) {
+  // launched as a programmatic dependent: the operands come from the previous kernel
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (call_failed(P.ctrl)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -691,14 +695,32 @@ __global__ void to_tiles_kernel(const float* __restrict__ X, int n, int m, int t
   }
 }
 
+// Launch with programmatic dependent launch allowed: the kernel's CTAs may
+// start while the previous kernel on the stream finishes, and wait
+// (griddepcontrol.wait) before reading anything it wrote.
+cudaError_t launch_pdl(const void* fn, int ctas, size_t smem, cudaStream_t s, const CUtensorMap& mA,
+                       const CUtensorMap& mB, const TcParams& P) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {const_cast<CUtensorMap*>(&mA), const_cast<CUtensorMap*>(&mB), const_cast<TcParams*>(&P)};
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 template <int NV>
 cudaError_t launch_nv(const CUtensorMap& mA, const CUtensorMap& mB, const TcParams& P, int ctas, cudaStream_t s) {
   const size_t smem = tc_smem_bytes(NV);
   cudaError_t e = allow_dynamic_smem((const void*)xpass_tc_kernel<NV>, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  xpass_tc_kernel<NV><<<ctas, kThreads, smem, s>>>(mA, mB, P);
-  return cudaGetLastError();
+  return launch_pdl((const void*)xpass_tc_kernel<NV>, ctas, smem, s, mA, mB, P);
 }
 
 // Three-part kernel: X ring stages that fit beside the two operand rings
@@ -718,8 +740,7 @@ cudaError_t launch3_nv(const CUtensorMap& mA, const CUtensorMap& mB, const TcPar
   cudaError_t e = allow_dynamic_smem((const void*)xpass_tc3_kernel<NV>, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  xpass_tc3_kernel<NV><<<ctas, kThreads, smem, s>>>(mA, mB, P);
-  return cudaGetLastError();
+  return launch_pdl((const void*)xpass_tc3_kernel<NV>, ctas, smem, s, mA, mB, P);
 }
 
 }  // namespace
