@@ -96,7 +96,11 @@ __device__ __forceinline__ bool grid_wait(unsigned int* bar, unsigned int target
     cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(*bar);
     int ok = 1;
     const unsigned long long t0 = global_ns();
+    unsigned int spins = 0;
     while (cnt.load(cuda::memory_order_acquire) < target) {
+      // the abort flag and the clock every 16 polls: a tighter loop notices
+      // the last arrival sooner, and the wait stays bounded
+      if ((++spins & 15u) != 0u) continue;
       if (*((volatile int*)&c->abort)) { ok = 0; break; }
       if (global_ns() - t0 > wait_ns) {
         set_status(c, NMF_ERR_DEVICE_TIMEOUT);
@@ -167,11 +171,19 @@ __device__ __forceinline__ void form_h(const float* Rw, int p, int nu, float* Ws
     Ws[c * kWs + k] = c < p ? Rw[c * nu + k] : 0.f;
   }
   __syncthreads();
-  for (int i = tid; i < PM * PM; i += NT) {
-    const int c = i / PM, d = i % PM;
+  // the upper triangle, mirrored (fmaf(a, b, s) = fmaf(b, a, s): H_dc equals H_cd bit for bit)
+  constexpr int E = PM * (PM + 1) / 2;
+  for (int e = tid; e < E; e += NT) {
+    int c = 0, r = e;
+    while (r >= PM - c) {
+      r -= PM - c;
+      ++c;
+    }
+    const int d = c + r;
     float s = 0.f;
     for (int k = 0; k < nu; ++k) s = fmaf(Ws[c * kWs + k], Ws[d * kWs + k], s);
-    Hs[i] = s;
+    Hs[c * PM + d] = s;
+    Hs[d * PM + c] = s;
   }
   __syncthreads();
 }
@@ -190,27 +202,61 @@ __device__ __forceinline__ void form_b(const float* Ws, const float* Ds, int nu,
 
 // This CTA's share of the other side's W: part[o] = sum_t Y[c][t] E[k][t],
 // o = c nu + k (the epilogue of solve_kernel, same order).
+// Each thread forms the outputs (c, k) and (c + 1, k): the two share the read
+// of row k of Es (the reads that bound this step), and every output keeps
+// the arithmetic of the one-output form (four chains over t, then
+// (s0 + s1) + (s2 + s3)). From PM = 24 on, where the kernel has no
+// registers to spare, one output per thread.
+template <int PM>
 __device__ __forceinline__ void form_share(const float* Ys, const float* Es, int p, int nu, int P4, float* part) {
   const int P = p * nu;
-  for (int o = threadIdx.x; o < P4; o += blockDim.x) {
-    float s = 0.f;
-    if (o < P) {
-      const int c = o / nu, k = o % nu;
-      const float4* fa = reinterpret_cast<const float4*>(Ys + c * kFs);
-      const float4* ob = reinterpret_cast<const float4*>(Es + k * kFs);
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  if constexpr (PM >= 24) {
+    for (int o = threadIdx.x; o < P4; o += blockDim.x) {
+      float s = 0.f;
+      if (o < P) {
+        const int c = o / nu, k = o % nu;
+        const float4* fa = reinterpret_cast<const float4*>(Ys + c * kFs);
+        const float4* ob = reinterpret_cast<const float4*>(Es + k * kFs);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll 8
-      for (int t4 = 0; t4 < T / 4; ++t4) {
-        const float4 x = fa[t4], z = ob[t4];
-        s0 = fmaf(x.x, z.x, s0);
-        s1 = fmaf(x.y, z.y, s1);
-        s2 = fmaf(x.z, z.z, s2);
-        s3 = fmaf(x.w, z.w, s3);
+        for (int t4 = 0; t4 < T / 4; ++t4) {
+          const float4 x = fa[t4], z = ob[t4];
+          s0 = fmaf(x.x, z.x, s0);
+          s1 = fmaf(x.y, z.y, s1);
+          s2 = fmaf(x.z, z.z, s2);
+          s3 = fmaf(x.w, z.w, s3);
+        }
+        s = (s0 + s1) + (s2 + s3);
       }
-      s = (s0 + s1) + (s2 + s3);
+      part[o] = s;
     }
-    part[o] = s;
+    return;
   }
+  const int pairs = (p + 1) / 2;
+  for (int task = threadIdx.x; task < pairs * nu; task += blockDim.x) {
+    const int c = 2 * (task / nu), k = task % nu;
+    const bool two = c + 1 < p;
+    const float4* fa = reinterpret_cast<const float4*>(Ys + c * kFs);
+    const float4* fb = reinterpret_cast<const float4*>(Ys + (two ? c + 1 : c) * kFs);
+    const float4* ob = reinterpret_cast<const float4*>(Es + k * kFs);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+#pragma unroll 4
+    for (int t4 = 0; t4 < T / 4; ++t4) {
+      const float4 z = ob[t4], x = fa[t4], y = fb[t4];
+      a0 = fmaf(x.x, z.x, a0);
+      a1 = fmaf(x.y, z.y, a1);
+      a2 = fmaf(x.z, z.z, a2);
+      a3 = fmaf(x.w, z.w, a3);
+      b0 = fmaf(y.x, z.x, b0);
+      b1 = fmaf(y.y, z.y, b1);
+      b2 = fmaf(y.z, z.z, b2);
+      b3 = fmaf(y.w, z.w, b3);
+    }
+    part[c * nu + k] = (a0 + a1) + (a2 + a3);
+    if (two) part[(c + 1) * nu + k] = (b0 + b1) + (b2 + b3);
+  }
+  // the padding of the share
+  for (int o = P + threadIdx.x; o < P4; o += blockDim.x) part[o] = 0.f;
 }
 
 template <int PM, bool TEST, bool RESTART>
@@ -264,8 +310,8 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
 
   unsigned int rounds = 0;  // barrier arrivals so far (the same count in every CTA)
   // ---- shares of both W's at (G0, F0) ----
-  if (cta < a.ctasF) form_share(YF, EF, p, nu, P4, a.partF + (size_t)cta * P4);
-  if (TEST && cta < a.ctasG) form_share(YG, EG, p, nu, P4, a.partG + (size_t)cta * P4);
+  if (cta < a.ctasF) form_share<PM>(YF, EF, p, nu, P4, a.partF + (size_t)cta * P4);
+  if (TEST && cta < a.ctasG) form_share<PM>(YG, EG, p, nu, P4, a.partG + (size_t)cta * P4);
   grid_arrive(a.bar);
   ++rounds;
 
@@ -472,7 +518,7 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
         }
       }
       __syncthreads();  // Ys complete
-      if (mine) form_share(Y, s == 0 ? EG : EF, p, nu, P4, (s == 0 ? a.partG : a.partF) + (size_t)cta * P4);
+      if (mine) form_share<PM>(Y, s == 0 ? EG : EF, p, nu, P4, (s == 0 ? a.partG : a.partF) + (size_t)cta * P4);
       if (s == 1 && a.times) {
         __syncthreads();
         if (tid == 0) {
