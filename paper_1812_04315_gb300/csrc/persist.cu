@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
   __shared__ float2 red[kThreadsAll / 32];
   __shared__ int ok_s;
   __shared__ StopShared stop_s;
+  __shared__ float pterm[TEST ? kBlockP * T : 1];  // the current block's stop-test terms, per thread
   __shared__ double lam_s, eps2_s;
   __shared__ __align__(16) float lam_dg[2 * PM];
   extern __shared__ __align__(16) float dyn[];
@@ -460,8 +461,9 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
           }
           iters = k + 1;
           if (TEST && k + 1 >= a.min_inner) {
-            stop_record<PM>(stop_s, nrec, active ? pg_sq<PM>(f, gf) : 0.f, f, keep, eps2_f);
+            stop_record_term<PM>(pterm, nrec, active ? pg_sq<PM>(f, gf) : 0.f, f, keep, eps2_f);
             if (++nrec == kBlockP || k + 1 == a.max_inner) {
+              stop_sum_terms(stop_s, nrec, pterm);
               const int r = stop_decide(stop_s, nrec, base, a.slots, epoch, eps2, eps2_f, ctas_s, a.withhold != 0,
                                         ctrl, a.wait_ns);
               if (r == -2) {

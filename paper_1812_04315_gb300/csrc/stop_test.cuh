@@ -91,6 +91,40 @@ __device__ __forceinline__ void stop_record(StopShared& S, int i, float term, co
   if ((threadIdx.x & 31) == 0) S.part[i][threadIdx.x >> 5] = fails ? __int_as_float(0x7f800000) : ws;
 }
 
+// stop_record with the warp sum left for later: the vote and the kept
+// iterate as stop_record takes them, and this thread's term (+inf when its
+// warp fails the test, so that the later warp sum is +inf as stop_record
+// records it) in pterm[i][T].
+template <int PM>
+__device__ __forceinline__ void stop_record_term(float* pterm, int i, float term, const float* f, float* keep,
+                                                 float eps2_f) {
+  const bool fails = __any_sync(0xffffffffu, term > eps2_f);
+  if (!fails) {
+    float* slot = keep + (size_t)i * PM * T;
+#pragma unroll
+    for (int k = 0; k < PM; ++k) slot[k * T + threadIdx.x] = f[k];
+  }
+  pterm[i * T + threadIdx.x] = fails ? __int_as_float(0x7f800000) : term;
+}
+
+// The warp sums of the block's nb tests recorded by stop_record_term, into
+// S.part (the values stop_record writes): all kMaxStopBlock sums advance
+// together through warp_sum's butterfly (the same steps per value, so the
+// same sums), their shuffles interleaved.
+__device__ __forceinline__ void stop_sum_terms(StopShared& S, int nb, const float* pterm) {
+  float v[kMaxStopBlock];
+#pragma unroll
+  for (int i = 0; i < kMaxStopBlock; ++i) v[i] = i < nb ? pterm[i * T + threadIdx.x] : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < kMaxStopBlock; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < kMaxStopBlock; ++i)
+      if (i < nb) S.part[i][threadIdx.x >> 5] = v[i];
+}
+
 // Decides the nb tests base .. base+nb-1 just recorded (every thread calls
 // it; two block barriers). `ctas` CTAs (0 .. ctas-1) take part; slots holds
 // one row of ctas words per test. Returns the block index of the first test
