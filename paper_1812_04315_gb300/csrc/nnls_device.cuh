@@ -237,8 +237,14 @@ __device__ double lambda_max_cta(const float* Hs, float* Ms, float* dg, double* 
   constexpr int LS = lam_stride<PM>();
   constexpr int E = PM * (PM + 1) / 2;
   const int tid = threadIdx.x, NT = blockDim.x;
+  // the trace: every diagonal load issued first, then the sum in index order
+  float dgl[PM];
+#pragma unroll
+  for (int c = 0; c < PM; ++c) dgl[c] = c < p ? Hs[c * PM + c] : 0.f;
   float tr = 0.f;
-  for (int c = 0; c < p; ++c) tr += Hs[c * PM + c];
+#pragma unroll
+  for (int c = 0; c < PM; ++c)
+    if (c < p) tr += dgl[c];
   if (!(tr > 0.f) || !isfinite(tr)) {
     // every thread sees the same trace: a uniform exit
     const double r = isfinite(tr) ? 0.0 : (double)tr;
@@ -323,10 +329,20 @@ __device__ double lambda_max_cta(const float* Hs, float* Ms, float* dg, double* 
     }
     const float* vrow = A + jb * LS;
     const float vc = lane < p ? vrow[lane] : 0.f;
+    // (H v)_lane in four independent float-float sums, combined in a fixed order
     DF hv{0.f, 0.f};
     if (lane < p) {
+      DF h1{0.f, 0.f}, h2{0.f, 0.f}, h3{0.f, 0.f};
 #pragma unroll
-      for (int d = 0; d < PM; ++d) df_add_product(hv, Hs[lane * PM + d], vrow[d]);
+      for (int d = 0; d < PM; d += 4) {
+        df_add_product(hv, Hs[lane * PM + d], vrow[d]);
+        df_add_product(h1, Hs[lane * PM + d + 1], vrow[d + 1]);
+        df_add_product(h2, Hs[lane * PM + d + 2], vrow[d + 2]);
+        df_add_product(h3, Hs[lane * PM + d + 3], vrow[d + 3]);
+      }
+      df_add(hv, h1.hi, h1.lo);
+      df_add(h2, h3.hi, h3.lo);
+      df_add(hv, h2.hi, h2.lo);
     }
     DF num{0.f, 0.f}, den{0.f, 0.f};
     df_add_product(num, vc, hv.hi);
