@@ -318,8 +318,11 @@ __device__ double lambda_max_cta(const float* Hs, float* Ms, float* dg, double* 
     const int lane = tid;
     float best = lane < p ? A[lane * LS + lane] : -1.f;
     int jb = lane;
+    // lanes from PM on hold nothing (-1 here, zeros below): the butterflies
+    // start at the smallest power of two covering PM lanes (the same results)
+    constexpr int o0 = PM > 16 ? 16 : PM > 8 ? 8 : PM > 4 ? 4 : 2;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = o0; o > 0; o >>= 1) {
       const float ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
       if (ob > best || (ob == best && oj < jb)) {
@@ -349,7 +352,7 @@ __device__ double lambda_max_cta(const float* Hs, float* Ms, float* dg, double* 
     num.lo = fmaf(vc, hv.lo, num.lo);
     df_add_product(den, vc, vc);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = o0; o > 0; o >>= 1) {
       const float nh = __shfl_xor_sync(0xffffffffu, num.hi, o), nl = __shfl_xor_sync(0xffffffffu, num.lo, o);
       const float dh = __shfl_xor_sync(0xffffffffu, den.hi, o), dl = __shfl_xor_sync(0xffffffffu, den.lo, o);
       DF a = (lane & o) ? DF{nh, nl} : num, b = (lane & o) ? num : DF{nh, nl};

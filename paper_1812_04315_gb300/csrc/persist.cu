@@ -310,6 +310,7 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
   __syncthreads();
 
   unsigned int rounds = 0;  // barrier arrivals so far (the same count in every CTA)
+  long long total_inner_G = 0, total_inner_F = 0;  // CTA 0, thread 0: the statistics' running totals
   // ---- shares of both W's at (G0, F0) ----
   if (cta < a.ctasF) form_share<PM>(YF, EF, p, nu, P4, a.partF + (size_t)cta * P4);
   if (TEST && cta < a.ctasG) form_share<PM>(YG, EG, p, nu, P4, a.partG + (size_t)cta * P4);
@@ -514,8 +515,18 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
         ctrl->iters[s] = iters;
         ctrl->lipschitz[s] = Lc;
         if (a.stats) {
+          // running totals in registers: a store, not a read-modify-write whose
+          // load every thread would wait for at the barrier below
+          long long tot;
+          if (s == 0) {
+            total_inner_G += iters;
+            tot = total_inner_G;
+          } else {
+            total_inner_F += iters;
+            tot = total_inner_F;
+          }
           a.stats->last_inner[s] = iters;
-          a.stats->total_inner[s] += iters;
+          a.stats->total_inner[s] = tot;
           a.stats->lipschitz[s] = Lc_d;
         }
       }
