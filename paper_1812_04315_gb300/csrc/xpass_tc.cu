@@ -410,26 +410,35 @@ __global__ void __launch_bounds__(kThreads, 1)
 // (3 NV rows x 128 columns, the tile's columns) per tile, the B slice per row
 // of tiles, each double buffered. Part j of a tile feeds the MMAs with
 // operand parts 0 .. 2 - j.
-constexpr int kMaxStages3 = 4;
-__host__ __device__ constexpr int op3_box_bytes(int NV) { return 3 * NV * kBoxK * 2; }  // 3 NV rows x 128 bytes
-__host__ __device__ constexpr int op3_tile_bytes(int NV) { return 2 * op3_box_bytes(NV); }
+//
+// (The one-part bfloat16 pass stays on xpass_tc_kernel, operands with every
+// stage: on this ring, with five X stages and a separate operand producer, it
+// measured 187 against 182 us per dual product at n = m = 10^4, nu = 20.)
+constexpr int kMaxStagesRing = 6;
+__host__ __device__ constexpr int op_box_bytes(int NV, int parts) { return parts * NV * kBoxK * 2; }  // rows x 128 B
+__host__ __device__ constexpr int op_tile_bytes(int NV, int parts) { return 2 * op_box_bytes(NV, parts); }
 
-template <int NV>
-__global__ void __launch_bounds__(kThreads, 1)
-    xpass_tc3_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcParams P) {
+// Warps of the ring kernel: 0 = X producer, 1 = MMA issuer (and TMEM owner),
+// 2..5 = epilogue, 6 = operand producer.
+constexpr int kRingWarps = 7;
+
+template <int NV, int PARTS>
+__global__ void __launch_bounds__(kRingWarps * 32, 1)
+    xpass_ring_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcParams P) {
   // launched as a programmatic dependent: the operands come from the previous kernel
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (call_failed(P.ctrl)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  constexpr int box = op3_box_bytes(NV);
-  constexpr int opTile = op3_tile_bytes(NV);
+  constexpr int box = op_box_bytes(NV, PARTS);
+  constexpr int opTile = op_tile_bytes(NV, PARTS);
+  constexpr int ACC = PARTS == 3 ? 3 : 1;  // accumulators per output (see load_acc)
   const int kStages = P.stages;
   uint8_t* xring = smem;
   uint8_t* aring = xring + (size_t)kStages * kXStageBytes;
   uint8_t* bring = aring + 2 * opTile;
   float* stage_area = reinterpret_cast<float*>(bring + 2 * opTile);
-  __shared__ uint64_t xfull[kMaxStages3], xempty[kMaxStages3], afull[2], aempty[2], bfull[2], bempty[2];
+  __shared__ uint64_t xfull[kMaxStagesRing], xempty[kMaxStagesRing], afull[2], aempty[2], bfull[2], bempty[2];
   __shared__ uint64_t tfull[2], tempty[2], tdone;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
@@ -469,10 +478,35 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = &abort_s;
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- X producer: the tiles' parts through the X ring ----------------
     if (lane == 0) {
-      int it = 0, at = 0, bt = 0;
-      for (int rt = rt0; rt < rt1 && !*abort_flag; ++rt) {
+      int it = 0;
+      bool ok = true;
+      for (int rt = rt0; rt < rt1 && ok && !*abort_flag; ++rt)
+        for (int ct = ct0; ct < ct1 && ok; ++ct)
+          for (int j = 0; j < PARTS; ++j, ++it) {
+            const int st = it % kStages;
+            if (!mbar_wait(&xempty[st], ((uint32_t)(it / kStages) & 1u) ^ 1u, abort_flag, P.wait_ns)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&xfull[st], (uint32_t)kXStageBytes);
+            if (P.withhold && blockIdx.x == 0 && it == 0) continue;  // failure-path testing: the stage never fills
+            bulk_load(xring + (size_t)st * kXStageBytes,
+                      P.Xt + (((size_t)rt * P.tiles_c + ct) * PARTS + j) * kXStageBytes, (uint32_t)kXStageBytes,
+                      &xfull[st]);
+          }
+      if (*abort_flag)  // let the copies already issued land before the CTA exits
+        for (int k = it - kStages < 0 ? 0 : it - kStages; k < it; ++k)
+          mbar_drain(&xfull[k % kStages], (uint32_t)(k / kStages) & 1u, P.wait_ns);
+    }
+  } else if (warp == kRingWarps - 1) {
+    // ---------------- operand producer: B per row of tiles, A per tile ----------------
+    // (its own thread, so the X ring runs ahead of the operand rings)
+    if (lane == 0) {
+      int at = 0, bt = 0;
+      bool ok = true;
+      for (int rt = rt0; rt < rt1 && ok && !*abort_flag; ++rt) {
         if (P.doT) {
           const int b = bt & 1;
           if (!mbar_wait(&bempty[b], ((uint32_t)(bt >> 1) & 1u) ^ 1u, abort_flag, P.wait_ns)) break;
@@ -481,34 +515,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           tma_load_2d(bring + (size_t)b * opTile + box, &mapB, &bfull[b], rt * kTM + kBoxK, 0);
           ++bt;
         }
-        bool ok = true;
-        for (int ct = ct0; ct < ct1 && ok; ++ct) {
-          if (P.doN) {
-            const int a = at & 1;
-            if (!mbar_wait(&aempty[a], ((uint32_t)(at >> 1) & 1u) ^ 1u, abort_flag, P.wait_ns)) { ok = false; break; }
-            mbar_arrive_expect_tx(&afull[a], (uint32_t)opTile);
-            tma_load_2d(aring + (size_t)a * opTile, &mapA, &afull[a], ct * kTK, 0);
-            tma_load_2d(aring + (size_t)a * opTile + box, &mapA, &afull[a], ct * kTK + kBoxK, 0);
-            ++at;
+        for (int ct = ct0; ct < ct1 && P.doN; ++ct) {
+          const int a = at & 1;
+          if (!mbar_wait(&aempty[a], ((uint32_t)(at >> 1) & 1u) ^ 1u, abort_flag, P.wait_ns)) {
+            ok = false;
+            break;
           }
-          for (int j = 0; j < 3; ++j, ++it) {
-            const int st = it % kStages;
-            if (!mbar_wait(&xempty[st], ((uint32_t)(it / kStages) & 1u) ^ 1u, abort_flag, P.wait_ns)) {
-              ok = false;
-              break;
-            }
-            mbar_arrive_expect_tx(&xfull[st], (uint32_t)kXStageBytes);
-            if (P.withhold && blockIdx.x == 0 && it == 0) continue;  // failure-path testing: the stage never fills
-            bulk_load(xring + (size_t)st * kXStageBytes, P.Xt + (((size_t)rt * P.tiles_c + ct) * 3 + j) * kXStageBytes,
-                      (uint32_t)kXStageBytes, &xfull[st]);
-          }
+          mbar_arrive_expect_tx(&afull[a], (uint32_t)opTile);
+          tma_load_2d(aring + (size_t)a * opTile, &mapA, &afull[a], ct * kTK, 0);
+          tma_load_2d(aring + (size_t)a * opTile + box, &mapA, &afull[a], ct * kTK + kBoxK, 0);
+          ++at;
         }
-        if (!ok) break;
       }
       if (*abort_flag) {
-        // let the copies already issued land before the CTA exits
-        for (int k = it - kStages < 0 ? 0 : it - kStages; k < it; ++k)
-          mbar_drain(&xfull[k % kStages], (uint32_t)(k / kStages) & 1u, P.wait_ns);
         for (int k = at - 2 < 0 ? 0 : at - 2; k < at; ++k) mbar_drain(&afull[k & 1], (uint32_t)(k >> 1) & 1u, P.wait_ns);
         for (int k = bt - 2 < 0 ? 0 : bt - 2; k < bt; ++k) mbar_drain(&bfull[k & 1], (uint32_t)(k >> 1) & 1u, P.wait_ns);
       }
@@ -522,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int ri = 0; ri < nrt && ok; ++ri) {
         const int buf = ri & 1;
-        const uint32_t dN = tmem + (uint32_t)(buf * 3 * NV);  // L, then S_a, S_b
+        const uint32_t dN = tmem + (uint32_t)(buf * ACC * NV);  // PARTS = 3: L, then S_a, S_b
         int b = 0;
         if (P.doN) {
           if (!mbar_wait(&tempty[buf], ((uint32_t)(ri >> 1) & 1u) ^ 1u, abort_flag, P.wait_ns)) { ok = false; break; }
@@ -542,7 +561,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
           }
           const uint32_t opa = smem_u32(aring + (size_t)a * opTile);
-          for (int j = 0; j < 3; ++j, ++it) {
+          for (int j = 0; j < PARTS; ++j, ++it) {
             const int st = it % kStages;
             if (!mbar_wait(&xfull[st], (uint32_t)(it / kStages) & 1u, abort_flag, P.wait_ns)) { ok = false; break; }
             tc_fence_after();
@@ -550,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // Per K step: part 0 issues L and [S_a | S_b] MMAs, parts 1 and 2
             // one [S_a | S_b] or S_a MMA; N and T alternate so that
             // consecutive MMAs go to different accumulators.
-            const uint32_t dT = tmem + (uint32_t)((6 + 3 * ci) * NV);
+            const uint32_t dT = tmem + (uint32_t)((2 + ci) * ACC * NV);
             const bool firstN = ci == 0 && j == 0, firstT = ri == 0 && j == 0;
             // operand rows of the small-term MMA: A_1 (j = 0) or A_0 (j = 1, 2)
             const uint32_t srow = (uint32_t)(j == 0 ? NV * 128 : 0);
@@ -569,12 +588,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                   tc_mma(dT, smem_desc(xa + xoffT, kXStageBytes / 2, 1024), smem_desc(opb + boff, 16, 1024), idT1,
                          firstT ? acc : 1u);
               }
-              if (P.doN)
-                tc_mma(dN + NV, smem_desc(xa + xoffN, 16, 1024), smem_desc(opa + boff + srow, 16, 1024), idNs,
-                       firstN ? acc : 1u);
-              if (P.doT)
-                tc_mma(dT + NV, smem_desc(xa + xoffT, kXStageBytes / 2, 1024), smem_desc(opb + boff + srow, 16, 1024),
-                       idTs, firstT ? acc : 1u);
+              if constexpr (PARTS == 3) {
+                if (P.doN)
+                  tc_mma(dN + NV, smem_desc(xa + xoffN, 16, 1024), smem_desc(opa + boff + srow, 16, 1024), idNs,
+                         firstN ? acc : 1u);
+                if (P.doT)
+                  tc_mma(dT + NV, smem_desc(xa + xoffT, kXStageBytes / 2, 1024),
+                         smem_desc(opb + boff + srow, 16, 1024), idTs, firstT ? acc : 1u);
+              }
             }
             tc_commit(&xempty[st]);
           }
@@ -592,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_commit(&tdone);
     }
   } else {
-    epilogue<NV, 3>(P, tmem, stage_area, tfull, tempty, &tdone, abort_flag, rt0, ct0, nrt, nct, rg, cg);
+    epilogue<NV, ACC>(P, tmem, stage_area, tfull, tempty, &tdone, abort_flag, rt0, ct0, nrt, nct, rg, cg);
   }
   teardown(P, tmem, &tdone, abort_flag);
 }
@@ -698,11 +719,11 @@ __global__ void to_tiles_kernel(const float* __restrict__ X, int n, int m, int t
 // Launch with programmatic dependent launch allowed: the kernel's CTAs may
 // start while the previous kernel on the stream finishes, and wait
 // (griddepcontrol.wait) before reading anything it wrote.
-cudaError_t launch_pdl(const void* fn, int ctas, size_t smem, cudaStream_t s, const CUtensorMap& mA,
+cudaError_t launch_pdl(const void* fn, int ctas, int threads, size_t smem, cudaStream_t s, const CUtensorMap& mA,
                        const CUtensorMap& mB, const TcParams& P) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(ctas);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -720,27 +741,27 @@ cudaError_t launch_nv(const CUtensorMap& mA, const CUtensorMap& mB, const TcPara
   cudaError_t e = allow_dynamic_smem((const void*)xpass_tc_kernel<NV>, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  return launch_pdl((const void*)xpass_tc_kernel<NV>, ctas, smem, s, mA, mB, P);
+  return launch_pdl((const void*)xpass_tc_kernel<NV>, ctas, kThreads, smem, s, mA, mB, P);
 }
 
-// Three-part kernel: X ring stages that fit beside the two operand rings
-// (double buffered) and the epilogue staging.
-int tc3_stages(int NV) {
-  const long room = (long)kSmemBudget - 1024 - kStageArea - 4l * op3_tile_bytes(NV);
+// Ring kernel: X ring stages that fit beside the two operand rings (double
+// buffered) and the epilogue staging.
+int ring_stages(int NV, int parts) {
+  const long room = (long)kSmemBudget - 1024 - kStageArea - 4l * op_tile_bytes(NV, parts);
   const long st = room / kXStageBytes;
-  return (int)(st > kMaxStages3 ? kMaxStages3 : st);
+  return (int)(st > kMaxStagesRing ? kMaxStagesRing : st);
 }
-size_t tc3_smem_bytes(int NV) {
-  return (size_t)tc3_stages(NV) * kXStageBytes + 4 * (size_t)op3_tile_bytes(NV) + kStageArea + 1024;
+size_t ring_smem_bytes(int NV, int parts) {
+  return (size_t)ring_stages(NV, parts) * kXStageBytes + 4 * (size_t)op_tile_bytes(NV, parts) + kStageArea + 1024;
 }
 
-template <int NV>
-cudaError_t launch3_nv(const CUtensorMap& mA, const CUtensorMap& mB, const TcParams& P, int ctas, cudaStream_t s) {
-  const size_t smem = tc3_smem_bytes(NV);
-  cudaError_t e = allow_dynamic_smem((const void*)xpass_tc3_kernel<NV>, (int)smem);
+template <int NV, int PARTS>
+cudaError_t launch_ring(const CUtensorMap& mA, const CUtensorMap& mB, const TcParams& P, int ctas, cudaStream_t s) {
+  const size_t smem = ring_smem_bytes(NV, PARTS);
+  cudaError_t e = allow_dynamic_smem((const void*)xpass_ring_kernel<NV, PARTS>, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  return launch_pdl((const void*)xpass_tc3_kernel<NV>, ctas, smem, s, mA, mB, P);
+  return launch_pdl((const void*)xpass_ring_kernel<NV, PARTS>, ctas, kRingWarps * 32, smem, s, mA, mB, P);
 }
 
 }  // namespace
@@ -815,7 +836,7 @@ cudaError_t xpass_tc_launch(const XPassPlan& pl, const XPassArgs& a, cudaStream_
   P.Xt = static_cast<const uint8_t*>(a.X);
   P.n = a.n;
   P.m = a.m;
-  P.stages = pl.parts == 3 ? tc3_stages(pl.NV) : tc_stages(pl.NV);
+  P.stages = pl.parts == 3 ? ring_stages(pl.NV, pl.parts) : tc_stages(pl.NV);
   P.tiles_r = pl.tiles_r;
   P.tiles_c = pl.tiles_c;
   P.S_r = pl.S_r;
@@ -830,11 +851,12 @@ cudaError_t xpass_tc_launch(const XPassPlan& pl, const XPassArgs& a, cudaStream_
   P.withhold = injected_fault() == NMF_FAULT_XPASS_COPY ? 1 : 0;
   if (pl.parts == 3) {
     switch (pl.NV) {
-      case 16: return launch3_nv<16>(mA, mB, P, pl.ctas, s);
-      case 32: return launch3_nv<32>(mA, mB, P, pl.ctas, s);
+      case 16: return launch_ring<16, 3>(mA, mB, P, pl.ctas, s);
+      case 32: return launch_ring<32, 3>(mA, mB, P, pl.ctas, s);
       default: return cudaErrorInvalidValue;
     }
   }
+
   switch (pl.NV) {
     case 16: return launch_nv<16>(mA, mB, P, pl.ctas, s);
     case 32: return launch_nv<32>(mA, mB, P, pl.ctas, s);
