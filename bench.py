@@ -738,12 +738,13 @@ def time_to_rre(c, tau=None, tau_rule=None):
 
 
 # Plain NeNMF with the stop test spans one co-resident grid of solve CTAs
-# (at most 320 CTAs of 128 columns); beyond that nenmf_solve returns
+# (at most 320 CTAs of 128 columns, fewer where a CTA's registers or shared
+# memory allow fewer per SM); beyond that nenmf_solve returns
 # NMF_ERR_UNSUPPORTED, so the plain-versus-compressed comparison with a
-# tolerance is limited to n, m <= 40960 (compressed NeNMF has no such limit:
+# tolerance is limited to such sizes (compressed NeNMF has no such limit:
 # larger problems run on the batched kernel).
-PLAIN_STOP_TEST_LIMIT = ("plain NeNMF with tol > 0 runs for n, m <= 40960 (one co-resident grid of 320 x 128 "
-                         "columns); compressed NeNMF has no such limit")
+PLAIN_STOP_TEST_LIMIT = ("plain NeNMF with tol > 0 runs while n and m fit one co-resident grid of solve CTAs "
+                         "(at most 320 x 128 = 40960 columns, fewer for large p); compressed NeNMF has no such limit")
 
 
 PAPER = dict(sizes=(500, 5000, 10000), draws=3, p=15, nu=25, q=4, snr_db=30.0, max_outer=60, max_inner=500,
