@@ -434,7 +434,8 @@ def run_batched(args):
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
               "data": "synthetic (seeded low-rank nonnegative + 20 dB noise drawn on the device; random init)",
               "config": {"workload": BATCH_NAME.replace("256", str(len(probs))), "problems": len(probs),
-                         "cluster": cluster, "clusters": clusters, "cluster_planner": planned,
+                         "cluster": cluster[0], "threads_per_cta": cluster[1], "clusters": clusters,
+                         "cluster_planner": list(planned),
                          "autotune_ms_2outer": {str(k): round(v, 4) for k, v in tune_ms.items()},
                          "l2": "inputs larger than L2 (X totals ~10 GB float32)"},
               "breakdown_ms": {"compress_batched_eager": round(ms_compress, 4), "solve_batched_eager": round(ms_solve, 4),

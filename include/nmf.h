@@ -321,6 +321,8 @@ nmf_status_t nenmf_backward_f64(nmf_stream_t stream, const nenmf_problem_f64_t* 
  */
 typedef struct nenmf_batch_config {
   int cluster; /* CTAs per problem: 0 = chosen by the planner, else 1, 2, 4 or 8 */
+  int threads; /* threads per CTA: 0 = 256, else 128 or 256 (128: two CTAs per SM,
+                  so twice the clusters in flight, each with half the lanes) */
 } nenmf_batch_config_t;
 
 /* Workspace bytes for nenmf_solve_batched with these arguments (0 on invalid
@@ -328,8 +330,9 @@ typedef struct nenmf_batch_config {
 size_t nenmf_solve_batched_workspace_size(int count, const nenmf_problem_t* problems,
                                           const nenmf_params_t* params, const nenmf_batch_config_t* config);
 
-/* The plan nenmf_solve_batched would use: chosen->cluster and the number of
- * clusters launched. Host-only; needs the device current for occupancy. */
+/* The plan nenmf_solve_batched would use: chosen->cluster, chosen->threads and
+ * the number of clusters launched. Host-only; needs the device current for
+ * occupancy. */
 nmf_status_t nenmf_batch_plan_info(int count, const nenmf_problem_t* problems, const nenmf_params_t* params,
                                    const nenmf_batch_config_t* config, nenmf_batch_config_t* chosen,
                                    int* clusters);
@@ -352,13 +355,15 @@ nmf_status_t nenmf_solve_batched(nmf_stream_t stream, int count, const nenmf_pro
                                  size_t workspace_bytes);
 
 /*
- * Measured choice of the cluster size (CTAs per problem) for
- * nenmf_solve_batched: each candidate 1, 2, 4, 8 with a valid plan runs
- * trial_outer outer iterations of these problems (params otherwise as
- * given; record_* ignored) from scratch copies of G and F, once untimed and
- * once timed with CUDA events; best->cluster receives the fastest.
- * trial_ms (host, 4 floats, may be NULL) receives each candidate's time in
- * ms (-1: not a valid plan). The caller's G and F are not modified.
+ * Measured choice of the cluster size (CTAs per problem) and of the threads
+ * per CTA for nenmf_solve_batched: each candidate (cluster 1, 2, 4, 8) x
+ * (threads 256, 128) with a valid plan runs trial_outer outer iterations of
+ * these problems (params otherwise as given; record_* ignored) from scratch
+ * copies of G and F, once untimed and once timed with CUDA events;
+ * best->cluster and best->threads receive the fastest. trial_ms (host, 8
+ * floats, may be NULL) receives each candidate's time in ms, index
+ * 2 * (cluster index) + (threads == 128), -1 where a candidate has no valid
+ * plan. The caller's G and F are not modified.
  * Synchronous: returns after the trials ran (it reads their times).
  * Errors: as nenmf_solve_batched; NMF_ERR_INVALID_ARG if trial_outer < 1,
  * count < 1 or best is NULL; the first device error of a trial.

@@ -59,7 +59,7 @@ class CompressItem(ctypes.Structure):
 
 
 class BatchConfig(ctypes.Structure):
-    _fields_ = [("cluster", ctypes.c_int)]
+    _fields_ = [("cluster", ctypes.c_int), ("threads", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -376,19 +376,20 @@ def _batch_args(problems, max_outer, max_inner, min_inner, tol, tol_mode, cluste
     pa.max_outer, pa.max_inner, pa.min_inner, pa.tol_mode, pa.tol = max_outer, max_inner, min_inner, tol_mode, tol
     pa.restart = int(bool(restart))
     cfg = BatchConfig()
-    cfg.cluster = cluster
+    # a configuration is a cluster size or a (cluster size, threads per CTA) pair; 0: the planner's choice
+    cfg.cluster, cfg.threads = (cluster, 0) if isinstance(cluster, int) else (int(cluster[0]), int(cluster[1]))
     return arr, pa, cfg
 
 
 def batch_plan(problems, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
                tol_mode: int = TOL_REL, cluster: int = 0):
-    """(CTAs per problem, clusters launched) that nenmf_solve_batched would use."""
+    """((CTAs per problem, threads per CTA), clusters launched) that nenmf_solve_batched would use."""
     arr, pa, cfg = _batch_args(problems, max_outer, max_inner, min_inner, tol, tol_mode, cluster)
     out = BatchConfig()
     ncl = ctypes.c_int(0)
     _ok(lib().nenmf_batch_plan_info(len(problems), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(pa),
                                     ctypes.byref(cfg), ctypes.byref(out), ctypes.byref(ncl)), "nenmf_batch_plan_info")
-    return out.cluster, ncl.value
+    return (out.cluster, out.threads), ncl.value
 
 
 def batch_workspace_size(problems, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
@@ -452,8 +453,8 @@ def backward(problem: Problem, G0, F0, record: SolveRecord, dG_T, dF_T, max_oute
 
 def batch_autotune(problems, Gs, Fs, max_outer: int, max_inner: int, min_inner: int = 1, tol: float = 0.0,
                    tol_mode: int = TOL_REL, restart: bool = False, trial_outer: int = 2, ws=None):
-    """nenmf_batch_autotune: (fastest cluster size, {cluster: trial ms}) for these problems;
-    Gs, Fs are left unchanged. Synchronous."""
+    """nenmf_batch_autotune: (fastest (cluster size, threads per CTA), {(cluster, threads): trial ms})
+    for these problems; Gs, Fs are left unchanged. Synchronous."""
     count = len(problems)
     for pr, G, F in zip(problems, Gs, Fs):
         _check_f32("G", G, (pr.n, pr.p))
@@ -465,11 +466,12 @@ def batch_autotune(problems, Gs, Fs, max_outer: int, max_inner: int, min_inner: 
         ws = workspace(lib().nenmf_batch_autotune_workspace_size(count, ctypes.cast(arr, ctypes.c_void_p),
                                                                  ctypes.byref(pa), trial_outer))
     best = BatchConfig()
-    ms = (ctypes.c_float * 4)()
+    ms = (ctypes.c_float * 8)()
     _ok(lib().nenmf_batch_autotune(_stream(), count, ctypes.cast(arr, ctypes.c_void_p), ctypes.cast(gp, ctypes.c_void_p),
                                    ctypes.cast(fp, ctypes.c_void_p), ctypes.byref(pa), trial_outer, ctypes.byref(best),
                                    ms, _ptr(ws), ws.numel()), "nenmf_batch_autotune")
-    return best.cluster, {c: float(ms[k]) for k, c in enumerate((1, 2, 4, 8)) if ms[k] >= 0.0}
+    cands = [(c, t) for c in (1, 2, 4, 8) for t in (256, 128)]
+    return (best.cluster, best.threads), {ct: float(ms[k]) for k, ct in enumerate(cands) if ms[k] >= 0.0}
 
 
 def read_batch_stats(stats, count: int):

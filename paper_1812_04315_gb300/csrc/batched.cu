@@ -682,7 +682,8 @@ nmf_status_t make_plan(int count, const nenmf_problem_t* pr, const nenmf_params_
     pl.max_j = std::max(pl.max_j, std::max(pr[i].n, pr[i].m));
   }
   const int want = cfg ? cfg->cluster : 0;
-  const int tb = kBatchThreads;
+  const int tb = cfg && cfg->threads ? cfg->threads : kBatchThreads;
+  if (tb != 128 && tb != kBatchThreads) return NMF_ERR_INVALID_ARG;
   std::vector<int> sizes;
   if (want > 0) sizes.push_back(want);
   else sizes = {1, 2, 4, 8};
@@ -774,7 +775,10 @@ extern "C" nmf_status_t nenmf_batch_plan_info(int count, const nenmf_problem_t* 
   BatchPlan pl;
   st = make_plan(count, problems, *params, config, pl);
   if (st != NMF_OK) return st;
-  if (chosen) chosen->cluster = pl.cluster;
+  if (chosen) {
+    chosen->cluster = pl.cluster;
+    chosen->threads = pl.threads;
+  }
   if (clusters) *clusters = pl.clusters;
   return NMF_OK;
 }
@@ -873,6 +877,7 @@ extern "C" nmf_status_t nenmf_solve_batched(nmf_stream_t stream, int count, cons
 namespace {
 
 constexpr int kTuneCandidates[4] = {1, 2, 4, 8};
+constexpr int kTuneThreads[2] = {kBatchThreads, 128};
 
 // Scratch copies of every problem's G and F (each 256-byte aligned), then the
 // largest batched-solve workspace over the candidates.
@@ -893,10 +898,11 @@ TuneWs carve_tune(void* base, int count, const nenmf_problem_t* pr, const nenmf_
     w.F[i] = cv.take<float>((size_t)pr[i].p * pr[i].m);
   }
   size_t need = 0;
-  for (int c : kTuneCandidates) {
-    const nenmf_batch_config_t cfg{c};
-    need = std::max(need, nenmf_solve_batched_workspace_size(count, pr, &trial, &cfg));
-  }
+  for (int c : kTuneCandidates)
+    for (int tb : kTuneThreads) {
+      const nenmf_batch_config_t cfg{c, tb};
+      need = std::max(need, nenmf_solve_batched_workspace_size(count, pr, &trial, &cfg));
+    }
   w.solve_ws = cv.take<char>(need);
   w.solve_bytes = need;
   w.bytes = cv.size();
@@ -943,11 +949,11 @@ extern "C" nmf_status_t nenmf_batch_autotune(nmf_stream_t stream, int count, con
     return NMF_ERR_CUDA;
   }
   float best_ms = -1.f;
-  int best_c = 0;
+  int best_c = 0, best_t = 0;
   st = NMF_OK;
-  for (int k = 0; k < 4 && st == NMF_OK; ++k) {
-    const int c = kTuneCandidates[k];
-    const nenmf_batch_config_t cfg{c};
+  for (int k = 0; k < 8 && st == NMF_OK; ++k) {
+    const int c = kTuneCandidates[k / 2], tb = kTuneThreads[k % 2];
+    const nenmf_batch_config_t cfg{c, tb};
     if (trial_ms) trial_ms[k] = -1.f;
     if (nenmf_solve_batched_workspace_size(count, problems, &t, &cfg) == 0) continue;  // not a valid plan
     // one untimed run (first-use costs), then the timed one, each from the caller's factors
@@ -985,6 +991,7 @@ extern "C" nmf_status_t nenmf_batch_autotune(nmf_stream_t stream, int count, con
     if (best_ms < 0.f || ms < best_ms) {
       best_ms = ms;
       best_c = c;
+      best_t = tb;
     }
   }
   cudaEventDestroy(e0);
@@ -992,5 +999,6 @@ extern "C" nmf_status_t nenmf_batch_autotune(nmf_stream_t stream, int count, con
   if (st != NMF_OK) return st;
   if (best_c == 0) return NMF_ERR_UNSUPPORTED;
   best->cluster = best_c;
+  best->threads = best_t;
   return NMF_OK;
 }

@@ -44,6 +44,12 @@ static std::atomic<long long> g_launches{0};
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 constexpr unsigned long long kDefaultWaitNs = 2000000000ull;  // 2 s
+// Programmatic dependent launch of the compression kernels, per host thread.
+static thread_local int t_pdl_off = 0;
+bool pdl_allowed() { return t_pdl_off == 0; }
+PdlOff::PdlOff() { ++t_pdl_off; }
+PdlOff::~PdlOff() { --t_pdl_off; }
+
 static std::atomic<int> g_fault{NMF_FAULT_NONE};
 static std::atomic<unsigned long long> g_wait_ns{kDefaultWaitNs};
 int injected_fault() { return g_fault.load(std::memory_order_relaxed); }
@@ -646,6 +652,10 @@ nmf_status_t nmf_compress_batched(nmf_stream_t stream, int count, const nmf_comp
   // fork: every lane starts after what the caller's stream holds
   NMF_CU(cudaEventRecord(L->fork, s));
   for (int k = 0; k < lanes; ++k) NMF_CU(cudaStreamWaitEvent(L->s[k], L->fork, 0));
+  // Programmatic dependent launch stays off on the lanes: a dependent X pass
+  // whose CTAs start early would hold SMs (and their shared memory) while it
+  // waits, away from the other lanes' kernels.
+  PdlOff pdl_off;
   for (int i = 0; i < count; ++i) {
     const int k = i % lanes;
     const nmf_compress_item_t& it = items[i];
@@ -697,7 +707,7 @@ size_t large_workspace(const nenmf_problem_t& pr) {
   worst.min_inner = 1;
   worst.tol = 1.0;
   worst.tol_mode = NENMF_TOL_REL;
-  const nenmf_batch_config_t cfg{kLargeCluster};
+  const nenmf_batch_config_t cfg{kLargeCluster, 0};
   return nenmf_solve_batched_workspace_size(1, &pr, &worst, &cfg);
 }
 
@@ -730,7 +740,7 @@ nmf_status_t nenmf_solve(nmf_stream_t stream, const nenmf_problem_t* problem, fl
     // more vectors than one co-resident grid: compressed problems go to the
     // batched kernel (snapshots are single-kernel only)
     if (plain || pa.record_G || pa.record_F || pa.record_time_ns) return NMF_ERR_UNSUPPORTED;
-    const nenmf_batch_config_t cfg{kLargeCluster};
+    const nenmf_batch_config_t cfg{kLargeCluster, 0};
     return nenmf_solve_batched(stream, 1, &pr, &G, &F, &pa, &cfg, stats, workspace, workspace_bytes);
   }
   cudaStream_t s = (cudaStream_t)stream;

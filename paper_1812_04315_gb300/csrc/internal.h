@@ -284,6 +284,13 @@ void count_launches(int k);
 // Failure-path testing (nmf_inject_fault): the fault the next launches carry
 // and the limit of every bounded device wait (2 s unless a test lowers it).
 int injected_fault();
+// Whether the compression kernels may be launched as programmatic dependents
+// (on by default; a PdlOff object turns it off for this host thread while it lives).
+bool pdl_allowed();
+struct PdlOff {
+  PdlOff();
+  ~PdlOff();
+};
 unsigned long long wait_limit_ns();
 
 // Raises a kernel's dynamic shared-memory limit to `bytes` once per device

@@ -578,7 +578,7 @@ cudaError_t rows_launch(const RowJob* jobs, int njobs, Control* ctrl, cudaStream
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl_allowed() ? 1 : 0;
   count_launches(1);
   return cudaLaunchKernelEx(&cfg, rows_kernel, rj, ctrl);
 }

@@ -730,7 +730,7 @@ cudaError_t launch_pdl(const void* fn, int ctas, int threads, size_t smem, cudaS
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl_allowed() ? 1 : 0;
   void* args[] = {const_cast<CUtensorMap*>(&mA), const_cast<CUtensorMap*>(&mB), const_cast<TcParams*>(&P)};
   return cudaLaunchKernelExC(&cfg, fn, args);
 }

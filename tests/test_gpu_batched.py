@@ -99,9 +99,9 @@ def test_batched_first_outer_iteration_factors(nmf, batch):
         assert_entrywise(_np(F), Fo, 1e-4, "F after one outer iteration")
 
 
-@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8, (2, 128), (8, 128)])
 def test_cluster_sizes_agree(nmf, batch, cluster):
-    # a different cluster size splits the sums differently: float32 rounding only
+    # a different cluster size (or CTA size) splits the sums differently: float32 rounding only
     Gs, Fs, stats = _run(nmf, batch, 6, 10, cluster=cluster)
     for b, G, F, st in zip(batch, Gs, Fs, stats):
         assert st.status == 0
@@ -192,16 +192,18 @@ def test_full_size_batch(nmf):
 
 
 def test_autotune_picks_a_measured_cluster_size(nmf, batch):
-    # the autotuner times every valid cluster size on copies of the factors:
-    # it returns the fastest of its own measurements and leaves G, F alone
+    # the autotuner times every valid (cluster size, threads per CTA) on copies
+    # of the factors: it returns the fastest of its own measurements and leaves G, F alone
     probs, Gs, Fs = [], [], []
     for b in batch:
         probs.append(nmf.compressed_problem(_t(b["L"]), _t(b["R"]), _t(b["XL"]), _t(b["XR"]), b["p"]))
         Gs.append(_t(b["G0"]))
         Fs.append(_t(b["F0"]))
     best, times = nmf.batch_autotune(probs, Gs, Fs, 20, 10, tol=1e-6, trial_outer=2)
-    assert best in (1, 2, 4, 8) and best in times
+    assert best[0] in (1, 2, 4, 8) and best[1] in (128, 256) and best in times
     assert times[best] == min(times.values()) and all(t > 0.0 for t in times.values())
+    assert len(times) >= 2  # both CTA sizes were measured
+    assert nmf.batch_plan([probs[0]], 20, 10, cluster=best)[0] == best
     for b, G, F in zip(batch, Gs, Fs):
         np.testing.assert_array_equal(_np(G), b["G0"].astype(np.float64))
         np.testing.assert_array_equal(_np(F), b["F0"].astype(np.float64))
