@@ -508,10 +508,10 @@ nmf_status_t nmf_rre(nmf_stream_t stream, int n, int m, int p, const float* X, c
  * The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory. Examples: a hook that evaluates the fit
  * between solver calls inside a framework that owns all device memory
- * through its own pool, code running while a stream is being captured into a
- * CUDA graph (where a cudaMalloc would break or be barred from the capture),
- * or a loop that must not call cudaMalloc because it can synchronise the
- * device. Such callers still pass X, G, F and `out`, but no workspace.
+ * through its own pool and hands out no buffers to plug-ins, or a
+ * monitoring loop that must not call cudaMalloc because cudaMalloc can
+ * synchronise the device and stall the work it watches. Such callers still
+ * pass X, G, F and `out`, but no workspace.
  *
  * Same result as nmf_rre (same kernels, same fixed summation order). The
  * per-block partial sums live in one fixed array inside the library

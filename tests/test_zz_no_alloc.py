@@ -1,12 +1,13 @@
 """nmf_rre_static: the RRE entry point that allocates nothing.
 
 Callers that cannot allocate device memory (a fit-monitoring hook inside a
-framework that owns every device allocation, code running under stream
-capture) use it with only X, G, F and the output; its scratch is a fixed array
-inside the library. Checked through the C ABI against nmf_rre (the entry
-point with a caller workspace) on two calls in a row, with different sizes so
-that contents left by the first call would show in the second. This file is
-collected last, so a run that stops at the first failure has run all others.
+framework that owns every device allocation, a loop that must not call
+cudaMalloc because it can synchronise the device) use it with only X, G, F and
+the output; its scratch is a fixed array inside the library. Checked through
+the C ABI against nmf_rre (the entry point with a caller workspace) on two
+calls in a row, with different sizes so that contents left by the first call
+would show in the second. This file is collected last, so a run that stops
+at the first failure has run all others.
 """
 
 import ctypes
