@@ -95,14 +95,16 @@ __device__ __forceinline__ bool grid_wait(unsigned int* bar, unsigned int target
   if (threadIdx.x == 0) {
     cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(*bar);
     int ok = 1;
-    const unsigned long long t0 = global_ns();
+    unsigned long long t0 = 0ull;  // the clock is read from the first check on
     unsigned int spins = 0;
     while (cnt.load(cuda::memory_order_acquire) < target) {
       // the abort flag and the clock every 16 polls: a tighter loop notices
       // the last arrival sooner, and the wait stays bounded
       if ((++spins & 15u) != 0u) continue;
       if (*((volatile int*)&c->abort)) { ok = 0; break; }
-      if (global_ns() - t0 > wait_ns) {
+      if (t0 == 0ull) {
+        t0 = global_ns();
+      } else if (global_ns() - t0 > wait_ns) {
         set_status(c, NMF_ERR_DEVICE_TIMEOUT);
         *((volatile int*)&c->abort) = 1;
         ok = 0;
@@ -465,8 +467,9 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
             stop_record_term<PM>(pterm, nrec, active ? pg_sq<PM>(f, gf) : 0.f, f, keep, eps2_f);
             if (++nrec == kBlockP || k + 1 == a.max_inner) {
               stop_sum_terms(stop_s, nrec, pterm);
+              // pterm is free once summed: it gathers the other CTAs' words
               const int r = stop_decide(stop_s, nrec, base, a.slots, epoch, eps2, eps2_f, ctas_s, a.withhold != 0,
-                                        ctrl, a.wait_ns);
+                                        ctrl, a.wait_ns, pterm, kBlockP * T);
               if (r == -2) {
                 aborted = true;
                 break;

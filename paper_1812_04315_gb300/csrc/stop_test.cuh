@@ -70,6 +70,8 @@ __device__ __forceinline__ uint32_t stop_tag(int epoch, int j) { return ((uint32
 struct StopShared {
   float part[kMaxStopBlock][kWarps];  // the warps' partials of the block's tests (+inf: failed by the warp's terms)
   int result;                         // the block's outcome (see stop_decide)
+  unsigned int fails;                 // the tests this CTA's partial fails on its own (bit i: test i)
+  int ok;                             // the gathering of the other CTAs' words completed
   double total;                       // the total of the test that passed
 };
 
@@ -125,14 +127,70 @@ __device__ __forceinline__ void stop_sum_terms(StopShared& S, int nb, const floa
       if (i < nb) S.part[i][threadIdx.x >> 5] = v[i];
 }
 
+// Every CTA's word of the tests not in `fails` (nb tests, ctas words each)
+// into stage[i * ctas + q] as floats, all loads of a thread in flight
+// together: one round trip to L2 instead of one per test. False when a wait
+// gave up (in every thread).
+__device__ inline bool stop_stage_words(const unsigned long long* slots, int nb, int base, int epoch, int ctas,
+                                        unsigned int fails, float* stage, Control* c, unsigned long long wait_ns,
+                                        int* ok_s) {
+  constexpr int kInFlight = 8;
+  const int NT = blockDim.x, total = nb * ctas;
+  unsigned long long t0 = 0ull;  // the clock is read only once a word is found missing
+  bool ok = true;
+  for (int i0 = threadIdx.x; i0 < total && ok; i0 += kInFlight * NT) {
+    unsigned long long w[kInFlight];
+#pragma unroll
+    for (int u = 0; u < kInFlight; ++u) {
+      const int idx = i0 + u * NT;
+      w[u] = 0ull;
+      if (idx < total && !((fails >> (idx / ctas)) & 1u)) {
+        cuda::atomic_ref<const unsigned long long, cuda::thread_scope_device> r(slots[(size_t)base * ctas + idx]);
+        w[u] = r.load(cuda::memory_order_relaxed);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kInFlight; ++u) {
+      const int idx = i0 + u * NT;
+      if (idx >= total) continue;
+      const int i = idx / ctas;
+      if ((fails >> i) & 1u) continue;
+      const uint32_t tag = stop_tag(epoch, base + i);
+      cuda::atomic_ref<const unsigned long long, cuda::thread_scope_device> r(slots[(size_t)base * ctas + idx]);
+      while ((uint32_t)(w[u] >> 32) != tag) {
+        if (t0 == 0ull) t0 = global_ns();
+        if (*((volatile int*)&c->abort) || global_ns() - t0 > wait_ns) {
+          ok = false;
+          break;
+        }
+        w[u] = r.load(cuda::memory_order_relaxed);
+      }
+      if (!ok) break;
+      stage[idx] = __uint_as_float((uint32_t)w[u]);
+    }
+  }
+  if (threadIdx.x == 0) *ok_s = 1;
+  __syncthreads();
+  if (!ok) *ok_s = 0;
+  __syncthreads();
+  return *ok_s != 0;
+}
+
 // Decides the nb tests base .. base+nb-1 just recorded (every thread calls
-// it; two block barriers). `ctas` CTAs (0 .. ctas-1) take part; slots holds
+// it; block barriers only). `ctas` CTAs (0 .. ctas-1) take part; slots holds
 // one row of ctas words per test. Returns the block index of the first test
 // that passed (its iterate is in keep slot i; S.total holds its total), -1
 // when none did, -2 when a wait gave up (status and abort flag are set).
+// With `stage` (stage_cap floats of shared memory, free during the call) and
+// nb * ctas <= stage_cap, the other CTAs' words of every undecided test are
+// gathered at once by the whole block before warp 0 sums them; otherwise
+// warp 0 gathers them test by test. Both take the same sums in the same
+// order, so the outcome and the totals are the same.
 __device__ inline int stop_decide(StopShared& S, int nb, int base, unsigned long long* slots, int epoch, double eps2,
-                                  float eps2_f, int ctas, bool withhold, Control* c, unsigned long long wait_ns) {
+                                  float eps2_f, int ctas, bool withhold, Control* c, unsigned long long wait_ns,
+                                  float* stage = nullptr, int stage_cap = 0) {
   __syncthreads();  // the block's partials are in S.part
+  const bool staged = stage != nullptr && nb * ctas <= stage_cap;
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     float own = 0.f;
@@ -151,6 +209,58 @@ __device__ inline int stop_decide(StopShared& S, int nb, int base, unsigned long
     // A CTA partial above eps^2 fails the test in every CTA (partials are
     // nonnegative and the sums below monotone): no other CTA's word needed.
     const unsigned int fails = __ballot_sync(0xffffffffu, lane < nb && own > eps2_f);
+    if (lane == 0) S.fails = fails;
+  }
+  if (staged) {
+    __syncthreads();
+    const unsigned int fails = S.fails;
+    if ((~fails & ((1u << nb) - 1u)) == 0u) return -1;  // every test failed on this CTA's own partial
+    if (!stop_stage_words(slots, nb, base, epoch, ctas, fails, stage, c, wait_ns, &S.ok)) {
+      if (threadIdx.x == 0) {
+        S.result = -2;
+        set_status(c, NMF_ERR_DEVICE_TIMEOUT);
+        *((volatile int*)&c->abort) = 1;
+      }
+      __syncthreads();
+      return -2;
+    }
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      int result = -1;
+      double total = 0.0;
+      for (int i = 0; i < nb; ++i) {
+        if ((fails >> i) & 1u) continue;
+        // every CTA's partial of test base + i, summed in float-float in a fixed order
+        DF acc{0.f, 0.f};
+        for (int q = lane; q < ctas; q += 32) df_add(acc, stage[i * ctas + q], 0.f);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+          const float lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+          DF a = (lane & o) ? DF{hi, lo} : acc;  // lower lane's value first in both lanes
+          const DF b = (lane & o) ? acc : DF{hi, lo};
+          df_add(a, b.hi, b.lo);
+          acc = a;
+        }
+        const double tot = (double)acc.hi + (double)acc.lo;
+        if (tot <= eps2) {
+          result = i;
+          total = tot;
+          break;
+        }
+      }
+      if (lane == 0) {
+        S.result = result;
+        S.total = total;
+      }
+    }
+    __syncthreads();
+    return S.result;
+  }
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    __syncwarp();  // lane 0's S.fails
+    const unsigned int fails = S.fails;
     int result = -1;
     double total = 0.0;
     for (int i = 0; i < nb; ++i) {
@@ -158,13 +268,14 @@ __device__ inline int stop_decide(StopShared& S, int nb, int base, unsigned long
       // every CTA's partial of test base + i, summed in float-float in a fixed order
       const uint32_t tag = stop_tag(epoch, base + i);
       const unsigned long long* row = slots + (size_t)(base + i) * ctas;
-      const unsigned long long t0 = global_ns();
+      unsigned long long t0 = 0ull;  // the clock is read only once a word is found missing
       int ok = 1;
       DF acc{0.f, 0.f};
       for (int q = lane; q < ctas && ok; q += 32) {
         cuda::atomic_ref<const unsigned long long, cuda::thread_scope_device> r(row[q]);
         unsigned long long w = r.load(cuda::memory_order_relaxed);
         while ((uint32_t)(w >> 32) != tag) {
+          if (t0 == 0ull) t0 = global_ns();
           if (*((volatile int*)&c->abort) || global_ns() - t0 > wait_ns) {
             ok = 0;
             break;
