@@ -74,7 +74,8 @@ __device__ __forceinline__ bool mbar_done(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait for phase `parity`; false after wait_ns or on abort.
 __device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, Control* c, unsigned long long wait_ns) {
-  const unsigned long long t0 = global_ns();
+  if (mbar_done(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();  // the clock is read only for a wait that did not end at once
   while (!mbar_done(bar, parity)) {
     if (*((volatile int*)&c->abort) || global_ns() - t0 > wait_ns) return false;
   }

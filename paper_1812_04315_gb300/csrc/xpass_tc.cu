@@ -90,7 +90,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Bounded wait: false when the deadline passed or the CTA is aborting.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           unsigned long long wait_ns) {
-  const unsigned long long t0 = global_ns();
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();  // the clock is read only for a wait that did not end at once
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
     if (global_ns() - t0 > wait_ns) {
