@@ -78,18 +78,20 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Grid barrier on a counter that only grows: arrival r of every CTA lifts it
-// to r * gridDim.x. The arrival's fence publishes the CTA's stores (taken
-// after the block barrier) before the count; the waiter fences after it.
+// to r * gridDim.x. After the block barrier, thread 0's release reduction
+// publishes the CTA's stores with the count; the waiter's acquire load of
+// the count makes them visible, and the block barrier after it passes them
+// on to the CTA's threads.
 __device__ __forceinline__ void grid_arrive(unsigned int* bar) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1u);
-  }
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
 }
 
 // Thread 0 waits for `target` arrivals; false (in every thread) on timeout,
-// an abort raised elsewhere or a device error already recorded by any CTA.
+// an abort raised elsewhere or a device error recorded by any CTA. The
+// status word is loaded together with the count in every poll, so the last
+// poll costs one round trip; an error recorded just before the last arrival
+// may be seen one wait later (the call still ends with that status).
 __device__ __forceinline__ bool grid_wait(unsigned int* bar, unsigned int target, Control* c,
                                           unsigned long long wait_ns, int* ok_s) {
   if (threadIdx.x == 0) {
@@ -97,7 +99,12 @@ __device__ __forceinline__ bool grid_wait(unsigned int* bar, unsigned int target
     int ok = 1;
     unsigned long long t0 = 0ull;  // the clock is read from the first check on
     unsigned int spins = 0;
-    while (cnt.load(cuda::memory_order_acquire) < target) {
+    int status = 0;
+    for (;;) {
+      // the status first: the acquire load of the count orders what follows it
+      status = *((volatile int*)&c->status);
+      const unsigned int arrived = cnt.load(cuda::memory_order_acquire);
+      if (arrived >= target) break;
       // the abort flag and the clock every 16 polls: a tighter loop notices
       // the last arrival sooner, and the wait stays bounded
       if ((++spins & 15u) != 0u) continue;
@@ -111,8 +118,7 @@ __device__ __forceinline__ bool grid_wait(unsigned int* bar, unsigned int target
         break;
       }
     }
-    __threadfence();
-    if (*((volatile int*)&c->status) != 0) ok = 0;
+    if (status != 0) ok = 0;
     *ok_s = ok;
   }
   __syncthreads();
@@ -183,6 +189,7 @@ __device__ __forceinline__ void form_h(const float* Rw, int p, int nu, float* Ws
     }
     const int d = c + r;
     float s = 0.f;
+#pragma unroll 4
     for (int k = 0; k < nu; ++k) s = fmaf(Ws[c * kWs + k], Ws[d * kWs + k], s);
     Hs[c * PM + d] = s;
     Hs[d * PM + c] = s;
@@ -195,6 +202,7 @@ template <int PM>
 __device__ __forceinline__ void form_b(const float* Ws, const float* Ds, int nu, float* b) {
 #pragma unroll
   for (int c = 0; c < PM; ++c) b[c] = 0.f;
+#pragma unroll 4
   for (int k = 0; k < nu; ++k) {
     const float dk = Ds[k * kFs + threadIdx.x];
 #pragma unroll
