@@ -333,12 +333,16 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowJobs jobs, Control
   // (its X pass partials, Gram partials, flags) before reading anything
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
-  if (call_failed(ctrl)) return;
   int jj = 0;
   while (jj + 1 < jobs.njobs && (int)blockIdx.x >= jobs.start[jj + 1]) ++jj;
   const RowJob& J = jobs.j[jj];
-  if (J.run_flag && *((volatile const int*)J.run_flag) == 0) return;
-  if (J.skip_flag && *((volatile const int*)J.skip_flag) != 0) return;
+  {
+    // the call's status and this job's flags, loaded together (one round trip)
+    const int failed = *((volatile const int*)&ctrl->status);
+    const int run = J.run_flag ? *((volatile const int*)J.run_flag) : 1;
+    const int skip = J.skip_flag ? *((volatile const int*)J.skip_flag) : 0;
+    if (failed != 0 || run == 0 || skip != 0) return;
+  }
   const int cta = blockIdx.x - jobs.start[jj];
   const int r0 = cta * kOrthRows;
   const int rows = min(kOrthRows, J.N - r0);
