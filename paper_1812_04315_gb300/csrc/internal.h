@@ -219,6 +219,7 @@ int solve_max_coresident(int p, int nu, int epi, int groups_in);
 struct PersistPlan {
   bool ok;
   int ctas, PM;
+  int PL;  // rows of the inner loop's register arithmetic (<= PM; see persist.cu)
   size_t smem;
   bool keep_shared;  // pending stop-test iterates in shared memory (else in the workspace)
 };

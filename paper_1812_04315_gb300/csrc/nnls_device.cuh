@@ -43,13 +43,14 @@ __host__ __device__ constexpr int packed_index(int i, int j) {
   return i <= j ? i * PM - i * (i - 1) / 2 + (j - i) : j * PM - j * (j - 1) / 2 + (i - j);
 }
 // Small PM: the upper triangle of H held in registers (every index below is
-// a compile-time constant), loaded once per solve.
-template <int PM>
+// a compile-time constant), loaded once per solve; LD is the row stride of
+// Hs (its padded rank, >= PM).
+template <int PM, int LD = PM>
 __device__ __forceinline__ void load_packed(const float* Hs, float* Hp) {
 #pragma unroll
   for (int i = 0; i < PM; ++i)
 #pragma unroll
-    for (int j = i; j < PM; ++j) Hp[packed_index<PM>(i, j)] = Hs[i * PM + j];
+    for (int j = i; j < PM; ++j) Hp[packed_index<PM>(i, j)] = Hs[i * LD + j];
 }
 // g = H y - b from the packed registers: the operations of hmatvec in the
 // same order (H is exactly symmetric: H_cd and H_dc are the same products

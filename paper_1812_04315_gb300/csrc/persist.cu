@@ -269,8 +269,15 @@ __device__ __forceinline__ void form_share(const float* Ys, const float* Es, int
   for (int o = P + threadIdx.x; o < P4; o += blockDim.x) part[o] = 0.f;
 }
 
-template <int PM, bool TEST, bool RESTART>
+// PM: the padded rank of H, W, the kept iterates' layout and the columns in
+// shared memory. PL <= PM: the rows the inner loop's register arithmetic
+// runs over (iterates, gradients, b and the packed upper triangle of H); the
+// rows from p on are exact zeros (zero rows of W give zero rows of H and b,
+// hence zero gradients and iterates), so leaving out those from PL on gives
+// the values of the full-width loop (up to the sign of a zero).
+template <int PM, int PL, bool TEST, bool RESTART>
 __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
+  static_assert(PL <= PM && (PL == PM || PL <= kPackedMax), "a shorter loop rank needs H in registers");
   Control* ctrl = a.ctrl;
   const int p = a.p, nu = a.nu;
   const int tid = threadIdx.x, NT = blockDim.x;
@@ -397,17 +404,17 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
       stage_shares(s == 0 ? a.partF : a.partG, G, P4, scratch);
       sum_shares(scratch, G, P4, Rw, Red);
       form_h<PM>(Rw, p, nu, Ws, Hs);
-      float y[PM], b[PM], f[PM];
+      float y[PL], b[PL], f[PL];
 #pragma unroll
-      for (int c = 0; c < PM; ++c) {
+      for (int c = 0; c < PL; ++c) {
         y[c] = active ? Y[c * kFs + tid] : 0.f;
         b[c] = 0.f;
       }
       if (active) {
-        form_b<PM>(Ws, s == 0 ? DG : DF, nu, b);
+        form_b<PL>(Ws, s == 0 ? DG : DF, nu, b);
         bool bad = false;
 #pragma unroll
-        for (int c = 0; c < PM; ++c) bad |= !isfinite(b[c]) || !isfinite(y[c]);
+        for (int c = 0; c < PL; ++c) bad |= !isfinite(b[c]) || !isfinite(y[c]);
         if (bad) set_status(ctrl, NMF_ERR_NONFINITE);
       }
       // L_c by the whole block (the reduction scratch is consumed)
@@ -421,17 +428,17 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
       const float Lc = (float)Lc_d;
       int iters = 0;
 #pragma unroll
-      for (int c = 0; c < PM; ++c) f[c] = y[c];
+      for (int c = 0; c < PL; ++c) f[c] = y[c];
       double pg2_final = 0.0;
       if (Lc > 0.f && mine) {
-        constexpr bool packed = PM <= kPackedMax;
-        float Hp[packed ? PM * (PM + 1) / 2 : 1];
-        if constexpr (packed) load_packed<PM>(Hs, Hp);
-        float g[PM], fp[PM], gp[PM];
-        if constexpr (packed) hmatvec_packed<PM>(Hp, y, b, g);
+        constexpr bool packed = PL <= kPackedMax;
+        float Hp[packed ? PL * (PL + 1) / 2 : 1];
+        if constexpr (packed) load_packed<PL, PM>(Hs, Hp);
+        float g[PL], fp[PL], gp[PL];
+        if constexpr (packed) hmatvec_packed<PL>(Hp, y, b, g);
         else hmatvec<PM>(Hs, y, b, g);
 #pragma unroll
-        for (int c = 0; c < PM; ++c) {
+        for (int c = 0; c < PL; ++c) {
           fp[c] = y[c];
           gp[c] = g[c];
         }
@@ -444,16 +451,16 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
         bool aborted = false;
         for (int k = 0; k < a.max_inner; ++k) {
 #pragma unroll
-          for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
+          for (int c = 0; c < PL; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], inv_Lc, y[c]));
           float beta = beta_next;
           if (k + 1 < a.max_inner) beta_next = __ldg(a.beta + k + 1);
-          float gf[PM];
-          if constexpr (packed) hmatvec_packed<PM>(Hp, f, b, gf);
+          float gf[PL];
+          if constexpr (packed) hmatvec_packed<PL>(Hp, f, b, gf);
           else hmatvec<PM>(Hs, f, b, gf);
           if (RESTART) {
             float obj = 0.f, sc = 0.f;
 #pragma unroll
-            for (int c = 0; c < PM; ++c) {
+            for (int c = 0; c < PL; ++c) {
               obj = fmaf(f[c], gf[c] - b[c], obj);
               sc = fmaf(fabsf(f[c]), fabsf(gf[c]) + fabsf(b[c]), sc);
             }
@@ -464,7 +471,7 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
             ++rs;
           }
 #pragma unroll
-          for (int c = 0; c < PM; ++c) {
+          for (int c = 0; c < PL; ++c) {
             y[c] = fmaf(beta, f[c] - fp[c], f[c]);
             g[c] = fmaf(beta, gf[c] - gp[c], gf[c]);
             fp[c] = f[c];
@@ -472,7 +479,7 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
           }
           iters = k + 1;
           if (TEST && k + 1 >= a.min_inner) {
-            stop_record_term<PM>(pterm, nrec, active ? pg_sq<PM>(f, gf) : 0.f, f, keep, eps2_f);
+            stop_record_term<PL>(pterm, nrec, active ? pg_sq<PL>(f, gf) : 0.f, f, keep, eps2_f);
             if (++nrec == kBlockP || k + 1 == a.max_inner) {
               stop_sum_terms(stop_s, nrec, pterm);
               // pterm is free once summed: it gathers the other CTAs' words
@@ -484,9 +491,9 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
               }
               if (r >= 0) {
                 // the first test that passed: its iterate, as the sequential rule returns it
-                const float* slot = keep + (size_t)r * PM * T;
+                const float* slot = keep + (size_t)r * PL * T;
 #pragma unroll
-                for (int c = 0; c < PM; ++c) f[c] = slot[c * T + tid];
+                for (int c = 0; c < PL; ++c) f[c] = slot[c * T + tid];
                 stop_j = base + r;
                 break;
               }
@@ -500,24 +507,24 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
         // ||P grad||^2 of the returned iterate: only the last update's
         // reaches the statistics
         if (stop_j >= 0) pg2_final = cta == 0 ? stop_s.total : 0.0;
-        else if (t == a.max_outer - 1) pg2_final = block_sum_df(active ? pg_sq<PM>(fp, gp) : 0.f, red);
+        else if (t == a.max_outer - 1) pg2_final = block_sum_df(active ? pg_sq<PL>(fp, gp) : 0.f, red);
       }
       // ---- outputs of the phase ----
       if (active) {
         bool bad = false;
 #pragma unroll
-        for (int c = 0; c < PM; ++c) {
+        for (int c = 0; c < PL; ++c) {
           bad |= c < p && !isfinite(f[c]);
           Y[c * kFs + tid] = c < p ? f[c] : 0.f;
         }
         if (bad) set_status(ctrl, NMF_ERR_NONFINITE);
         if (s == 0 && a.record_G) {
 #pragma unroll
-          for (int c = 0; c < PM; ++c)
+          for (int c = 0; c < PL; ++c)
             if (c < p) a.record_G[((size_t)t * a.n + col) * p + c] = f[c];
         } else if (s == 1 && a.record_F) {
 #pragma unroll
-          for (int c = 0; c < PM; ++c)
+          for (int c = 0; c < PL; ++c)
             if (c < p) a.record_F[((size_t)t * p + c) * a.m + col] = f[c];
         }
       }
@@ -576,22 +583,22 @@ size_t persist_smem(int nu, int p, int ctas, bool keep_shared) {
   return ((size_t)2 * PM * kFs + 4 * vecF + scratch) * sizeof(float);
 }
 
-template <int PM, bool TEST, bool RESTART>
+template <int PM, int PL, bool TEST, bool RESTART>
 const void* persist_fn() {
-  return (const void*)persist_kernel<PM, TEST, RESTART>;
+  return (const void*)persist_kernel<PM, PL, TEST, RESTART>;
 }
 
-template <int PM>
+template <int PM, int PL = PM>
 const void* pick(bool test, bool restart) {
-  return test ? (restart ? persist_fn<PM, true, true>() : persist_fn<PM, true, false>())
-              : (restart ? persist_fn<PM, false, true>() : persist_fn<PM, false, false>());
+  return test ? (restart ? persist_fn<PM, PL, true, true>() : persist_fn<PM, PL, true, false>())
+              : (restart ? persist_fn<PM, PL, false, true>() : persist_fn<PM, PL, false, false>());
 }
 
-const void* kernel_for(int PM, bool test, bool restart) {
+const void* kernel_for(int PM, int PL, bool test, bool restart) {
   switch (PM) {
     case 4: return pick<4>(test, restart);
-    case 8: return pick<8>(test, restart);
-    case 12: return pick<12>(test, restart);
+    case 8: return PL == 6 ? pick<8, 6>(test, restart) : pick<8>(test, restart);
+    case 12: return PL == 10 ? pick<12, 10>(test, restart) : pick<12>(test, restart);
     case 16: return pick<16>(test, restart);
     case 24: return pick<24>(test, restart);
     default: return pick<32>(test, restart);
@@ -610,6 +617,9 @@ size_t smem_for(int PM, int nu, int p, int ctas, bool keep_shared) {
 }
 
 int pad_rank_p(int p) { return p <= 4 ? 4 : p <= 8 ? 8 : p <= 12 ? 12 : p <= 16 ? 16 : p <= 24 ? 24 : 32; }
+// The inner loop's rank: two rows fewer than the padding where p leaves
+// them zero, for the register-resident ranks 8 and 12.
+int loop_rank(int p, int PM) { return (PM == 8 || PM == 12) && p <= PM - 2 ? PM - 2 : PM; }
 
 }  // namespace
 
@@ -621,13 +631,14 @@ PersistPlan persist_plan(int n, int m, int p, int nu, bool test, bool restart) {
   const int P4 = partial_stride(p * nu);
   pl.ctas = C;
   pl.PM = pad_rank_p(p);
+  pl.PL = loop_rank(p, pl.PM);
   if ((long)C * P4 > kMaxReduceFloats) return pl;  // every CTA reads every share: keep that small
   if (C > kMaxStopCtas) return pl;
   int dev = 0, max_smem = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return pl;
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fn = kernel_for(pl.PM, test, restart);
+  const void* fn = kernel_for(pl.PM, pl.PL, test, restart);
   cudaFuncAttributes fa{};
   if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return pl;
   // pending iterates in shared memory when they fit, else in the workspace
@@ -684,7 +695,7 @@ cudaError_t persist_launch(const PersistPlan& pl, const PersistLaunch& L, cudaSt
   a.ctasG = ceil_div(L.n, T);
   a.ctasF = ceil_div(L.m, T);
   const bool test = L.tol > 0.0;
-  const void* fn = kernel_for(pl.PM, test, L.restart != 0);
+  const void* fn = kernel_for(pl.PM, pl.PL, test, L.restart != 0);
   cudaError_t e = allow_dynamic_smem(fn, (int)pl.smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg{};

@@ -3,12 +3,14 @@ cooperative launch) against the per-update launches of the same method.
 
 Both paths run the same arithmetic in the same order: the per-CTA shares of
 the p x nu products, their fixed-order sums, H, L_c, B, the inner loop of
-Sec. 2 with its stop test, eps from the projected gradients at (G0, F0). So
-their factors, statistics and snapshots agree bit for bit; the oracle
-parity of the default (persistent) path is tests/test_gpu_solve.py's.
-Cases cover ragged tiles, n != m (CTAs idle on one side), p = 1, nu = 1,
-p = 32, the stop test with early stops, min_inner, adaptive restart,
-snapshots, zero outer iterations and a zero factor (L_c = 0).
+Sec. 2 with its stop test, eps from the projected gradients at (G0, F0).
+(For p <= 6 at padded rank 8 and p in 9..10 at rank 12 the persistent
+inner loop leaves out two padding rows, which hold exact zeros.) So their
+factors, statistics and snapshots agree bit for bit; the oracle parity of
+the default (persistent) path is tests/test_gpu_solve.py's. Cases cover
+ragged tiles, n != m (CTAs idle on one side), p = 1, nu = 1, p = 32, both
+shortened loop ranks, the stop test with early stops, min_inner, adaptive
+restart, snapshots, zero outer iterations and a zero factor (L_c = 0).
 """
 
 import numpy as np
@@ -61,6 +63,8 @@ CASES = [
     (500, 400, 6, 10, 5, 10, dict(tol=0.0, restart=True)),
     (64, 40, 4, 6, 5, 10, dict(tol=1e-6)),
     (300, 300, 6, 12, 0, 10, dict(tol=1e-6)),
+    (900, 1100, 6, 14, 8, 10, dict(tol=1e-5)),
+    (600, 500, 9, 19, 6, 20, dict(tol=1e-6, restart=True)),
 ]
 
 
