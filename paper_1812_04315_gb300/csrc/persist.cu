@@ -448,6 +448,7 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
         const float inv_Lc = 1.f / Lc;
         const float eps2_f = eps2 < 0.0 ? 0.f : __double2float_rd(eps2);  // eps^2 rounded down to float
         int stop_j = -1, nrec = 0, base = 0;  // tests: recorded in this block, decided before it
+        unsigned int wfail = 0u;              // the warp's failed votes in this block (bit per test)
         bool aborted = false;
         for (int k = 0; k < a.max_inner; ++k) {
 #pragma unroll
@@ -479,9 +480,11 @@ __global__ void __launch_bounds__(kThreadsAll, 1) persist_kernel(PArgs a) {
           }
           iters = k + 1;
           if (TEST && k + 1 >= a.min_inner) {
-            stop_record_term<PL>(pterm, nrec, active ? pg_sq<PL>(f, gf) : 0.f, f, keep, eps2_f);
+            if (stop_record_term<PL>(pterm, nrec, active ? pg_sq<PL>(f, gf) : 0.f, f, keep, eps2_f))
+              wfail |= 1u << nrec;
             if (++nrec == kBlockP || k + 1 == a.max_inner) {
-              stop_sum_terms(stop_s, nrec, pterm);
+              stop_sum_terms(stop_s, nrec, pterm, wfail);
+              wfail = 0u;
               // pterm is free once summed: it gathers the other CTAs' words
               const int r = stop_decide(stop_s, nrec, base, a.slots, epoch, eps2, eps2_f, ctas_s, a.withhold != 0,
                                         ctrl, a.wait_ns, pterm, kBlockP * T);

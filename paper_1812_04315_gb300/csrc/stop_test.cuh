@@ -97,8 +97,9 @@ __device__ __forceinline__ void stop_record(StopShared& S, int i, float term, co
 // iterate as stop_record takes them, and this thread's term (+inf when its
 // warp fails the test, so that the later warp sum is +inf as stop_record
 // records it) in pterm[i][T].
+// Returns the warp's vote (true: the test fails in this warp).
 template <int PM>
-__device__ __forceinline__ void stop_record_term(float* pterm, int i, float term, const float* f, float* keep,
+__device__ __forceinline__ bool stop_record_term(float* pterm, int i, float term, const float* f, float* keep,
                                                  float eps2_f) {
   const bool fails = __any_sync(0xffffffffu, term > eps2_f);
   if (!fails) {
@@ -107,13 +108,22 @@ __device__ __forceinline__ void stop_record_term(float* pterm, int i, float term
     for (int k = 0; k < PM; ++k) slot[k * T + threadIdx.x] = f[k];
   }
   pterm[i * T + threadIdx.x] = fails ? __int_as_float(0x7f800000) : term;
+  return fails;
 }
 
 // The warp sums of the block's nb tests recorded by stop_record_term, into
 // S.part (the values stop_record writes): all kMaxStopBlock sums advance
 // together through warp_sum's butterfly (the same steps per value, so the
-// same sums), their shuffles interleaved.
-__device__ __forceinline__ void stop_sum_terms(StopShared& S, int nb, const float* pterm) {
+// same sums), their shuffles interleaved. failed: bit i set when the warp's
+// vote failed test i (warp-uniform); when every test failed, each sum is
+// +inf (every lane recorded +inf) and is written as such.
+__device__ __forceinline__ void stop_sum_terms(StopShared& S, int nb, const float* pterm, unsigned int failed) {
+  const unsigned int all = (1u << nb) - 1u;
+  if ((failed & all) == all) {
+    if ((threadIdx.x & 31) == 0)
+      for (int i = 0; i < nb; ++i) S.part[i][threadIdx.x >> 5] = __int_as_float(0x7f800000);
+    return;
+  }
   float v[kMaxStopBlock];
 #pragma unroll
   for (int i = 0; i < kMaxStopBlock; ++i) v[i] = i < nb ? pterm[i * T + threadIdx.x] : 0.f;
