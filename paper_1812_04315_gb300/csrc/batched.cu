@@ -205,21 +205,21 @@ struct LoopState {
 // extrapolated point), g = grad at y, fp and gp = previous iterate and its
 // gradient; with restart on, rs (iterations since the vector's last
 // restart) and objp (its previous objective); f returns the last iterate.
-template <int PM>
+template <int PL, int PM>
 __device__ __forceinline__ void iterate(const float* Hs, const float* b, const float* beta, float invL, int k0, int k1,
                                         float* y, float* g, float* fp, float* gp, float* f, float* pgt, int restart,
                                         int& rs, float& objp) {
   for (int k = k0; k < k1; ++k) {
 #pragma unroll
-    for (int c = 0; c < PM; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], invL, y[c]));
-    float gf[PM];
-    hmatvec_rolled<PM>(Hs, f, b, gf);
+    for (int c = 0; c < PL; ++c) f[c] = fmaxf(0.f, fmaf(-g[c], invL, y[c]));
+    float gf[PL];
+    hmatvec_rolled<PL, PM>(Hs, f, b, gf);
     float bk;
     if (restart) {
       // the vector's objective 1/2 f^T H f - b^T f = 1/2 f^T (gf - b); a rise drops the momentum
       float obj = 0.f, sc = 0.f;
 #pragma unroll
-      for (int c = 0; c < PM; ++c) {
+      for (int c = 0; c < PL; ++c) {
         obj = fmaf(f[c], gf[c] - b[c], obj);
         sc = fmaf(fabsf(f[c]), fabsf(gf[c]) + fabsf(b[c]), sc);
       }
@@ -231,9 +231,9 @@ __device__ __forceinline__ void iterate(const float* Hs, const float* b, const f
     } else {
       bk = __ldg(beta + k);
     }
-    if (pgt) pgt[(k - k0) * blockDim.x + threadIdx.x] += pg_sq<PM>(f, gf);
+    if (pgt) pgt[(k - k0) * blockDim.x + threadIdx.x] += pg_sq<PL>(f, gf);
 #pragma unroll
-    for (int c = 0; c < PM; ++c) {
+    for (int c = 0; c < PL; ++c) {
       y[c] = fmaf(bk, f[c] - fp[c], f[c]);
       g[c] = fmaf(bk, gf[c] - gp[c], gf[c]);
       fp[c] = f[c];
@@ -243,8 +243,11 @@ __device__ __forceinline__ void iterate(const float* Hs, const float* b, const f
 }
 
 // One factor update (mode 0: evaluate ||P grad||^2 at the current factor;
-// mode 1: the inner solve). `ph` counts phases (double buffers).
-template <int PM>
+// mode 1: the inner solve). `ph` counts phases (double buffers). PM: the
+// padded rank of W, H and the saved loop state; PL <= PM: the rows of the
+// per-vector arithmetic (from p on every row is an exact zero, so leaving
+// out rows PL.. gives the same values).
+template <int PM, int PL>
 __device__ PhaseOut phase(const Side& s, int p, int nu, int mode, double eps2, const BatchArgs& A, Shared& S,
                           const LoopState& LS, int ph) {
   const uint32_t rank = cl_rank(), CS = cl_size();
@@ -333,21 +336,21 @@ __device__ PhaseOut phase(const Side& s, int p, int nu, int mode, double eps2, c
     const bool last = k1 == K;
     if (kind != 2) clear_pgt(S);
     for (int j = j0 + tid; j < j1; j += TB) {
-      float b[PM], y[PM], g[PM], fp[PM], gp[PM], f[PM];
+      float b[PL], y[PL], g[PL], fp[PL], gp[PL], f[PL];
       int rs = 0;
       float objp = 0.f;
-      form_b<PM>(s, S.Ws, nu, j, b);
+      form_b<PL>(s, S.Ws, nu, j, b);
       if (kb == 0) {
-        load_u<PM>(s, p, j, y);
-        hmatvec_rolled<PM>(S.Hs, y, b, g);
+        load_u<PL>(s, p, j, y);
+        hmatvec_rolled<PL, PM>(S.Hs, y, b, g);
 #pragma unroll
-        for (int c = 0; c < PM; ++c) {
+        for (int c = 0; c < PL; ++c) {
           fp[c] = y[c];
           gp[c] = g[c];
         }
       } else {
 #pragma unroll
-        for (int c = 0; c < PM; ++c) {
+        for (int c = 0; c < PL; ++c) {
           y[c] = S_in[(size_t)(0 * PM + c) * MJ + j];
           g[c] = S_in[(size_t)(1 * PM + c) * MJ + j];
           fp[c] = S_in[(size_t)(2 * PM + c) * MJ + j];
@@ -357,18 +360,18 @@ __device__ PhaseOut phase(const Side& s, int p, int nu, int mode, double eps2, c
         objp = S_in[(size_t)(4 * PM + 1) * MJ + j];
       }
       if (kind == 0) {
-        S.pgt[tid] += pg_sq<PM>(y, g);
+        S.pgt[tid] += pg_sq<PL>(y, g);
         continue;
       }
-      iterate<PM>(S.Hs, b, A.beta, invL, kb, kend, y, g, fp, gp, f, kind == 1 ? S.pgt : nullptr, A.restart, rs,
-                  objp);
+      iterate<PL, PM>(S.Hs, b, A.beta, invL, kb, kend, y, g, fp, gp, f, kind == 1 ? S.pgt : nullptr, A.restart, rs,
+                      objp);
       if (kind == 2) {
-        store_u<PM>(s, p, j, f, out.bad);
+        store_u<PL>(s, p, j, f, out.bad);
         continue;
       }
       if (!last) {
 #pragma unroll
-        for (int c = 0; c < PM; ++c) {
+        for (int c = 0; c < PL; ++c) {
           S_out[(size_t)(0 * PM + c) * MJ + j] = y[c];
           S_out[(size_t)(1 * PM + c) * MJ + j] = g[c];
           S_out[(size_t)(2 * PM + c) * MJ + j] = fp[c];
@@ -379,9 +382,9 @@ __device__ PhaseOut phase(const Side& s, int p, int nu, int mode, double eps2, c
       }
       if (test) {
 #pragma unroll
-        for (int c = 0; c < PM; ++c) LS.res[(size_t)c * MJ + j] = f[c];
+        for (int c = 0; c < PL; ++c) LS.res[(size_t)c * MJ + j] = f[c];
       } else if (last) {
-        store_u<PM>(s, p, j, f, out.bad);
+        store_u<PL>(s, p, j, f, out.bad);
       }
     }
     if (kind == 2) break;
@@ -411,10 +414,10 @@ __device__ PhaseOut phase(const Side& s, int p, int nu, int mode, double eps2, c
       }
       if (test)  // the block's last iterate is the result
         for (int j = j0 + tid; j < j1; j += TB) {
-          float f[PM];
+          float f[PL];
 #pragma unroll
-          for (int c = 0; c < PM; ++c) f[c] = LS.res[(size_t)c * MJ + j];
-          store_u<PM>(s, p, j, f, out.bad);
+          for (int c = 0; c < PL; ++c) f[c] = LS.res[(size_t)c * MJ + j];
+          store_u<PL>(s, p, j, f, out.bad);
         }
       break;
     }
@@ -427,7 +430,7 @@ __device__ PhaseOut phase(const Side& s, int p, int nu, int mode, double eps2, c
   return out;
 }
 
-template <int PM>
+template <int PM, int PL = PM>
 __device__ void solve_problem(const BatchDesc& d, int inst, const BatchArgs& A, Shared& S, const LoopState& LS,
                               int& ph) {
   const int p = d.p, nu = d.nu;
@@ -446,7 +449,7 @@ __device__ void solve_problem(const BatchDesc& d, int inst, const BatchArgs& A, 
   for (int st = 0; st < steps; ++st) {
     const int sd = st & 1;
     const bool eval = st < nev;
-    const PhaseOut o = phase<PM>(sd ? sF : sG, p, nu, eval ? 0 : 1, eps2, A, S, LS, ph++);
+    const PhaseOut o = phase<PM, PL>(sd ? sF : sG, p, nu, eval ? 0 : 1, eps2, A, S, LS, ph++);
     if (eval) {
       ev += o.pg2;
       if (st == nev - 1) eps2 = A.tol * A.tol * ev;
@@ -533,12 +536,19 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batched_kernel(BatchArgs A) 
   for (int ii = A.start[cl]; ii < A.start[cl + 1]; ++ii) {
     const int inst = A.order[ii];
     const BatchDesc d = A.desc[inst];
-    // the smallest padded rank that holds p
+    // the smallest padded rank that holds p; in the classes 8 to 16 the
+    // per-vector arithmetic leaves out the two padding rows when p allows
     const int pm = d.p <= 4 ? 4 : d.p <= 8 ? 8 : d.p <= 12 ? 12 : d.p <= 16 ? 16 : d.p <= 24 ? 24 : 32;
+    const bool short_loop = d.p <= pm - 2;
     if (pm == 4) solve_problem<4>(d, inst, A, S, LS, ph);
-    if constexpr (PMAX >= 8) if (pm == 8) solve_problem<8>(d, inst, A, S, LS, ph);
-    if constexpr (PMAX >= 12) if (pm == 12) solve_problem<12>(d, inst, A, S, LS, ph);
-    if constexpr (PMAX >= 16) if (pm == 16) solve_problem<16>(d, inst, A, S, LS, ph);
+    if constexpr (PMAX >= 8)
+      if (pm == 8) short_loop ? solve_problem<8, 6>(d, inst, A, S, LS, ph) : solve_problem<8>(d, inst, A, S, LS, ph);
+    if constexpr (PMAX >= 12)
+      if (pm == 12)
+        short_loop ? solve_problem<12, 10>(d, inst, A, S, LS, ph) : solve_problem<12>(d, inst, A, S, LS, ph);
+    if constexpr (PMAX >= 16)
+      if (pm == 16)
+        short_loop ? solve_problem<16, 14>(d, inst, A, S, LS, ph) : solve_problem<16>(d, inst, A, S, LS, ph);
     if constexpr (PMAX >= 24) if (pm == 24) solve_problem<24>(d, inst, A, S, LS, ph);
     if constexpr (PMAX >= 32) if (pm == 32) solve_problem<32>(d, inst, A, S, LS, ph);
   }

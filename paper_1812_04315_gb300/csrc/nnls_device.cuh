@@ -67,24 +67,28 @@ __device__ __forceinline__ void hmatvec_packed(const float* Hp, const float* y, 
 
 // The same product with the loop over d kept rolled: one row of H live at a
 // time, for kernels with enough warps per SM to hide the shared-memory
-// latency and too many other live values to hold more of H.
-template <int PM>
+// latency and too many other live values to hold more of H. LD: the row
+// stride of Hs (a multiple of 4, >= PM); with PM < LD only the first PM rows
+// and columns take part (the others must be zero in y, which makes their
+// terms exact zeros).
+template <int PM, int LD = PM>
 __device__ __forceinline__ void hmatvec_rolled(const float* Hs, const float* y, const float* b, float* g) {
+  static_assert(LD % 4 == 0 && LD >= PM, "rows of H are read as float4");
 #pragma unroll
   for (int c = 0; c < PM; ++c) g[c] = -b[c];
 #pragma unroll 1
   for (int d = 0; d < PM; ++d) {
-    const float4* h = reinterpret_cast<const float4*>(Hs + d * PM);
+    const float4* h = reinterpret_cast<const float4*>(Hs + d * LD);
     float yd = 0.f;
 #pragma unroll
     for (int e = 0; e < PM; ++e) yd = (e == d) ? y[e] : yd;
 #pragma unroll
-    for (int c4 = 0; c4 < PM / 4; ++c4) {
+    for (int c4 = 0; c4 < (PM + 3) / 4; ++c4) {
       const float4 v = h[c4];
-      g[4 * c4 + 0] = fmaf(v.x, yd, g[4 * c4 + 0]);
-      g[4 * c4 + 1] = fmaf(v.y, yd, g[4 * c4 + 1]);
-      g[4 * c4 + 2] = fmaf(v.z, yd, g[4 * c4 + 2]);
-      g[4 * c4 + 3] = fmaf(v.w, yd, g[4 * c4 + 3]);
+      if (4 * c4 + 0 < PM) g[4 * c4 + 0] = fmaf(v.x, yd, g[4 * c4 + 0]);
+      if (4 * c4 + 1 < PM) g[4 * c4 + 1] = fmaf(v.y, yd, g[4 * c4 + 1]);
+      if (4 * c4 + 2 < PM) g[4 * c4 + 2] = fmaf(v.z, yd, g[4 * c4 + 2]);
+      if (4 * c4 + 3 < PM) g[4 * c4 + 3] = fmaf(v.w, yd, g[4 * c4 + 3]);
     }
   }
 }
