@@ -149,7 +149,12 @@ nmf_status_t nmf_compress_variant(nmf_stream_t stream, int n, int m, int nu, int
  * Many independent compressions (Alg. 2 and X_L, X_R for each): the items run
  * on up to 8 library-owned streams forked from `stream` (an event fork and
  * join, so the call is stream-ordered and capturable); each item draws its
- * sketches from its own seed. Results per item equal nmf_compress_variant's.
+ * sketches from its own seed. Each item's X passes are planned for one
+ * stream's share of the SMs (the device's SMs / min(count, 8)), so that the
+ * streams' passes run side by side: an item whose tile grid fits that share
+ * gets nmf_compress_variant's plan and results bit for bit; a larger one
+ * gets a split-K partition with fewer parts (the same products summed in
+ * another order: equal to rounding).
  * The library creates its streams and events once per device and keeps
  * them; concurrent enqueues on one device are serialised by a mutex.
  * Workspace: min(count, 8) slots of the largest item's compression workspace.

@@ -133,10 +133,21 @@ struct CompressWs {
   size_t bytes;
 };
 
+// SMs an X pass of the compression is planned for: all of them, or the
+// share of one lane while a batched compression (or its workspace query)
+// sets a budget on this host thread. A pass planned for fewer SMs leaves
+// the others to the other lanes' passes, which then run side by side.
+static thread_local int t_xpass_sms = 0;
+struct XPassSmBudget {
+  int prev;
+  explicit XPassSmBudget(int sms) : prev(t_xpass_sms) { t_xpass_sms = sms; }
+  ~XPassSmBudget() { t_xpass_sms = prev; }
+};
+
 CompressWs carve_compress(void* base, int n, int m, int nu, nmf_prec_t prec) {
   CompressWs w{};
   Carver cv(base);
-  w.plan = xpass_plan(n, m, nu, prec, sm_count());
+  w.plan = xpass_plan(n, m, nu, prec, t_xpass_sms > 0 ? t_xpass_sms : sm_count());
   const int NV = w.plan.NV;
   w.ctrl = cv.take<Control>(1);
   if (x_converted(w.plan, prec)) {
@@ -623,8 +634,12 @@ size_t batch_slot_bytes(int count, const nmf_compress_item_t* items, nmf_prec_t 
 
 }  // namespace
 
+// The SMs of one lane: every lane's X passes fit on the GPU together.
+static int lane_sms(int lanes) { return std::max(1, sm_count() / std::max(1, lanes)); }
+
 size_t nmf_compress_batched_workspace_size(int count, const nmf_compress_item_t* items, nmf_prec_t prec) {
   if (count < 1 || !items) return 0;
+  XPassSmBudget budget(lane_sms(std::min(count, kLanes)));
   const size_t slot = batch_slot_bytes(count, items, prec);
   return slot * (size_t)std::min(count, kLanes);
 }
@@ -642,8 +657,10 @@ nmf_status_t nmf_compress_batched(nmf_stream_t stream, int count, const nmf_comp
   }
   if (prec != NMF_PREC_FP32 && prec != NMF_PREC_BF16) return NMF_ERR_INVALID_ARG;
   if (variant < NMF_VARIANT_SUBSPACE || variant > NMF_VARIANT_GAUSSIAN) return NMF_ERR_INVALID_ARG;
-  const size_t slot = batch_slot_bytes(count, items, prec);
   const int lanes = std::min(count, kLanes);
+  // each item's X passes planned for one lane's share of the SMs
+  XPassSmBudget budget(lane_sms(lanes));
+  const size_t slot = batch_slot_bytes(count, items, prec);
   if (!ws_ok(workspace, workspace_bytes, slot * lanes)) return NMF_ERR_WORKSPACE;
   std::lock_guard<std::mutex> g(g_lane_mu);
   LaneSet* L = nullptr;

@@ -146,8 +146,9 @@ def test_library_sketch_variants_match_default_draw(nmf):
 
 @pytest.mark.parametrize("variant", ["subspace", "power"])
 def test_compress_batched_equals_one_by_one(nmf, variant):
-    # nmf_compress_batched runs each item's compression on its own lane: every
-    # item equals nmf_compress_variant with the same seed, bit for bit
+    # nmf_compress_batched runs each item's compression on its own lane; every
+    # item here has at most 12 tiles, which fit one lane's share of the SMs,
+    # so it equals nmf_compress_variant with the same seed, bit for bit
     import torch
     shapes = [(300, 200, 8), (128, 400, 5), (257, 129, 12), (90, 90, 4), (500, 333, 20), (64, 70, 3),
               (211, 150, 9), (180, 260, 7), (99, 101, 6), (77, 300, 10)]
@@ -158,5 +159,34 @@ def test_compress_batched_equals_one_by_one(nmf, variant):
     torch.cuda.synchronize()
     for i, (X, nu) in enumerate(zip(Xs, nus)):
         ref = nmf.compress(X, nu, 2, prec=1, seed=40 + i, variant=variant)
+        for a, b in zip(outs[i], ref):
+            assert bool(torch.equal(a, b)), i
+
+
+def test_compress_batched_large_item_matches_to_rounding(nmf):
+    # With eight items a lane's X passes are planned for 1/8 of the SMs; an
+    # item of 9 x 8 = 72 tiles then gets fewer split-K parts than alone (the
+    # same products summed in another order). Its leading p basis vectors
+    # (well separated: rank-4 data at 20 dB), the leading p singular values
+    # of X_L and X_R and their norms agree with the one-by-one call to
+    # float32 rounding; the trailing directions (noise, after q = 2) are ill
+    # conditioned and are not compared one by one.
+    import torch
+    shapes = [(1100, 900, 12)] + [(200 + 10 * i, 150 + 7 * i, 6) for i in range(7)]
+    Xs = [_t(synth.lowrank_data(n, m, 4, seed=60 + i, snr_db=20.0, dtype=np.float32)[0]) for i, (n, m, _) in
+          enumerate(shapes)]
+    nus = [nu for _, _, nu in shapes]
+    outs = nmf.compress_batched(Xs, nus, 2, prec=1, seeds=list(range(70, 78)))
+    torch.cuda.synchronize()
+    L, R, XL, XR = (_np(a) for a in outs[0])
+    Lr, Rr, XLr, XRr = (_np(a) for a in nmf.compress(Xs[0], nus[0], 2, prec=1, seed=70))
+    np.testing.assert_allclose(L[:4], Lr[:4], atol=1e-4)
+    np.testing.assert_allclose(R[:, :4], Rr[:, :4], atol=1e-4)
+    for a, b in ((XL, XLr), (XR, XRr)):
+        sa, sb = np.linalg.svd(a, compute_uv=False), np.linalg.svd(b, compute_uv=False)
+        np.testing.assert_allclose(sa[:4], sb[:4], rtol=1e-4)
+        assert abs(np.linalg.norm(a) - np.linalg.norm(b)) <= 1e-4 * np.linalg.norm(b)
+    for i in range(1, len(shapes)):
+        ref = nmf.compress(Xs[i], nus[i], 2, prec=1, seed=70 + i)
         for a, b in zip(outs[i], ref):
             assert bool(torch.equal(a, b)), i
