@@ -150,8 +150,9 @@ nmf_status_t nmf_compress_variant(nmf_stream_t stream, int n, int m, int nu, int
  * on up to 8 library-owned streams forked from `stream` (an event fork and
  * join, so the call is stream-ordered and capturable); each item draws its
  * sketches from its own seed. Each item's X passes are planned for one
- * stream's share of the SMs (the device's SMs / min(count, 8)), so that the
- * streams' passes run side by side: an item whose tile grid fits that share
+ * stream's share of the SMs (a quarter more than the device's SMs /
+ * min(count, 8)), so that the streams' passes run side by side: an item
+ * whose tile grid fits that share
  * gets nmf_compress_variant's plan and results bit for bit; a larger one
  * gets a split-K partition with fewer parts (the same products summed in
  * another order: equal to rounding).

@@ -634,8 +634,15 @@ size_t batch_slot_bytes(int count, const nmf_compress_item_t* items, nmf_prec_t 
 
 }  // namespace
 
-// The SMs of one lane: every lane's X passes fit on the GPU together.
-static int lane_sms(int lanes) { return std::max(1, sm_count() / std::max(1, lanes)); }
+// The SMs one lane's X passes are planned for: a quarter more than an even
+// share (the lanes' passes seldom coincide all at once; at 8 lanes on 152
+// SMs the batched compression measured 24.2 ms with 24 SMs a lane, 24.8
+// with 19, 25.7 with 16 and 27.2 with 12).
+static int lane_sms(int lanes) {
+  lanes = std::max(1, lanes);
+  const int sms = sm_count();
+  return std::min(sms, std::max(1, (5 * sms + 4 * lanes - 1) / (4 * lanes)));
+}
 
 size_t nmf_compress_batched_workspace_size(int count, const nmf_compress_item_t* items, nmf_prec_t prec) {
   if (count < 1 || !items) return 0;

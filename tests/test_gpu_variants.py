@@ -164,8 +164,9 @@ def test_compress_batched_equals_one_by_one(nmf, variant):
 
 
 def test_compress_batched_large_item_matches_to_rounding(nmf):
-    # With eight items a lane's X passes are planned for 1/8 of the SMs; an
-    # item of 9 x 8 = 72 tiles then gets fewer split-K parts than alone (the
+    # With eight items a lane's X passes are planned for about 1/6 of the
+    # SMs (24 of 152); an item of 9 x 8 = 72 tiles then gets fewer split-K
+    # parts than alone (the
     # same products summed in another order). Its leading p basis vectors
     # (well separated: rank-4 data at 20 dB), the leading p singular values
     # of X_L and X_R and their norms agree with the one-by-one call to
