@@ -553,15 +553,18 @@ def run_ours(args):
 
     # X of step k goes to buffer k % 2 on the copy stream once the step that
     # last read that buffer has finished its compression (the solve does not
-    # read X); the compute stream waits for the copy of its own step.
+    # read X); the compute stream waits for the copy of its own step. The next
+    # step's copy is issued after this step's small copies of G0 and F0, so
+    # that they do not queue behind its 400 MB on the copy engine.
     Xbufs = [Xg, torch.empty_like(Xg)]
     cstream = torch.cuda.Stream(device=dev)
     copied = [torch.cuda.Event() for _ in range(2)]
     freed = [torch.cuda.Event() for _ in range(2)]
+    inputs_in = [torch.cuda.Event() for _ in range(2)]
 
-    def issue_copy(k, start):
+    def issue_copy(k, after):
         j = k % 2
-        cstream.wait_event(start)
+        cstream.wait_event(after)
         cstream.wait_event(freed[j])
         with torch.cuda.stream(cstream):
             Xbufs[j].copy_(Xh, non_blocking=True)
@@ -570,12 +573,13 @@ def run_ours(args):
     def e2e_run(steps, start):
         issue_copy(0, start)
         for k in range(steps):
-            if k + 1 < steps:
-                issue_copy(k + 1, start)
             j = k % 2
             stream.wait_event(copied[j])
             G.copy_(G0h, non_blocking=True)
             F.copy_(F0h, non_blocking=True)
+            if k + 1 < steps:
+                inputs_in[j].record(stream)
+                issue_copy(k + 1, inputs_in[j])
             nmf.compress(Xbufs[j], nu, q, prec=prec, seed=w["sketch_seed"], ws=ws_c, out=out)
             comp_status[k:k + 1].copy_(ws_c[:4].view(torch.int32))
             freed[j].record(stream)
