@@ -13,9 +13,11 @@
 // After the block, warp 0 decides its tests in order: lane i sums test i's
 // warp partials in a fixed order and publishes the CTA's partial as one
 // tagged 64-bit word (tag << 32 | float bits) in global memory; a CTA
-// partial above eps^2 fails the test at once; for the others warp 0 waits
-// until every CTA's word of that test carries the tag and sums them in
-// float-float in one fixed order (identical in every CTA). The first test
+// partial above eps^2 fails the test at once; for the others every CTA's
+// word of that test must carry the tag, and warp 0 sums them in float-float
+// in one fixed order (identical in every CTA). The words are gathered test
+// by test by warp 0, or, given a free shared buffer, for all those tests at
+// once by the whole CTA (one round trip to L2). The first test
 // whose total is <= eps^2 stops the loop: its kept iterate is returned, as
 // the sequential rule returns it; the iterations run after it inside the
 // block are discarded. A single relaxed 64-bit store publishes value and tag
