@@ -1,7 +1,8 @@
 """Row-sharded compressed NeNMF (paper_1812_04315_gb300.sharded) on CPU ranks.
 
-Two gloo ranks (spawned processes, as torch.distributed.run launches them)
-split X by rows and run the sharded schedule with a float64 numpy backend;
+Two gloo ranks (and, in one case, three with an uneven row split; spawned
+processes, as torch.distributed.run launches them) split X by rows and run
+the sharded schedule with a float64 numpy backend;
 rank 0 gathers G and compares everything with the single-process oracle
 (Alg. 2 by Householder QR, Alg. 1 by oracle.nenmf) on the same sketches:
 bases, compressed data, the G and F trajectory and the inner-iteration
@@ -108,12 +109,12 @@ def _worker(rank, world, port, case, q):
         dist.destroy_process_group()
 
 
-def _run_two_ranks(case):
+def _run_ranks(case, world=2):
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, case, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, case, q)) for r in range(world)]
     for pr in procs:
         pr.start()
     got = dict(q.get(timeout=300) for _ in procs)
@@ -131,14 +132,12 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("case", CASES)
-def test_two_ranks_match_the_oracle(case):
+def _check_against_oracle(case, got, world):
     n, m, p, nu, qq, T, K, min_inner, tol, seed = case
-    got = _run_two_ranks(case)
     X, G0, F0, OmL, OmR = _inputs(n, m, p, nu, seed)
     L, R, XL, XR = subspace.compress(X, nu, qq, OmL, OmR)
     G, F, info = nenmf.nenmf_compressed(L, R, XL, XR, G0, F0, T, K, min_inner, tol, record=True)
-    for rank in (0, 1):
+    for rank in range(world):
         o = got[rank]
         np.testing.assert_allclose(o["Lt"], L.T, atol=1e-10)
         np.testing.assert_allclose(o["R"], R, atol=1e-10)
@@ -150,8 +149,20 @@ def test_two_ranks_match_the_oracle(case):
         for (g, f), gs, fs in zip(info["history"], o["Ghist"], o["Fhist"]):
             np.testing.assert_allclose(gs, g, atol=1e-9 * np.abs(g).max())
             np.testing.assert_allclose(fs, f, atol=1e-9 * np.abs(f).max())
-    # both ranks hold the same replicated F
-    np.testing.assert_array_equal(got[0]["F"], got[1]["F"])
+    # every rank holds the same replicated F
+    for rank in range(1, world):
+        np.testing.assert_array_equal(got[0]["F"], got[rank]["F"])
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_two_ranks_match_the_oracle(case):
+    _check_against_oracle(case, _run_ranks(case, 2), 2)
+
+
+def test_three_ranks_uneven_rows_match_the_oracle():
+    # 100 rows over three ranks (33, 33, 34), the stop test across blocks
+    case = (100, 140, 4, 9, 1, 5, 30, 1, 1e-4, 19)
+    _check_against_oracle(case, _run_ranks(case, 3), 3)
 
 
 def test_row_blocks():
